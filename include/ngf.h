@@ -1,0 +1,208 @@
+/*
+ * ngf.h -- C ABI of the B300 (sm_103a) matrix-free NGF + curvature
+ * registration library (libngf_b300.so).
+ *
+ * The method (Koenig, Ruehaak, Derksen, Lellmann, "A matrix-free approach to
+ * parallel and memory-efficient deformable image registration"): minimise
+ * J(y) = D(y) + alpha S(y) over a nodal deformation grid y, with D the
+ * normalized-gradient-fields distance (Eq. NGF_discretized) and S the
+ * curvature regulariser (Eq. CURV_discretized), by Gauss-Newton with a
+ * (preconditioned) CG inner solve and Armijo line search, coarse to fine
+ * (Sec. 2.3).  Every derivative is evaluated matrix-free (Sec. 4): no
+ * Jacobian, sparse matrix or other O(voxels) derivative storage is kept.
+ *
+ * Layout (Sec. 2.2, Table 1), 0-based:
+ *  - images R, T: m[0]*m[1]*m[2] float32, x fastest, cell centres at
+ *    (i + 1/2) h; the template T lives on the same grid as R and is zero
+ *    outside it (trilinear interpolation with Dirichlet boundary);
+ *  - nodal vector fields (u, p, q, grad, diag): 3*N float32 with
+ *    N = n[0]*n[1]*n[2], component-major (all x components, then y, then z),
+ *    x fastest; node j sits at j * hy with hy_k = m_k h_k / (n_k - 1), so the
+ *    nodes span the image domain [0, m h];
+ *  - the unknown is the displacement u = y - x^y (physical units of h); the
+ *    warped point of voxel i is x_i + (P u)_i.
+ *
+ * Precision: bulk arithmetic float32; every global reduction (D, S, PCG
+ * inner products), the line-search comparison and the stopping tests in
+ * float64 on the device.
+ *
+ * Ownership and streams: every data pointer is caller-owned and is never
+ * freed by the library.  Plan functions take CUDA device pointers (device or
+ * managed memory) and enqueue their kernels on the plan's stream; a function
+ * that returns host scalars synchronises that stream first, the *_dev
+ * variants write float64 results to device memory and never synchronise.
+ * Workspace is allocated at plan creation, never in an operator call.  A
+ * plan must not be used from two streams or threads at the same time.
+ *
+ * Errors: no exception crosses the ABI; every call returns an ngf_status.
+ * Arguments are validated before any launch (sizes, 2 <= n_k <= m_k + 1,
+ * tau, rho > 0, alpha >= 0, pointer kinds via cudaPointerGetAttributes);
+ * ngf_last_error() returns a message for the last failure.
+ */
+#ifndef NGF_B300_H
+#define NGF_B300_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NGF_ABI_VERSION 1
+
+typedef enum {
+    NGF_OK = 0,
+    NGF_EINVAL = -1,       /* bad size, parameter or pointer kind          */
+    NGF_ECUDA = -2,        /* a CUDA runtime call or launch failed          */
+    NGF_ENOMEM = -3,       /* device allocation failed                      */
+    NGF_ENONFINITE = -4,   /* NaN or Inf in an input image or field         */
+    NGF_EBREAKDOWN = -5,   /* PCG: d^T A d <= 0 or not finite               */
+    NGF_ELINESEARCH = -6,  /* Armijo: no acceptable step in ls_max trials   */
+    NGF_EMAXITER = -7,     /* iteration budget exhausted (not an error)     */
+    NGF_EBOUNDS = -8       /* a size exceeds a documented limit             */
+} ngf_status;
+
+/* One resolution level (Sec. 2.2, Table 1). */
+typedef struct {
+    int32_t m[3];   /* image cells per axis, >= 1                                 */
+    double  h[3];   /* image spacing per axis (e.g. mm), > 0                      */
+    int32_t n[3];   /* deformation-grid NODES per axis, 2 <= n_k <= m_k + 1
+                       (the image grid is at least as fine, Sec. 2.2)            */
+    double  alpha;  /* curvature weight, >= 0 (Eq. discreteenergy)               */
+    double  tau;    /* NGF edge parameter of the template, > 0 (Eq. ngf)         */
+    double  rho;    /* NGF edge parameter of the reference, > 0 (Eq. ngf)        */
+} ngf_level_desc;
+
+typedef struct ngf_plan ngf_plan;
+
+/* Create a plan for one level: validates desc, allocates the workspace (grid
+ * conversion tables, the tile partials of the transposed conversion, reduction
+ * buffers) on the current device and binds the plan to cuda_stream
+ * (cudaStream_t; NULL = legacy default stream). */
+ngf_status ngf_plan_create(ngf_plan** plan, const ngf_level_desc* desc, void* cuda_stream);
+ngf_status ngf_plan_destroy(ngf_plan* plan);
+ngf_status ngf_plan_set_stream(ngf_plan* plan, void* cuda_stream);
+/* Message of the last failure of this plan (plan == NULL: of the last failed
+ * call without a plan on this thread).  Never NULL. */
+const char* ngf_last_error(const ngf_plan* plan);
+
+/* D and S at u (Eqs. NGF_discretized, CURV_discretized); J = D + alpha S.
+ * R, T: device images; u: device 3*N field; D, S: host (synchronises).
+ * D is reduced in float64 from a cancellation-free float32 form of 1 - r^2. */
+ngf_status ngf_objective(ngf_plan* plan, const float* R, const float* T, const float* u,
+                         double* D, double* S);
+/* Same, no synchronisation: dev_DS[0] = D, dev_DS[1] = S (device doubles). */
+ngf_status ngf_objective_dev(ngf_plan* plan, const float* R, const float* T, const float* u,
+                             double* dev_DS);
+
+/* grad = grad D + alpha grad S (Eqs. NGF_discretized_gradient, dPsi,
+ * gradNGF, curvatureMF), device 3*N; D, S: host, nullable (if both are NULL
+ * the call does not synchronise). */
+ngf_status ngf_gradient(ngf_plan* plan, const float* R, const float* T, const float* u,
+                        float* grad, double* D, double* S);
+/* Same with dev_DS (device, 2 doubles, nullable) instead of host scalars. */
+ngf_status ngf_gradient_dev(ngf_plan* plan, const float* R, const float* T, const float* u,
+                            float* grad, double* dev_DS);
+
+/* q = (H + alpha grad^2 S) p with H the Gauss-Newton matrix
+ * 2 hbar P^T dT^T dr^T dr dT P (Eqs. NGF_discretized_hessian, HNGF, hessMult,
+ * curv_hessMult); u, p, q device 3*N; q must not alias p or u.  The
+ * transposed grid conversion is a deterministic tile reduction: repeated
+ * calls return bitwise identical q. */
+ngf_status gn_hessvec(ngf_plan* plan, const float* R, const float* T, const float* u,
+                      const float* p, float* q);
+
+/* q = 2 hbar^y Lap(Lap p) (Eq. curv_hessMult without alpha; Eq.
+ * curvatureMF for p = u); Sp (host, nullable) = hbar^y sum (Lap p)^2.
+ * q may be NULL when only Sp is wanted. */
+ngf_status curvature_apply(ngf_plan* plan, const float* p, float* q, double* Sp);
+
+/* Exact diagonal of H + alpha grad^2 S at u (the Jacobi preconditioner of
+ * the PCG solve), device 3*N.  Its image-grid part is accumulated with
+ * shared-memory atomics, so the last bits can differ between calls. */
+ngf_status ngf_gn_diagonal(ngf_plan* plan, const float* R, const float* T, const float* u,
+                           float* diag);
+
+/* ---- PCG on the device (Sec. 2.3.1) ------------------------------------
+ * Jacobi-preconditioned CG for (H + alpha grad^2 S) x = rhs from x = 0.
+ * All vectors are caller-owned device 3*N floats; dev_scalars is a
+ * caller-owned device array of NGF_PCG_NSCALARS doubles holding the state
+ * (delta = r^T z, d^T A d, alpha, beta, r^T r, b^T b, status, iterations).
+ * A diagonal entry <= 0 preconditions its component by 0 (such a row and
+ * column of the PSD matrix are zero).  pcg_step never synchronises and is a
+ * no-op once the solve has stopped (exact convergence, breakdown, rtol). */
+#define NGF_PCG_NSCALARS 8
+typedef struct {
+    float* x;
+    float* r;
+    float* z;
+    float* d;
+    float* q;
+    const float* diag;
+    double* dev_scalars;
+    double rtol;    /* stop when ||r|| <= rtol ||rhs||; <= 0: fixed iterations */
+} ngf_pcg_state;
+
+typedef struct {
+    int32_t iters_done;
+    int32_t status;     /* 0 running/ok, 1 exact convergence, 2 breakdown, 3 rtol */
+    double  delta;      /* r^T z                                                  */
+    double  rr;         /* r^T r                                                  */
+} ngf_pcg_info;
+
+/* x = 0, r = rhs, z = M^-1 r, d = z and the float64 state; rhs may alias r. */
+ngf_status pcg_init(ngf_plan* plan, ngf_pcg_state* st, const float* rhs);
+/* One iteration: q = A d (gn_hessvec), then the float64 scalars, x, r, z, d. */
+ngf_status pcg_step(ngf_plan* plan, ngf_pcg_state* st, const float* R, const float* T,
+                    const float* u);
+/* `iters` iterations of pcg_step, replayed as one captured CUDA graph when
+ * use_graph != 0 and the plan's stream is not the legacy default stream (the
+ * graph is cached in the plan for these pointers and this count). */
+ngf_status pcg_solve(ngf_plan* plan, ngf_pcg_state* st, const float* R, const float* T,
+                     const float* u, int32_t iters, int32_t use_graph);
+/* Read the state (synchronises). */
+ngf_status pcg_read(ngf_plan* plan, const ngf_pcg_state* st, ngf_pcg_info* info);
+
+/* ---- full registration (Sec. 2.3, coarse to fine) ---------------------- */
+typedef struct {
+    int32_t levels;       /* >= 1; level 0 is `finest`, each coarser level halves
+                             image cells and deformation cells (ceil)           */
+    int32_t gn_iters;     /* Gauss-Newton steps per level                       */
+    int32_t pcg_iters;    /* PCG iterations per Gauss-Newton step               */
+    int32_t ls_max;       /* Armijo trials (step 1, 1/2, 1/4, ...)              */
+    double  armijo_c1;    /* sufficient-decrease constant, e.g. 1e-4            */
+    double  pcg_rtol;     /* <= 0: fixed PCG iteration count                    */
+    int32_t start_level;  /* level at which u_init is given (if u_init)         */
+    const float* u_init;  /* nullable: start field on level start_level (3*N of
+                             that level; host or device); NULL = zero field on
+                             the coarsest level                                 */
+    int32_t use_graph;    /* capture each PCG solve as a CUDA graph             */
+} ngf_options;
+
+typedef struct {
+    double  J, D, S;      /* objective at the returned u (finest level)         */
+    int32_t gn_done;      /* accepted Gauss-Newton steps, all levels            */
+    int32_t pcg_total;    /* PCG iterations, all levels                         */
+    int32_t ls_trials;    /* objective evaluations in line searches             */
+    int32_t ls_fail;      /* levels ended by a failed line search               */
+    int32_t status;       /* 0, or the ngf_status that ended a level early      */
+    double  seconds;      /* wall time of the call                              */
+    int64_t hessvec_voxels; /* sum over gn_hessvec calls of the level's voxels  */
+} ngf_report;
+
+/* Multilevel Gauss-Newton registration.  R, T: finest-level images, u_out:
+ * finest-level 3*N field; each may be a host or a device pointer (host data
+ * is copied in once and the result copied out once, inside the call).  The
+ * image pyramid (mean of up to 8 children, physical extent kept) and the
+ * trilinear prolongation of u run on the device.  Synchronises the stream.
+ * R, T and u_init are checked for NaN/Inf (NGF_ENONFINITE). */
+ngf_status register_multilevel(const ngf_level_desc* finest, const ngf_options* opts,
+                               const float* R, const float* T, float* u_out,
+                               ngf_report* report, void* cuda_stream);
+
+/* Kernels launched by this library in this process so far. */
+int64_t ngf_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,665 @@
+// C-ABI of libngf_b300: plan creation (grid-conversion tables, tile-partial
+// geometry, workspace), validation, and the operator entry points.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ngf_plan.h"
+
+namespace ngf {
+
+std::atomic<int64_t>& launch_counter() {
+    static std::atomic<int64_t> c{0};
+    return c;
+}
+
+static thread_local std::string g_last_error = "no error";
+
+ngf_status set_error(Plan* p, ngf_status s, const std::string& msg) {
+    if (p) p->err = msg;
+    g_last_error = msg;
+    return s;
+}
+
+ngf_status cuda_check(Plan* p, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return NGF_OK;
+    return set_error(p, e == cudaErrorMemoryAllocation ? NGF_ENOMEM : NGF_ECUDA,
+                     std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define NGF_TRY(expr)                \
+    do {                             \
+        ngf_status _s = (expr);      \
+        if (_s != NGF_OK) return _s; \
+    } while (0)
+#define NGF_CU(p, expr, what) NGF_TRY(cuda_check((p), (expr), (what)))
+
+ngf_status validate_desc(const ngf_level_desc* d, std::string& why) {
+    if (!d) { why = "level descriptor is NULL"; return NGF_EINVAL; }
+    for (int a = 0; a < 3; ++a) {
+        if (d->m[a] < 1) { why = "image cells m must be >= 1 on every axis"; return NGF_EINVAL; }
+        if (!(d->h[a] > 0.0) || !std::isfinite(d->h[a])) { why = "spacing h must be finite and > 0"; return NGF_EINVAL; }
+        if (d->n[a] < 2) { why = "deformation nodes n must be >= 2 on every axis"; return NGF_EINVAL; }
+        if (d->n[a] - 1 > d->m[a]) {
+            why = "deformation grid finer than the image grid: need n_k - 1 <= m_k (Sec. 2.2)";
+            return NGF_EINVAL;
+        }
+    }
+    if (!(d->tau > 0.0) || !(d->rho > 0.0) || !std::isfinite(d->tau) || !std::isfinite(d->rho)) {
+        why = "NGF parameters tau and rho must be finite and > 0";
+        return NGF_EINVAL;
+    }
+    if (!(d->alpha >= 0.0) || !std::isfinite(d->alpha)) { why = "alpha must be finite and >= 0"; return NGF_EINVAL; }
+    const long long M = (long long)d->m[0] * d->m[1] * d->m[2];
+    const long long N = (long long)d->n[0] * d->n[1] * d->n[2];
+    if (M > (1LL << 40) || 3 * N > (1LL << 31) - 1) { why = "grid too large"; return NGF_EBOUNDS; }
+    return NGF_OK;
+}
+
+bool is_device_ptr(const void* ptr) {
+    if (!ptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int grid_for(long long n, int max_blocks) {
+    long long b = (n + NT - 1) / NT;
+    if (b < 1) b = 1;
+    return (int)std::min<long long>(b, max_blocks);
+}
+
+// per-axis grid-conversion table of Eq. (grid_conversion): image index v on
+// an axis with m cells and n nodes sits at node coordinate (v+1/2)(n-1)/m
+static void pw_table(int m, int n, std::vector<int>& f, std::vector<float>& w) {
+    f.resize(m);
+    w.resize(m);
+    for (int v = 0; v < m; ++v) {
+        const double c = ((double)v + 0.5) * (double)(n - 1) / (double)m;
+        const double fl = std::floor(c);
+        f[v] = (int)fl;
+        w[v] = (float)(c - fl);
+    }
+}
+
+// node boxes of the tiles along one axis and, per node, the tiles containing it
+static void axis_geometry(int m, int n, const std::vector<int>& f, int TL, int halo, std::vector<int>& b0,
+                          std::vector<int>& lo, std::vector<int>& hi, int& ntiles, int& maxbox) {
+    ntiles = (m + TL - 1) / TL;
+    b0.assign(ntiles, 0);
+    std::vector<int> b1(ntiles, 0);
+    maxbox = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        const int start = t * TL, end = std::min(m, start + TL);
+        if (halo == 0) {
+            b0[t] = f[start];
+            b1[t] = f[end - 1] + 1;
+        } else {
+            b0[t] = f[std::max(start - 1, 0)];
+            b1[t] = f[std::min(start + TL, m - 1)] + 1;
+        }
+        maxbox = std::max(maxbox, b1[t] - b0[t] + 1);
+    }
+    lo.assign(n, INT_MAX);
+    hi.assign(n, -1);
+    for (int t = 0; t < ntiles; ++t)
+        for (int k = b0[t]; k <= b1[t]; ++k) {
+            lo[k] = std::min(lo[k], t);
+            hi[k] = std::max(hi[k], t);
+        }
+}
+
+static ngf_status build_geometry(Plan* p, int halo, const std::vector<int>* f, Geometry& g) {
+    std::vector<int> b0[3], lo[3], hi[3];
+    int nt[3], mb[3];
+    const int TL[3] = {TX, TY, p->zc};
+    for (int a = 0; a < 3; ++a) {
+        axis_geometry(p->m[a], p->n[a], f[a], TL[a], halo, b0[a], lo[a], hi[a], nt[a], mb[a]);
+        for (int k = 0; k < p->n[a]; ++k)
+            if (lo[a][k] > hi[a][k]) return set_error(p, NGF_EINVAL, "internal: node not covered by a tile");
+    }
+    g.ntx = nt[0];
+    g.nty = nt[1];
+    g.ntz = nt[2];
+    g.pbx = mb[0];
+    g.pby = mb[1];
+    g.pbz = mb[2];
+    const size_t total = 2 * (size_t)(p->n[0] + p->n[1] + p->n[2]) + nt[0] + nt[1] + nt[2];
+    std::vector<int> h(total);
+    size_t o = 0;
+    size_t off[9];
+    for (int a = 0; a < 3; ++a) {
+        off[2 * a] = o;
+        std::copy(lo[a].begin(), lo[a].end(), h.begin() + o);
+        o += p->n[a];
+        off[2 * a + 1] = o;
+        std::copy(hi[a].begin(), hi[a].end(), h.begin() + o);
+        o += p->n[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+        off[6 + a] = o;
+        std::copy(b0[a].begin(), b0[a].end(), h.begin() + o);
+        o += nt[a];
+    }
+    NGF_CU(p, cudaMalloc(&g.mem, total * sizeof(int)), "cudaMalloc(geometry)");
+    NGF_CU(p, cudaMemcpy(g.mem, h.data(), total * sizeof(int), cudaMemcpyHostToDevice), "cudaMemcpy(geometry)");
+    g.xlo = g.mem + off[0];
+    g.xhi = g.mem + off[1];
+    g.ylo = g.mem + off[2];
+    g.yhi = g.mem + off[3];
+    g.zlo = g.mem + off[4];
+    g.zhi = g.mem + off[5];
+    g.xb0 = g.mem + off[6];
+    g.yb0 = g.mem + off[7];
+    g.zb0 = g.mem + off[8];
+    return NGF_OK;
+}
+
+static void free_plan(Plan* p) {
+    cudaFree(p->ftab);
+    cudaFree(p->wtab);
+    cudaFree(p->g0.mem);
+    cudaFree(p->g1.mem);
+    cudaFree(p->partial);
+    cudaFree(p->L);
+    cudaFree(p->cdiag);
+    cudaFree(p->dsc);
+    cudaFree(p->dpart);
+    cudaFree(p->dcount);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+}
+
+// curvature part of the Jacobi diagonal: diag(Lap^T Lap) per node.  With
+// Lap = sum_a K_a (K_a the 1-D clamped Laplacian along axis a, Kronecker-
+// extended), diag(Lap^2) = sum_a diag(K_a^2) + sum_{a != b} diag(K_a) diag(K_b);
+// the 1-D matrices are symmetric, so diag(K_a^2) is their column sum of squares.
+static void curvature_diagonal(const Plan* p, std::vector<float>& cd) {
+    cd.assign(p->N, 0.f);
+    std::vector<double> d1[3], dg[3];
+    for (int a = 0; a < 3; ++a) {
+        const double ih2 = 1.0 / (p->hy[a] * p->hy[a]);
+        const int nn = p->n[a];
+        d1[a].assign(nn, 0.0);
+        dg[a].assign(nn, 0.0);
+        for (int i = 0; i < nn; ++i) {
+            double row[3] = {0, 0, 0};  // entries at columns i-1, i, i+1 after clamping
+            for (int s = -1; s <= 1; s += 2) {
+                const int j = std::min(std::max(i + s, 0), nn - 1);
+                row[j - i + 1] += 1.0;
+                row[1] -= 1.0;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const int j = i + k - 1;
+                if (j >= 0 && j < nn) d1[a][j] += row[k] * row[k] * ih2 * ih2;
+            }
+            dg[a][i] = row[1] * ih2;
+        }
+    }
+    for (int z = 0; z < p->n[2]; ++z)
+        for (int y = 0; y < p->n[1]; ++y)
+            for (int x = 0; x < p->n[0]; ++x) {
+                const int idx[3] = {x, y, z};
+                double s = 0.0;
+                for (int a = 0; a < 3; ++a) s += d1[a][idx[a]];
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b)
+                        if (a != b) s += dg[a][idx[a]] * dg[b][idx[b]];
+                cd[x + (long long)p->n[0] * (y + (long long)p->n[1] * z)] = (float)s;
+            }
+}
+
+static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t stream) {
+    std::string why;
+    const ngf_status vs = validate_desc(d, why);
+    if (vs != NGF_OK) return set_error(p, vs, why);
+    p->desc = *d;
+    p->stream = stream;
+    for (int a = 0; a < 3; ++a) {
+        p->m[a] = d->m[a];
+        p->n[a] = d->n[a];
+        p->hy[a] = (double)d->m[a] * d->h[a] / (double)(d->n[a] - 1);
+    }
+    p->M = (long long)p->m[0] * p->m[1] * p->m[2];
+    p->N = (long long)p->n[0] * p->n[1] * p->n[2];
+    p->hbar = d->h[0] * d->h[1] * d->h[2];
+    p->hbary = p->hy[0] * p->hy[1] * p->hy[2];
+
+    // z-chunking: about two CTAs per SM, at least 8 planes per chunk
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long txy = (long long)((p->m[0] + TX - 1) / TX) * ((p->m[1] + TY - 1) / TY);
+    long long nchunk = (2LL * sms + txy / 2) / txy;
+    nchunk = std::max<long long>(1, std::min<long long>(nchunk, p->m[2]));
+    p->zc = (int)std::max<long long>(std::min<long long>(8, p->m[2]), (p->m[2] + nchunk - 1) / nchunk);
+
+    std::vector<int> f[3];
+    std::vector<float> w[3];
+    for (int a = 0; a < 3; ++a) pw_table(p->m[a], p->n[a], f[a], w[a]);
+    const size_t tl = (size_t)p->m[0] + p->m[1] + p->m[2];
+    std::vector<int> fh;
+    std::vector<float> wh;
+    for (int a = 0; a < 3; ++a) {
+        fh.insert(fh.end(), f[a].begin(), f[a].end());
+        wh.insert(wh.end(), w[a].begin(), w[a].end());
+    }
+    NGF_CU(p, cudaMalloc(&p->ftab, tl * sizeof(int)), "cudaMalloc(tables)");
+    NGF_CU(p, cudaMalloc(&p->wtab, tl * sizeof(float)), "cudaMalloc(tables)");
+    NGF_CU(p, cudaMemcpy(p->ftab, fh.data(), tl * sizeof(int), cudaMemcpyHostToDevice), "cudaMemcpy(tables)");
+    NGF_CU(p, cudaMemcpy(p->wtab, wh.data(), tl * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy(tables)");
+
+    NGF_TRY(build_geometry(p, 0, f, p->g0));
+    NGF_TRY(build_geometry(p, 1, f, p->g1));
+    if (p->g0.pbx > NBX || p->g0.pby > NBY || p->g1.pbx > DBX || p->g1.pby > DBY)
+        return set_error(p, NGF_EBOUNDS, "internal: tile node box exceeds the kernel's shared-memory box");
+    const long long pf = std::max(p->g0.partial_floats(), p->g1.partial_floats());
+    NGF_CU(p, cudaMalloc(&p->partial, pf * sizeof(float)), "cudaMalloc(partials)");
+    NGF_CU(p, cudaMalloc(&p->L, 3 * p->N * sizeof(float)), "cudaMalloc(L)");
+    {
+        std::vector<float> cd;
+        curvature_diagonal(p, cd);
+        NGF_CU(p, cudaMalloc(&p->cdiag, p->N * sizeof(float)), "cudaMalloc(cdiag)");
+        NGF_CU(p, cudaMemcpy(p->cdiag, cd.data(), p->N * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy(cdiag)");
+    }
+
+    p->img_blocks = (int)p->g0.tiles();
+    p->diag_blocks = (int)p->g1.tiles();
+    p->node_blocks = grid_for(3 * p->N, 4 * sms);
+    p->dpart_len = 2 * (size_t)std::max({p->img_blocks, p->diag_blocks, p->node_blocks, 8 * sms});
+    NGF_CU(p, cudaMalloc(&p->dsc, 16 * sizeof(double)), "cudaMalloc(scalars)");
+    NGF_CU(p, cudaMemset(p->dsc, 0, 16 * sizeof(double)), "cudaMemset(scalars)");
+    NGF_CU(p, cudaMalloc(&p->dpart, p->dpart_len * sizeof(double)), "cudaMalloc(partials64)");
+    NGF_CU(p, cudaMalloc(&p->dcount, 4 * sizeof(unsigned int)), "cudaMalloc(counter)");
+    NGF_CU(p, cudaMemset(p->dcount, 0, 4 * sizeof(unsigned int)), "cudaMemset(counter)");
+
+    NGF_CU(p, cudaFuncSetAttribute(k_image_obj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
+    NGF_CU(p, cudaFuncSetAttribute(k_image_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
+    NGF_CU(p, cudaFuncSetAttribute(k_image_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
+    NGF_CU(p, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
+    return NGF_OK;
+}
+
+NodeGeom node_geom(const Plan* p) {
+    NodeGeom G;
+    G.n0 = p->n[0];
+    G.n1 = p->n[1];
+    G.n2 = p->n[2];
+    G.N = p->N;
+    for (int a = 0; a < 3; ++a) G.ihy2[a] = (float)(1.0 / (p->hy[a] * p->hy[a]));
+    return G;
+}
+
+ImgParams img_params(const Plan* p, const float* R, const float* T, const float* u, const float* pv, int mode,
+                     const Geometry& g, double* dout) {
+    ImgParams P;
+    const ngf_level_desc& d = p->desc;
+    P.m0 = p->m[0];
+    P.m1 = p->m[1];
+    P.m2 = p->m[2];
+    P.n0 = p->n[0];
+    P.n1 = p->n[1];
+    P.n2 = p->n[2];
+    P.M = p->M;
+    P.N = p->N;
+    for (int a = 0; a < 3; ++a) {
+        P.ih[a] = (float)(1.0 / d.h[a]);
+        P.ihs[a] = (float)(1.0 / (d.h[a] * d.h[a]));
+        P.hh[a] = (float)(1.0 / (2.0 * d.h[a] * d.h[a]));
+    }
+    P.tau = (float)d.tau;
+    P.rho = (float)d.rho;
+    P.tr = (float)(d.tau * d.rho);
+    P.tau2 = (float)(d.tau * d.tau);
+    P.rho2 = (float)(d.rho * d.rho);
+    P.qscale = (float)((mode == MODE_GRAD ? -2.0 : 2.0) * p->hbar);
+    P.hbar = p->hbar;
+    P.R = R;
+    P.T = T;
+    P.u = u;
+    P.p = pv;
+    P.fx = p->ftab;
+    P.fy = p->ftab + p->m[0];
+    P.fz = p->ftab + p->m[0] + p->m[1];
+    P.wx = p->wtab;
+    P.wy = p->wtab + p->m[0];
+    P.wz = p->wtab + p->m[0] + p->m[1];
+    P.zc = p->zc;
+    P.pbx = g.pbx;
+    P.pby = g.pby;
+    P.pbz = g.pbz;
+    P.partial = p->partial;
+    P.dpart = p->dpart;
+    P.dcount = p->dcount;
+    P.dout = dout;
+    return P;
+}
+
+CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const float* L, const float* cdiag,
+                             const float* dotw, double* dout) {
+    CombineParams C;
+    C.G = node_geom(p);
+    C.partial = p->partial;
+    C.pbx = g.pbx;
+    C.pby = g.pby;
+    C.pbz = g.pbz;
+    C.ntx = g.ntx;
+    C.nty = g.nty;
+    C.xlo = g.xlo;
+    C.xhi = g.xhi;
+    C.ylo = g.ylo;
+    C.yhi = g.yhi;
+    C.zlo = g.zlo;
+    C.zhi = g.zhi;
+    C.xb0 = g.xb0;
+    C.yb0 = g.yb0;
+    C.zb0 = g.zb0;
+    C.L = L;
+    C.cdiag = cdiag;
+    C.cscale = (float)(p->desc.alpha * 2.0 * p->hbary);
+    C.out = out;
+    C.dotw = dotw;
+    C.dpart = p->dpart;
+    C.dcount = p->dcount;
+    C.dout = dout;
+    return C;
+}
+
+static dim3 img_grid(const Geometry& g) { return dim3(g.ntx, g.nty, g.ntz); }
+
+ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* u, double* dD, double* dS) {
+    ImgParams P = img_params(p, R, T, u, nullptr, MODE_OBJ, p->g0, dD);
+    NGF_CU(p, launch(k_image_obj, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_obj");
+    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
+                     p->dcount, dS, p->hbary),
+           "k_lap");
+    return NGF_OK;
+}
+
+ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u, float* g, double* dD,
+                         double* dS) {
+    ImgParams P = img_params(p, R, T, u, nullptr, MODE_GRAD, p->g0, dD);
+    NGF_CU(p, launch(k_image_grad, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_grad");
+    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
+                     p->dcount, dS, p->hbary),
+           "k_lap");
+    CombineParams C = combine_params(p, p->g0, g, p->L, nullptr, nullptr, nullptr);
+    NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+    return NGF_OK;
+}
+
+ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u, const float* pv, float* q,
+                        const float* dotw, double* dout) {
+    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), pv, p->L, p->dpart,
+                     p->dcount, (double*)nullptr, 0.0),
+           "k_lap");
+    ImgParams P = img_params(p, R, T, u, pv, MODE_HESS, p->g0, nullptr);
+    NGF_CU(p, launch(k_image_hess, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_hess");
+    CombineParams C = combine_params(p, p->g0, q, p->L, nullptr, dotw, dout);
+    NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+    return NGF_OK;
+}
+
+ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag) {
+    ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g1, nullptr);
+    NGF_CU(p, launch(k_diag, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P), "k_diag");
+    CombineParams C = combine_params(p, p->g1, diag, nullptr, p->cdiag, nullptr, nullptr);
+    NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+    return NGF_OK;
+}
+
+ngf_status dot_impl(Plan* p, long long n, const float* a, const float* b, double* dout) {
+    NGF_CU(p, launch(k_dot, dim3(grid_for(n, (int)(p->dpart_len / 2))), dim3(NT), 0, p->stream, n, a, b, p->dpart,
+                     p->dcount, dout),
+           "k_dot");
+    return NGF_OK;
+}
+
+static ngf_status need_dev(Plan* p, std::initializer_list<std::pair<const void*, const char*>> ptrs) {
+    for (auto& kv : ptrs)
+        if (!is_device_ptr(kv.first))
+            return set_error(p, NGF_EINVAL, std::string(kv.second) + " must be a CUDA device (or managed) pointer");
+    return NGF_OK;
+}
+
+static ngf_status sync_read(Plan* p, double* h, int count) {
+    NGF_CU(p, cudaMemcpyAsync(h, p->dsc, count * sizeof(double), cudaMemcpyDeviceToHost, p->stream), "read scalars");
+    NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    return NGF_OK;
+}
+
+}  // namespace ngf
+
+using namespace ngf;
+
+extern "C" {
+
+ngf_status ngf_plan_create(ngf_plan** out, const ngf_level_desc* desc, void* cuda_stream) {
+    if (!out) return set_error(nullptr, NGF_EINVAL, "plan output pointer is NULL");
+    *out = nullptr;
+    ngf_plan* pl = new (std::nothrow) ngf_plan();
+    if (!pl) return set_error(nullptr, NGF_ENOMEM, "host allocation failed");
+    ngf_status s = create_plan(&pl->impl, desc, (cudaStream_t)cuda_stream);
+    if (s != NGF_OK) {
+        g_last_error = pl->impl.err;
+        free_plan(&pl->impl);
+        delete pl;
+        return s;
+    }
+    *out = pl;
+    return NGF_OK;
+}
+
+ngf_status ngf_plan_destroy(ngf_plan* plan) {
+    if (!plan) return NGF_OK;
+    free_plan(&plan->impl);
+    delete plan;
+    return NGF_OK;
+}
+
+ngf_status ngf_plan_set_stream(ngf_plan* plan, void* cuda_stream) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    plan->impl.stream = (cudaStream_t)cuda_stream;
+    if (plan->impl.graph) cudaGraphExecDestroy(plan->impl.graph);
+    plan->impl.graph = nullptr;
+    plan->impl.graph_key.clear();
+    return NGF_OK;
+}
+
+const char* ngf_last_error(const ngf_plan* plan) {
+    if (plan) return plan->impl.err.empty() ? "no error" : plan->impl.err.c_str();
+    return g_last_error.c_str();
+}
+
+ngf_status ngf_objective_dev(ngf_plan* plan, const float* R, const float* T, const float* u, double* dev_DS) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}, {dev_DS, "dev_DS"}}));
+    return objective_impl(p, R, T, u, dev_DS, dev_DS + 1);
+}
+
+ngf_status ngf_objective(ngf_plan* plan, const float* R, const float* T, const float* u, double* D, double* S) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}}));
+    NGF_TRY(objective_impl(p, R, T, u, p->dsc, p->dsc + 1));
+    double h[2];
+    NGF_TRY(sync_read(p, h, 2));
+    if (D) *D = h[0];
+    if (S) *S = h[1];
+    return NGF_OK;
+}
+
+ngf_status ngf_gradient_dev(ngf_plan* plan, const float* R, const float* T, const float* u, float* grad,
+                            double* dev_DS) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}, {grad, "grad"}}));
+    if (dev_DS && !is_device_ptr(dev_DS)) return set_error(p, NGF_EINVAL, "dev_DS must be a device pointer");
+    double* dD = dev_DS ? dev_DS : p->dsc;
+    return gradient_impl(p, R, T, u, grad, dD, dD + 1);
+}
+
+ngf_status ngf_gradient(ngf_plan* plan, const float* R, const float* T, const float* u, float* grad, double* D,
+                        double* S) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}, {grad, "grad"}}));
+    NGF_TRY(gradient_impl(p, R, T, u, grad, p->dsc, p->dsc + 1));
+    if (D || S) {
+        double h[2];
+        NGF_TRY(sync_read(p, h, 2));
+        if (D) *D = h[0];
+        if (S) *S = h[1];
+    }
+    return NGF_OK;
+}
+
+ngf_status gn_hessvec(ngf_plan* plan, const float* R, const float* T, const float* u, const float* pv, float* q) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}, {pv, "p"}, {q, "q"}}));
+    if ((const void*)q == (const void*)pv || (const void*)q == (const void*)u)
+        return set_error(p, NGF_EINVAL, "q must not alias p or u");
+    return hessvec_impl(p, R, T, u, pv, q, nullptr, nullptr);
+}
+
+ngf_status curvature_apply(ngf_plan* plan, const float* pv, float* q, double* Sp) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(need_dev(p, {{pv, "p"}}));
+    if (q && !is_device_ptr(q)) return set_error(p, NGF_EINVAL, "q must be a device pointer");
+    if (q && (const void*)q == (const void*)pv) return set_error(p, NGF_EINVAL, "q must not alias p");
+    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), pv, p->L, p->dpart, p->dcount,
+                     Sp ? p->dsc + 1 : (double*)nullptr, p->hbary),
+           "k_lap");
+    if (q)
+        NGF_CU(p, launch(k_lap2, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), (const float*)p->L, q,
+                         (float)(2.0 * p->hbary)),
+               "k_lap2");
+    if (Sp) {
+        double h[2];
+        NGF_TRY(sync_read(p, h, 2));
+        *Sp = h[1];
+    }
+    return NGF_OK;
+}
+
+ngf_status ngf_gn_diagonal(ngf_plan* plan, const float* R, const float* T, const float* u, float* diag) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}, {diag, "diag"}}));
+    return diagonal_impl(p, R, T, u, diag);
+}
+
+static PcgParams pcg_params(Plan* p, ngf_pcg_state* st, const float* rhs) {
+    PcgParams P;
+    P.n = 3 * p->N;
+    P.x = st->x;
+    P.r = st->r;
+    P.z = st->z;
+    P.d = st->d;
+    P.q = st->q;
+    P.diag = st->diag;
+    P.rhs = rhs;
+    P.sc = st->dev_scalars;
+    P.part = p->dpart;
+    P.count = p->dcount;
+    P.rtol = st->rtol;
+    return P;
+}
+
+static ngf_status check_state(Plan* p, const ngf_pcg_state* st) {
+    if (!st) return set_error(p, NGF_EINVAL, "PCG state is NULL");
+    return need_dev(p, {{st->x, "x"}, {st->r, "r"}, {st->z, "z"}, {st->d, "d"}, {st->q, "q"}, {st->diag, "diag"},
+                        {st->dev_scalars, "dev_scalars"}});
+}
+
+ngf_status pcg_init(ngf_plan* plan, ngf_pcg_state* st, const float* rhs) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(check_state(p, st));
+    NGF_TRY(need_dev(p, {{rhs, "rhs"}}));
+    PcgParams P = pcg_params(p, st, rhs);
+    NGF_CU(p, launch(k_pcg_init, dim3(p->node_blocks), dim3(NT), 0, p->stream, P), "k_pcg_init");
+    return NGF_OK;
+}
+
+static ngf_status pcg_step_impl(Plan* p, ngf_pcg_state* st, const float* R, const float* T, const float* u) {
+    PcgParams P = pcg_params(p, st, nullptr);
+    NGF_TRY(hessvec_impl(p, R, T, u, st->d, st->q, st->d, st->dev_scalars + PS_DQ));
+    NGF_CU(p, launch(k_pcg_update, dim3(p->node_blocks), dim3(NT), 0, p->stream, P), "k_pcg_update");
+    NGF_CU(p, launch(k_pcg_dir, dim3(p->node_blocks), dim3(NT), 0, p->stream, P), "k_pcg_dir");
+    return NGF_OK;
+}
+
+ngf_status pcg_step(ngf_plan* plan, ngf_pcg_state* st, const float* R, const float* T, const float* u) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(check_state(p, st));
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}}));
+    return pcg_step_impl(p, st, R, T, u);
+}
+
+ngf_status pcg_solve(ngf_plan* plan, ngf_pcg_state* st, const float* R, const float* T, const float* u,
+                     int32_t iters, int32_t use_graph) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    NGF_TRY(check_state(p, st));
+    NGF_TRY(need_dev(p, {{R, "R"}, {T, "T"}, {u, "u"}}));
+    if (iters < 0) return set_error(p, NGF_EINVAL, "iters must be >= 0");
+    if (iters == 0) return NGF_OK;
+    // the legacy default stream cannot be captured: launch directly there
+    if (!use_graph || p->stream == nullptr) {
+        for (int i = 0; i < iters; ++i) NGF_TRY(pcg_step_impl(p, st, R, T, u));
+        return NGF_OK;
+    }
+    std::vector<const void*> key = {st->x, st->r, st->z, st->d, st->q, st->diag, st->dev_scalars, R, T, u};
+    if (!(p->graph && p->graph_iters == iters && key == p->graph_key)) {
+        if (p->graph) cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+        cudaGraph_t g;
+        const int64_t before = launch_counter().load();
+        NGF_CU(p, cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+        ngf_status s = NGF_OK;
+        for (int i = 0; i < iters && s == NGF_OK; ++i) s = pcg_step_impl(p, st, R, T, u);
+        cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+        if (s != NGF_OK) return s;
+        NGF_CU(p, e, "cudaStreamEndCapture");
+        p->graph_kernels = launch_counter().load() - before;
+        launch_counter().fetch_sub(p->graph_kernels);  // captured, not launched
+        cudaError_t ie = cudaGraphInstantiate(&p->graph, g, 0);
+        cudaGraphDestroy(g);
+        NGF_CU(p, ie, "cudaGraphInstantiate");
+        p->graph_key = key;
+        p->graph_iters = iters;
+    }
+    NGF_CU(p, cudaGraphLaunch(p->graph, p->stream), "cudaGraphLaunch");
+    launch_counter().fetch_add(p->graph_kernels);
+    return NGF_OK;
+}
+
+ngf_status pcg_read(ngf_plan* plan, const ngf_pcg_state* st, ngf_pcg_info* info) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    if (!st || !info) return set_error(p, NGF_EINVAL, "state or info is NULL");
+    double h[NGF_PCG_NSCALARS];
+    NGF_CU(p, cudaMemcpyAsync(h, st->dev_scalars, sizeof(h), cudaMemcpyDeviceToHost, p->stream), "read PCG state");
+    NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    info->iters_done = (int32_t)h[PS_ITERS];
+    info->status = (int32_t)h[PS_STATUS];
+    info->delta = h[PS_DELTA];
+    info->rr = h[PS_RR];
+    return NGF_OK;
+}
+
+int64_t ngf_launch_count(void) { return launch_counter().load(); }
+
+}  // extern "C"

@@ -1,0 +1,274 @@
+// Multilevel Gauss-Newton registration (Sec. 2.3): image pyramid and
+// prolongation on the device, per-level Gauss-Newton steps with a
+// Jacobi-preconditioned CG solve (optionally one captured CUDA graph per
+// solve) and Armijo backtracking decided in float64.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ngf_plan.h"
+
+namespace ngf {
+
+// coarse-to-fine level sequence: each coarser level halves image cells and
+// deformation cells (ceil) and keeps the physical extent of the domain
+static ngf_level_desc level_at(const ngf_level_desc& finest, int level) {
+    ngf_level_desc d = finest;
+    for (int k = 0; k < level; ++k)
+        for (int a = 0; a < 3; ++a) {
+            const int m = d.m[a], mc = (m + 1) / 2;
+            int cc = d.n[a] / 2;  // ceil((n - 1) / 2) deformation cells
+            if (cc > mc) cc = mc;
+            if (cc < 1) cc = 1;
+            d.h[a] = d.h[a] * (double)m / (double)mc;
+            d.m[a] = mc;
+            d.n[a] = cc + 1;
+        }
+    return d;
+}
+
+struct DevBuf {
+    void* ptr = nullptr;
+    ~DevBuf() { cudaFree(ptr); }
+    template <class T>
+    T* as() const { return static_cast<T*>(ptr); }
+};
+
+struct PlanGuard {
+    ngf_plan* p = nullptr;
+    ~PlanGuard() { ngf_plan_destroy(p); }
+};
+
+}  // namespace ngf
+
+using namespace ngf;
+
+#define DRV_CU(expr, what)                                           \
+    do {                                                             \
+        cudaError_t _e = (expr);                                     \
+        if (_e != cudaSuccess) return cuda_check(nullptr, _e, what); \
+    } while (0)
+#define DRV_TRY(expr)                \
+    do {                             \
+        ngf_status _s = (expr);      \
+        if (_s != NGF_OK) return _s; \
+    } while (0)
+
+extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ngf_options* o, const float* R,
+                                          const float* T, float* u_out, ngf_report* rep, void* cuda_stream) {
+    const auto t_start = std::chrono::steady_clock::now();
+    std::string why;
+    const ngf_status vs = validate_desc(finest, why);
+    if (vs != NGF_OK) return set_error(nullptr, vs, why);
+    if (!o || !R || !T || !u_out) return set_error(nullptr, NGF_EINVAL, "options, R, T and u_out must be non-NULL");
+    if (o->levels < 1 || o->levels > 16) return set_error(nullptr, NGF_EINVAL, "levels must be in [1, 16]");
+    if (o->gn_iters < 0 || o->pcg_iters < 0 || o->ls_max < 1)
+        return set_error(nullptr, NGF_EINVAL, "gn_iters, pcg_iters >= 0 and ls_max >= 1 required");
+    if (o->u_init && (o->start_level < 0 || o->start_level >= o->levels))
+        return set_error(nullptr, NGF_EINVAL, "start_level out of range");
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    ngf_report r{};
+
+    const int L = o->levels;
+    std::vector<ngf_level_desc> lv(L);
+    for (int l = 0; l < L; ++l) lv[l] = level_at(*finest, l);
+    for (int l = 0; l < L; ++l)
+        for (int a = 0; a < 3; ++a)
+            if (lv[l].n[a] > 4096) return set_error(nullptr, NGF_EBOUNDS, "more than 4096 nodes on an axis");
+    const long long M0 = (long long)lv[0].m[0] * lv[0].m[1] * lv[0].m[2];
+    const long long N0 = (long long)lv[0].n[0] * lv[0].n[1] * lv[0].n[2];
+
+    // images of every level (level 0 may be the caller's device arrays)
+    std::vector<DevBuf> imgs(2 * L);
+    std::vector<const float*> Rl(L), Tl(L);
+    const bool R_dev = is_device_ptr(R), T_dev = is_device_ptr(T), U_dev = is_device_ptr(u_out);
+    for (int l = 0; l < L; ++l) {
+        const long long M = (long long)lv[l].m[0] * lv[l].m[1] * lv[l].m[2];
+        if (l == 0 && R_dev) {
+            Rl[0] = R;
+        } else {
+            DRV_CU(cudaMalloc(&imgs[2 * l].ptr, M * sizeof(float)), "cudaMalloc(R level)");
+            Rl[l] = imgs[2 * l].as<float>();
+        }
+        if (l == 0 && T_dev) {
+            Tl[0] = T;
+        } else {
+            DRV_CU(cudaMalloc(&imgs[2 * l + 1].ptr, M * sizeof(float)), "cudaMalloc(T level)");
+            Tl[l] = imgs[2 * l + 1].as<float>();
+        }
+    }
+    if (!R_dev) DRV_CU(cudaMemcpyAsync((void*)Rl[0], R, M0 * sizeof(float), cudaMemcpyHostToDevice, stream), "copy R");
+    if (!T_dev) DRV_CU(cudaMemcpyAsync((void*)Tl[0], T, M0 * sizeof(float), cudaMemcpyHostToDevice, stream), "copy T");
+
+    // work vectors sized for the finest level
+    const long long n3 = 3 * N0;
+    DevBuf bu, but, bg, bdiag, bx, br, bz, bd, bq, bsc, bpart, bcnt, btab;
+    DRV_CU(cudaMalloc(&bu.ptr, n3 * sizeof(float)), "cudaMalloc(u)");
+    DRV_CU(cudaMalloc(&but.ptr, n3 * sizeof(float)), "cudaMalloc(ut)");
+    DRV_CU(cudaMalloc(&bg.ptr, n3 * sizeof(float)), "cudaMalloc(g)");
+    DRV_CU(cudaMalloc(&bdiag.ptr, n3 * sizeof(float)), "cudaMalloc(diag)");
+    DRV_CU(cudaMalloc(&bx.ptr, n3 * sizeof(float)), "cudaMalloc(x)");
+    DRV_CU(cudaMalloc(&br.ptr, n3 * sizeof(float)), "cudaMalloc(r)");
+    DRV_CU(cudaMalloc(&bz.ptr, n3 * sizeof(float)), "cudaMalloc(z)");
+    DRV_CU(cudaMalloc(&bd.ptr, n3 * sizeof(float)), "cudaMalloc(d)");
+    DRV_CU(cudaMalloc(&bq.ptr, n3 * sizeof(float)), "cudaMalloc(q)");
+    DRV_CU(cudaMalloc(&bsc.ptr, 32 * sizeof(double)), "cudaMalloc(scalars)");
+    DRV_CU(cudaMemsetAsync(bsc.ptr, 0, 32 * sizeof(double), stream), "memset(scalars)");
+    DRV_CU(cudaMalloc(&bpart.ptr, 4096 * sizeof(double)), "cudaMalloc(partials)");
+    DRV_CU(cudaMalloc(&bcnt.ptr, 4 * sizeof(unsigned int)), "cudaMalloc(counter)");
+    DRV_CU(cudaMemsetAsync(bcnt.ptr, 0, 4 * sizeof(unsigned int), stream), "memset(counter)");
+    DRV_CU(cudaMalloc(&btab.ptr, 3 * 4096 * (sizeof(int) + sizeof(float))), "cudaMalloc(prolongation tables)");
+    double* dsc = bsc.as<double>();  // 0 D, 1 S, 2 dot, 3 non-finite count; 8.. PCG state
+    double* pcg_sc = dsc + 8;
+
+    auto count_bad = [&](const float* a, long long n, double& bad) -> ngf_status {
+        DRV_CU(launch(k_nonfinite, dim3(grid_for(n, 2048)), dim3(NT), 0, stream, n, a, bpart.as<double>(),
+                      bcnt.as<unsigned int>(), dsc + 3),
+               "k_nonfinite");
+        DRV_CU(cudaMemcpyAsync(&bad, dsc + 3, sizeof(double), cudaMemcpyDeviceToHost, stream), "read check");
+        DRV_CU(cudaStreamSynchronize(stream), "sync");
+        return NGF_OK;
+    };
+    double bad = 0.0;
+    DRV_TRY(count_bad(Rl[0], M0, bad));
+    if (bad != 0.0) return set_error(nullptr, NGF_ENONFINITE, "R has NaN/Inf");
+    DRV_TRY(count_bad(Tl[0], M0, bad));
+    if (bad != 0.0) return set_error(nullptr, NGF_ENONFINITE, "T has NaN/Inf");
+
+    // image pyramid
+    for (int l = 1; l < L; ++l) {
+        const long long Mc = (long long)lv[l].m[0] * lv[l].m[1] * lv[l].m[2];
+        DRV_CU(launch(k_restrict, dim3(grid_for(Mc, 4096)), dim3(NT), 0, stream, lv[l - 1].m[0], lv[l - 1].m[1],
+                      lv[l - 1].m[2], Rl[l - 1], (float*)Rl[l]),
+               "k_restrict");
+        DRV_CU(launch(k_restrict, dim3(grid_for(Mc, 4096)), dim3(NT), 0, stream, lv[l - 1].m[0], lv[l - 1].m[1],
+                      lv[l - 1].m[2], Tl[l - 1], (float*)Tl[l]),
+               "k_restrict");
+    }
+
+    const int start = o->u_init ? o->start_level : L - 1;
+    float* u = bu.as<float>();
+    float* ut = but.as<float>();
+    {
+        const long long Ns = (long long)lv[start].n[0] * lv[start].n[1] * lv[start].n[2];
+        if (o->u_init) {
+            DRV_CU(cudaMemcpyAsync(u, o->u_init, 3 * Ns * sizeof(float), cudaMemcpyDefault, stream), "copy u_init");
+            DRV_TRY(count_bad(u, 3 * Ns, bad));
+            if (bad != 0.0) return set_error(nullptr, NGF_ENONFINITE, "u_init has NaN/Inf");
+        } else {
+            DRV_CU(cudaMemsetAsync(u, 0, 3 * Ns * sizeof(float), stream), "zero u");
+        }
+    }
+
+    for (int l = start; l >= 0; --l) {
+        const ngf_level_desc& d = lv[l];
+        const long long N = (long long)d.n[0] * d.n[1] * d.n[2];
+        const long long M = (long long)d.m[0] * d.m[1] * d.m[2];
+        if (l != start) {  // prolongate u from level l+1
+            const ngf_level_desc& c = lv[l + 1];
+            std::vector<int> tf;
+            std::vector<float> tw;
+            for (int a = 0; a < 3; ++a)
+                for (int i = 0; i < d.n[a]; ++i) {
+                    const double cc = (double)i * (double)(c.n[a] - 1) / (double)(d.n[a] - 1);
+                    double fl = std::floor(cc);
+                    if (fl > c.n[a] - 2) fl = c.n[a] - 2;
+                    tf.push_back((int)fl);
+                    tw.push_back((float)(cc - fl));
+                }
+            int* dtf = btab.as<int>();
+            float* dtw = reinterpret_cast<float*>(dtf + 3 * 4096);
+            DRV_CU(cudaMemcpyAsync(dtf, tf.data(), tf.size() * sizeof(int), cudaMemcpyHostToDevice, stream), "tables");
+            DRV_CU(cudaMemcpyAsync(dtw, tw.data(), tw.size() * sizeof(float), cudaMemcpyHostToDevice, stream), "tables");
+            const long long Nc = (long long)c.n[0] * c.n[1] * c.n[2];
+            DRV_CU(launch(k_prolong, dim3(grid_for(3 * N, 4096)), dim3(NT), 0, stream, d.n[0], d.n[1], d.n[2],
+                          c.n[0], c.n[1], Nc, (const int*)dtf, (const float*)dtw, (const float*)u, ut),
+                   "k_prolong");
+            std::swap(u, ut);
+            // the host tables must outlive the asynchronous copies
+            DRV_CU(cudaStreamSynchronize(stream), "sync");
+        }
+        PlanGuard pg;
+        DRV_TRY(ngf_plan_create(&pg.p, &d, stream));
+        Plan* p = &pg.p->impl;
+        ngf_pcg_state st;
+        st.x = bx.as<float>();
+        st.r = br.as<float>();
+        st.z = bz.as<float>();
+        st.d = bd.as<float>();
+        st.q = bq.as<float>();
+        st.diag = bdiag.as<float>();
+        st.dev_scalars = pcg_sc;
+        st.rtol = o->pcg_rtol;
+        float* g = bg.as<float>();
+        const long long n = 3 * N;
+        for (int k = 0; k < o->gn_iters; ++k) {
+            DRV_TRY(gradient_impl(p, Rl[l], Tl[l], u, g, dsc, dsc + 1));
+            DRV_TRY(dot_impl(p, n, g, g, dsc + 2));
+            double h[3];
+            DRV_CU(cudaMemcpyAsync(h, dsc, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
+            DRV_CU(cudaStreamSynchronize(stream), "sync");
+            const double J0 = h[0] + d.alpha * h[1], gg = h[2];
+            if (gg == 0.0) break;  // stationary point
+            DRV_TRY(diagonal_impl(p, Rl[l], Tl[l], u, bdiag.as<float>()));
+            DRV_CU(launch(k_scale, dim3(p->node_blocks), dim3(NT), 0, stream, n, -1.0f, (const float*)g, st.r),
+                   "k_scale");
+            DRV_TRY(pcg_init(pg.p, &st, st.r));
+            DRV_TRY(pcg_solve(pg.p, &st, Rl[l], Tl[l], u, o->pcg_iters, o->use_graph));
+            r.hessvec_voxels += (int64_t)o->pcg_iters * M;
+            double ps[NGF_PCG_NSCALARS];
+            DRV_TRY(dot_impl(p, n, g, st.x, dsc + 2));
+            DRV_CU(cudaMemcpyAsync(ps, pcg_sc, sizeof(ps), cudaMemcpyDeviceToHost, stream), "read PCG");
+            DRV_CU(cudaMemcpyAsync(h + 2, dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, stream), "read gs");
+            DRV_CU(cudaStreamSynchronize(stream), "sync");
+            r.pcg_total += (int32_t)ps[PS_ITERS];
+            double gs = h[2];
+            float* s = st.x;
+            if (!(gs < 0.0)) {  // not a descent direction: steepest descent
+                DRV_CU(launch(k_scale, dim3(p->node_blocks), dim3(NT), 0, stream, n, -1.0f, (const float*)g, s),
+                       "k_scale");
+                gs = -gg;
+            }
+            double eta = 1.0;
+            bool accepted = false;
+            for (int t = 0; t < o->ls_max; ++t) {
+                DRV_CU(launch(k_axpy, dim3(p->node_blocks), dim3(NT), 0, stream, n, (float)eta, (const float*)u,
+                              (const float*)s, ut),
+                       "k_axpy");
+                DRV_TRY(objective_impl(p, Rl[l], Tl[l], ut, dsc, dsc + 1));
+                DRV_CU(cudaMemcpyAsync(h, dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
+                DRV_CU(cudaStreamSynchronize(stream), "sync");
+                r.ls_trials++;
+                if (h[0] + d.alpha * h[1] <= J0 + o->armijo_c1 * eta * gs) {
+                    accepted = true;
+                    break;
+                }
+                eta *= 0.5;
+            }
+            if (!accepted) {
+                r.ls_fail++;
+                r.status = NGF_ELINESEARCH;
+                break;
+            }
+            std::swap(u, ut);
+            r.gn_done++;
+        }
+        DRV_TRY(objective_impl(p, Rl[l], Tl[l], u, dsc, dsc + 1));
+        double h[2];
+        DRV_CU(cudaMemcpyAsync(h, dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
+        DRV_CU(cudaStreamSynchronize(stream), "sync");
+        r.D = h[0];
+        r.S = h[1];
+        r.J = h[0] + d.alpha * h[1];
+    }
+    DRV_CU(cudaMemcpyAsync(u_out, u, n3 * sizeof(float), U_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           stream),
+           "copy u_out");
+    DRV_CU(cudaStreamSynchronize(stream), "sync");
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    if (rep) *rep = r;
+    return NGF_OK;
+}

@@ -1,0 +1,897 @@
+// Kernel bodies of libngf_b300 (declarations and shared-memory layouts are in
+// ngf_kernels.cuh).
+#include "ngf_kernels.cuh"
+
+namespace ngf {
+
+// position of ring element k of the (TX+2h) x (TY+2h) region minus the TX x TY core
+__device__ __forceinline__ void ring_coord(int k, int halo, int& lx, int& ly) {
+    const int W = TX + 2 * halo;
+    const int band = halo * W;
+    if (k < band) {
+        ly = -halo + k / W;
+        lx = -halo + k % W;
+    } else if (k < 2 * band) {
+        k -= band;
+        ly = TY + k / W;
+        lx = -halo + k % W;
+    } else {
+        k -= 2 * band;
+        const int per = 2 * halo;
+        ly = k / per;
+        const int c = k % per;
+        lx = (c < halo) ? (-halo + c) : (TX + c - halo);
+    }
+}
+
+// Block-wide float64 sum with a fixed tree order (all threads see the result).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    const int tid = threadIdx.x;
+    red[tid] = v;
+    __syncthreads();
+    for (int s = NT / 2; s > 0; s >>= 1) {
+        if (tid < s) red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    return red[0];
+}
+
+// Deterministic grid-wide float64 sum: each CTA stores its partial, the last
+// CTA to finish adds all partials in CTA order.  `scale` multiplies the result.
+__device__ __forceinline__ void grid_sum_finish(double blocksum, double* part, unsigned int* count,
+                                                double* out, double scale, double* red, int nblocks,
+                                                int bid) {
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        part[bid] = blocksum;
+        __threadfence();
+        const unsigned int ticket = atomicAdd(count, 1u);
+        is_last = (ticket == (unsigned int)(nblocks - 1));
+    }
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += ((volatile double*)part)[i];
+        red[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            *out = red[0] * scale;
+            *count = 0u;
+        }
+    }
+}
+
+// Trilinear sample of T at continuous voxel coordinate (g + d) per axis, zero
+// outside; returns the value and dT/dx_l in physical units.  The cell is
+// floor(d) relative to g (displacement form), so exact knots take the forward
+// cell and an identity warp reproduces T exactly.
+__device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy, int gz, float d0, float d1,
+                                             float d2, float& g0, float& g1, float& g2) {
+    g0 = g1 = g2 = 0.f;
+    if (!(fabsf(d0) < 1.0e9f) || !(fabsf(d1) < 1.0e9f) || !(fabsf(d2) < 1.0e9f)) return 0.f;
+    const float f0 = floorf(d0), f1 = floorf(d1), f2 = floorf(d2);
+    const int cx = gx + (int)f0, cy = gy + (int)f1, cz = gz + (int)f2;
+    if (cx < -1 || cx > P.m0 - 1 || cy < -1 || cy > P.m1 - 1 || cz < -1 || cz > P.m2 - 1) return 0.f;
+    const float tx = d0 - f0, ty = d1 - f1, tz = d2 - f2;
+    const bool x0ok = cx >= 0, x1ok = cx + 1 <= P.m0 - 1;
+    const bool y0ok = cy >= 0, y1ok = cy + 1 <= P.m1 - 1;
+    const bool z0ok = cz >= 0, z1ok = cz + 1 <= P.m2 - 1;
+    const long long sy = P.m0, sz = (long long)P.m0 * P.m1;
+    const long long b = (long long)cx + sy * cy + sz * cz;
+    const float* T = P.T;
+    const float v000 = (x0ok && y0ok && z0ok) ? __ldg(T + b) : 0.f;
+    const float v100 = (x1ok && y0ok && z0ok) ? __ldg(T + b + 1) : 0.f;
+    const float v010 = (x0ok && y1ok && z0ok) ? __ldg(T + b + sy) : 0.f;
+    const float v110 = (x1ok && y1ok && z0ok) ? __ldg(T + b + sy + 1) : 0.f;
+    const float v001 = (x0ok && y0ok && z1ok) ? __ldg(T + b + sz) : 0.f;
+    const float v101 = (x1ok && y0ok && z1ok) ? __ldg(T + b + sz + 1) : 0.f;
+    const float v011 = (x0ok && y1ok && z1ok) ? __ldg(T + b + sz + sy) : 0.f;
+    const float v111 = (x1ok && y1ok && z1ok) ? __ldg(T + b + sz + sy + 1) : 0.f;
+    // lerp along x on the four (y,z) edges
+    const float e00 = fmaf(tx, v100 - v000, v000);
+    const float e10 = fmaf(tx, v110 - v010, v010);
+    const float e01 = fmaf(tx, v101 - v001, v001);
+    const float e11 = fmaf(tx, v111 - v011, v011);
+    const float a0 = fmaf(ty, e10 - e00, e00);
+    const float a1 = fmaf(ty, e11 - e01, e01);
+    // x derivative: bilinear (y,z) blend of the x differences
+    const float q0 = fmaf(ty, (v110 - v010) - (v100 - v000), v100 - v000);
+    const float q1 = fmaf(ty, (v111 - v011) - (v101 - v001), v101 - v001);
+    g0 = fmaf(tz, q1 - q0, q0) * P.ih[0];
+    g1 = fmaf(tz, (e11 - e01) - (e10 - e00), e10 - e00) * P.ih[1];
+    g2 = (a1 - a0) * P.ih[2];
+    return fmaf(tz, a1 - a0, a0);
+}
+
+// ---------------------------------------------------------------------------
+// The fused image pass.
+//   MODE_OBJ : D = hbar sum (1 - r_i^2)                       (Eq. NGF_discretized)
+//   MODE_GRAD: D and the tile partials of P^T[dT (dr^T(-2 hbar r))]   (Eq. gradNGF)
+//   MODE_HESS: tile partials of P^T[2 hbar dT dr^T dr (dT . P p)]       (Eq. hessMult)
+// The transposed grid conversion is completed by k_node_combine.
+//
+// Pipeline per z-step zf (one __syncthreads between stages):
+//   stage 0: node values of u (and p) interpolated in z to plane zf;
+//   stage 1: warp T and dT (and s = dT . P p) on the front-end region of zf;
+//   stage 2: residual Jacobian row rho_hat (Eqs. rho, hatRho) on plane zf-1
+//            for the halo-1 region and the products pi_i(k) = rho_hat_i(k) w_i
+//            with w = r (gradient) or w = dr s (Hessian);
+//   stage 3: on plane zf-2, t_j = sum_k pi_{j+k}(-k) over true neighbours
+//            (column j of dr^T), q_hat = qscale dT_j t_j, and its P^T
+//            contribution accumulated into two live node planes.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ void image_pass(const ImgParams& P) {
+    NGF_DYNAMIC_SMEM(smraw);
+    ImgSmem& S = *reinterpret_cast<ImgSmem*>(smraw);
+    const int tid = threadIdx.x;
+    const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
+    const int z0 = blockIdx.z * P.zc, z1 = min(P.m2, z0 + P.zc);
+    const int txe = min(TX, P.m0 - xs), tye = min(TY, P.m1 - ys);
+    const int FH = (MODE == MODE_OBJ) ? 1 : 2;  // front-end halo
+
+    // node box of the front-end region (z-interpolated node planes)
+    const int UX0 = P.fx[max(xs - 2, 0)], UY0 = P.fy[max(ys - 2, 0)];
+    const int UXn = P.fx[min(xs + TX + 1, P.m0 - 1)] + 1 - UX0 + 1;
+    const int UYn = P.fy[min(ys + TY + 1, P.m1 - 1)] + 1 - UY0 + 1;
+    // node box of the owned columns (tile partials)
+    const int BX0 = P.fx[xs], BY0 = P.fy[ys], BZ0 = P.fz[z0];
+    const int nbx = P.fx[xs + txe - 1] + 1 - BX0 + 1;
+    const int nby = P.fy[ys + tye - 1] + 1 - BY0 + 1;
+    const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+
+    for (int i = tid; i < SX2; i += NT) {
+        const int gx = min(max(xs - 2 + i, 0), P.m0 - 1);
+        S.fx2[i] = P.fx[gx] - UX0;
+        S.wx2[i] = P.wx[gx];
+    }
+    for (int i = tid; i < SY2; i += NT) {
+        const int gy = min(max(ys - 2 + i, 0), P.m1 - 1);
+        S.fy2[i] = P.fy[gy] - UY0;
+        S.wy2[i] = P.wy[gy];
+    }
+    if (MODE != MODE_OBJ) {
+        for (int i = tid; i < TX; i += NT) S.fxb[i] = P.fx[min(xs + i, P.m0 - 1)] - BX0;
+        for (int i = tid; i < TY; i += NT) S.fyb[i] = P.fy[min(ys + i, P.m1 - 1)] - BY0;
+        for (int b = tid; b < nbx; b += NT) {
+            int lo = TX, hi = -1;
+            for (int lx = 0; lx < txe; ++lx) {
+                const int f = P.fx[xs + lx] - BX0;
+                if (f == b || f == b - 1) { lo = min(lo, lx); hi = max(hi, lx); }
+            }
+            S.xr_lo[b] = lo;
+            S.xr_hi[b] = hi;
+        }
+        for (int b = tid; b < nby; b += NT) {
+            int lo = TY, hi = -1;
+            for (int ly = 0; ly < tye; ++ly) {
+                const int f = P.fy[ys + ly] - BY0;
+                if (f == b || f == b - 1) { lo = min(lo, ly); hi = max(hi, ly); }
+            }
+            S.yr_lo[b] = lo;
+            S.yr_hi[b] = hi;
+        }
+        for (int i = tid; i < 2 * 3 * NBY * NBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
+    }
+    __syncthreads();
+
+    const int lx0 = tid % TX, ly0 = tid / TX;  // this thread's owned column
+    const bool own_ok = (lx0 < txe) && (ly0 < tye);
+    const int gx0 = xs + lx0, gy0 = ys + ly0;
+
+    // register queues of the owned column
+    float dq0[3] = {0.f, 0.f, 0.f}, dq1[3] = {0.f, 0.f, 0.f}, dq2[3] = {0.f, 0.f, 0.f};  // dT at zf, zf-1, zf-2
+    float pm_cur = 0.f, p0_cur = 0.f, pp_cur = 0.f;  // pi(-z), pi(0), pi(+z) of plane zq
+    float p0_last = 0.f, pp_last = 0.f, pp_last2 = 0.f;
+    double dacc = 0.0;
+    int cur = BZ0;  // lower live node plane of the P^T accumulators
+
+    const int nvec = (MODE == MODE_HESS) ? 6 : 3;
+    const int zbeg = z0 - FH, zend = (MODE == MODE_OBJ) ? z1 : z1 + 1;
+
+    for (int zf = zbeg; zf <= zend; ++zf) {
+        // ---- stage 0: node values interpolated in z to plane zf
+        const bool fe = (zf >= 0) && (zf < P.m2);
+        if (fe) {
+            const int fzz = P.fz[zf];
+            const float wzz = P.wz[zf];
+            const long long plane = (long long)P.n0 * P.n1;
+            const long long pl0 = (long long)fzz * plane;
+            const int box = UXn * UYn;
+            for (int i = tid; i < nvec * box; i += NT) {
+                const int c = i / box;
+                const int rem = i - c * box;
+                const int by = rem / UXn, bx = rem - by * UXn;
+                const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
+                const long long o = pl0 + (UX0 + bx) + (long long)P.n0 * (UY0 + by);
+                const float a = __ldg(src + o), b = __ldg(src + o + plane);
+                S.Uz[c][by][bx] = fmaf(wzz, b - a, a);
+            }
+        }
+        __syncthreads();
+        // ---- stage 1: warp (and s = dT . P p) on the front-end region of plane zf
+        dq2[0] = dq1[0]; dq2[1] = dq1[1]; dq2[2] = dq1[2];
+        dq1[0] = dq0[0]; dq1[1] = dq0[1]; dq1[2] = dq0[2];
+        dq0[0] = dq0[1] = dq0[2] = 0.f;
+        if (fe) {
+            const int slot = zf % 3;
+            const int nring = ring_size(FH);
+            for (int k = tid; k < NT + nring; k += NT) {
+                int lx, ly;
+                if (k < NT) { lx = k % TX; ly = k / TX; }
+                else ring_coord(k - NT, FH, lx, ly);
+                const int gx = xs + lx, gy = ys + ly;
+                if (gx < 0 || gx >= P.m0 || gy < 0 || gy >= P.m1) continue;
+                const int li = (ly + 2) * SX2 + (lx + 2);
+                const int ax = S.fx2[lx + 2], ay = S.fy2[ly + 2];
+                const float wxv = S.wx2[lx + 2], wyv = S.wy2[ly + 2];
+                float uh[6];
+                for (int c = 0; c < nvec; ++c) {
+                    const float v00 = S.Uz[c][ay][ax], v10 = S.Uz[c][ay][ax + 1];
+                    const float v01 = S.Uz[c][ay + 1][ax], v11 = S.Uz[c][ay + 1][ax + 1];
+                    const float a0 = fmaf(wxv, v10 - v00, v00), a1 = fmaf(wxv, v11 - v01, v01);
+                    uh[c] = fmaf(wyv, a1 - a0, a0);
+                }
+                float g0, g1, g2;
+                const float tw = warp_sample(P, gx, gy, zf, uh[0] * P.ih[0], uh[1] * P.ih[1], uh[2] * P.ih[2],
+                                             g0, g1, g2);
+                const long long gi = (long long)gx + (long long)P.m0 * (gy + (long long)P.m1 * zf);
+                S.R[slot][li] = __ldg(P.R + gi);
+                S.Tw[slot][li] = tw;
+                if (MODE == MODE_HESS) S.S[slot][li] = fmaf(g0, uh[3], fmaf(g1, uh[4], g2 * uh[5]));
+                if (k < NT) { dq0[0] = g0; dq0[1] = g1; dq0[2] = g2; }
+            }
+        }
+        __syncthreads();
+        // ---- stage 2: residual Jacobian rows on plane zq = zf - 1
+        const int zq = zf - 1;
+        const bool st2 = (zq >= 0) && (zq < P.m2) &&
+                         ((MODE == MODE_OBJ) ? (zq >= z0 && zq < z1) : (zq >= z0 - 1 && zq <= z1));
+        pm_cur = p0_cur = pp_cur = 0.f;
+        if (st2) {
+            const int sc = zq % 3;
+            const int szm = (zq > 0 ? zq - 1 : zq) % 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) % 3;
+            const int nring = (MODE == MODE_OBJ) ? 0 : ring_size(1);
+            for (int k = tid; k < NT + nring; k += NT) {
+                int lx, ly;
+                if (k < NT) { lx = k % TX; ly = k / TX; }
+                else ring_coord(k - NT, 1, lx, ly);
+                const int gx = xs + lx, gy = ys + ly;
+                if (gx < 0 || gx >= P.m0 || gy < 0 || gy >= P.m1) continue;
+                const int li = (ly + 2) * SX2 + (lx + 2);
+                // clamped neighbours (Eq. boundary_conditions), K order -z,-y,-x,+x,+y,+z
+                const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
+                const int ym = (gy > 0) ? li - SX2 : li, yp = (gy < P.m1 - 1) ? li + SX2 : li;
+                const float r0 = S.R[sc][li], t0 = S.Tw[sc][li];
+                const float dR[6] = {S.R[szm][li] - r0, S.R[sc][ym] - r0, S.R[sc][xm] - r0,
+                                     S.R[sc][xp] - r0, S.R[sc][yp] - r0, S.R[szp][li] - r0};
+                const float dT[6] = {S.Tw[szm][li] - t0, S.Tw[sc][ym] - t0, S.Tw[sc][xm] - t0,
+                                     S.Tw[sc][xp] - t0, S.Tw[sc][yp] - t0, S.Tw[szp][li] - t0};
+                const float ihs[6] = {P.ihs[2], P.ihs[1], P.ihs[0], P.ihs[0], P.ihs[1], P.ihs[2]};
+                float nn = 0.f, a2 = 0.f, b2 = 0.f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    nn = fmaf(dT[j] * dR[j], ihs[j], nn);
+                    a2 = fmaf(dT[j] * dT[j], ihs[j], a2);
+                    b2 = fmaf(dR[j] * dR[j], ihs[j], b2);
+                }
+                nn = fmaf(0.5f, nn, P.tr);   // N   = 1/2 <grad T, grad R> + tau rho
+                a2 = fmaf(0.5f, a2, P.tau2); // A^2 = ||grad T||_tau^2
+                b2 = fmaf(0.5f, b2, P.rho2); // B^2 = ||grad R||_rho^2
+                const float c1 = rsqrtf(a2 * b2);  // 1/(A B)
+                if (MODE != MODE_HESS && k < NT && zq >= z0 && zq < z1) {
+                    // 1 - r^2 = (A^2 B^2 - N^2)/(A^2 B^2), numerator by the Lagrange identity
+                    float a[6], b[6];
+                    const float ih6[6] = {P.ih[2], P.ih[1], P.ih[0], P.ih[0], P.ih[1], P.ih[2]};
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) { a[j] = dT[j] * ih6[j]; b[j] = dR[j] * ih6[j]; }
+                    float cross = 0.f, sq = 0.f;
+#pragma unroll
+                    for (int pj = 0; pj < 6; ++pj) {
+#pragma unroll
+                        for (int qj = pj + 1; qj < 6; ++qj) {
+                            const float t = fmaf(a[pj], b[qj], -a[qj] * b[pj]);
+                            cross = fmaf(t, t, cross);
+                        }
+                        const float t = fmaf(P.rho, a[pj], -P.tau * b[pj]);
+                        sq = fmaf(t, t, sq);
+                    }
+                    dacc += (double)(fmaf(0.25f, cross, 0.5f * sq) / (a2 * b2));
+                }
+                if (MODE == MODE_OBJ) continue;
+                const float c2 = nn * c1 / a2;     // N/(A^3 B)
+                const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
+                float rh[6], rs = 0.f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {       // Eqs. (rho), (hatRho)
+                    rh[j] = hh[j] * fmaf(dR[j], c1, -dT[j] * c2);
+                    rs += rh[j];
+                }
+                const float rh0 = -rs;
+                float w;
+                if (MODE == MODE_GRAD) {
+                    w = nn * c1;  // r_i
+                } else {          // v_i = (dr s)_i
+                    const float s0 = S.S[sc][li];
+                    const float sn[6] = {S.S[szm][li], S.S[sc][ym], S.S[sc][xm], S.S[sc][xp], S.S[sc][yp],
+                                         S.S[szp][li]};
+                    w = rh0 * s0;
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) w = fmaf(rh[j], sn[j], w);
+                }
+                const int l1 = (ly + 1) * SX1 + (lx + 1);
+                const int pb = zq & 1;
+                S.Pi[pb][0][l1] = rh[2] * w;  // pi(-x)
+                S.Pi[pb][1][l1] = rh[3] * w;  // pi(+x)
+                S.Pi[pb][2][l1] = rh[1] * w;  // pi(-y)
+                S.Pi[pb][3][l1] = rh[4] * w;  // pi(+y)
+                if (k < NT) { pm_cur = rh[0] * w; p0_cur = rh0 * w; pp_cur = rh[5] * w; }
+            }
+        }
+        if (MODE == MODE_OBJ) continue;
+        __syncthreads();
+        // ---- stage 3: column sums of dr^T (masked to true neighbours), q_hat, P^T
+        const int zo = zf - 2;
+        if (zo >= z0 && zo < z1) {
+            float t = 0.f;
+            if (own_ok) {
+                const int l1 = (ly0 + 1) * SX1 + (lx0 + 1);
+                const int pb = zo & 1;
+                t = p0_last;
+                if (gx0 > 0) t += S.Pi[pb][1][l1 - 1];
+                if (gx0 < P.m0 - 1) t += S.Pi[pb][0][l1 + 1];
+                if (gy0 > 0) t += S.Pi[pb][3][l1 - SX1];
+                if (gy0 < P.m1 - 1) t += S.Pi[pb][2][l1 + SX1];
+                if (zo > 0) t += pp_last2;
+                if (zo < P.m2 - 1) t += pm_cur;
+                t *= P.qscale;
+            }
+            S.Q[0][tid] = own_ok ? dq2[0] * t : 0.f;
+            S.Q[1][tid] = own_ok ? dq2[1] * t : 0.f;
+            S.Q[2][tid] = own_ok ? dq2[2] * t : 0.f;
+            __syncthreads();
+            const int fzo = P.fz[zo] - BZ0;
+            const float wzo = P.wz[zo];
+            const int items = 3 * nby * nbx;
+            if (fzo + BZ0 > cur) {  // node plane `cur` is complete: store its partial
+                for (int i = tid; i < items; i += NT) {
+                    const int c = i / (nby * nbx), rem = i % (nby * nbx), by = rem / nbx, bx = rem % nbx;
+                    float& a = S.Acc[cur & 1][c][by][bx];
+                    P.partial[((tile * 3 + c) * P.pbz + (cur - BZ0)) * (long long)(P.pby * P.pbx) + by * P.pbx + bx] = a;
+                    a = 0.f;
+                }
+                cur = fzo + BZ0;
+            }
+            for (int i = tid; i < items; i += NT) {
+                const int c = i / (nby * nbx), rem = i % (nby * nbx), by = rem / nbx, bx = rem % nbx;
+                float qv = 0.f;
+                for (int ly = S.yr_lo[by]; ly <= S.yr_hi[by]; ++ly) {
+                    const float wyl = S.wy2[ly + 2];
+                    const float wy = (S.fyb[ly] == by) ? 1.f - wyl : wyl;
+                    float row = 0.f;
+                    for (int lx = S.xr_lo[bx]; lx <= S.xr_hi[bx]; ++lx) {
+                        const float wxl = S.wx2[lx + 2];
+                        const float wx = (S.fxb[lx] == bx) ? 1.f - wxl : wxl;
+                        row = fmaf(wx, S.Q[c][ly * TX + lx], row);
+                    }
+                    qv = fmaf(wy, row, qv);
+                }
+                S.Acc[cur & 1][c][by][bx] = fmaf(1.f - wzo, qv, S.Acc[cur & 1][c][by][bx]);
+                S.Acc[(cur + 1) & 1][c][by][bx] = fmaf(wzo, qv, S.Acc[(cur + 1) & 1][c][by][bx]);
+            }
+        }
+        // advance the z queues of pi
+        pp_last2 = pp_last;
+        pp_last = pp_cur;
+        p0_last = p0_cur;
+    }
+
+    if (MODE != MODE_OBJ) {
+        // store the two live node planes
+        const int items = 3 * nby * nbx;
+        for (int pl = cur; pl <= cur + 1; ++pl) {
+            for (int i = tid; i < items; i += NT) {
+                const int c = i / (nby * nbx), rem = i % (nby * nbx), by = rem / nbx, bx = rem % nbx;
+                P.partial[((tile * 3 + c) * P.pbz + (pl - BZ0)) * (long long)(P.pby * P.pbx) + by * P.pbx + bx] =
+                    S.Acc[pl & 1][c][by][bx];
+            }
+        }
+    }
+    if (MODE != MODE_HESS) {
+        __syncthreads();
+        const double bs = block_sum(dacc, S.red);
+        const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+        grid_sum_finish(bs, P.dpart, P.dcount, P.dout, P.hbar, S.red, nblocks, (int)tile);
+    }
+}
+
+__global__ void __launch_bounds__(NT, 2) k_image_obj(const ImgParams P) { image_pass<MODE_OBJ>(P); }
+__global__ void __launch_bounds__(NT, 2) k_image_grad(const ImgParams P) { image_pass<MODE_GRAD>(P); }
+__global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) { image_pass<MODE_HESS>(P); }
+
+// ---------------------------------------------------------------------------
+// Exact Jacobi diagonal of the Gauss-Newton matrix (without the curvature
+// part): diag_{d,n} = 2 hbar sum_i J_{i,(d,n)}^2, J = dr dT P, row i formed
+// from the 7 entries of row i of dr (Eq. dr) and the trilinear weights of each
+// entry's voxel, using the separable structure of P:
+//   J(a,b,g) = ez ey ax + ez by ex + cz ey ex
+// with e* the weights of voxel i itself and ax/by/cz the coefficient-weighted
+// weights of its x/y/z stencil entries.  Rows of the owned columns scatter
+// their squared entries into shared node-plane accumulators (4 live planes),
+// which are stored as tile partials of the halo-1 geometry.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float pw_weight(int f, float w1, int node) {
+    return (node == f) ? 1.f - w1 : ((node == f + 1) ? w1 : 0.f);
+}
+
+__global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) {
+    NGF_DYNAMIC_SMEM(smraw);
+    DiagSmem& S = *reinterpret_cast<DiagSmem*>(smraw);
+    const int tid = threadIdx.x;
+    const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
+    const int z0 = blockIdx.z * P.zc, z1 = min(P.m2, z0 + P.zc);
+    const int txe = min(TX, P.m0 - xs), tye = min(TY, P.m1 - ys);
+    const int UX0 = P.fx[max(xs - 1, 0)], UY0 = P.fy[max(ys - 1, 0)];
+    const int UXn = P.fx[min(xs + TX, P.m0 - 1)] + 1 - UX0 + 1;
+    const int UYn = P.fy[min(ys + TY, P.m1 - 1)] + 1 - UY0 + 1;
+    // the partial box of the halo-1 geometry equals the Uz box in x and y
+    const int BZ0 = P.fz[max(z0 - 1, 0)], BZ1 = P.fz[min(z1, P.m2 - 1)] + 1;
+    const int nbx = UXn, nby = UYn;
+    const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+
+    for (int i = tid; i < SX1; i += NT) {
+        const int gx = min(max(xs - 1 + i, 0), P.m0 - 1);
+        S.fx1[i] = P.fx[gx] - UX0;
+        S.wx1[i] = P.wx[gx];
+    }
+    for (int i = tid; i < SY1; i += NT) {
+        const int gy = min(max(ys - 1 + i, 0), P.m1 - 1);
+        S.fy1[i] = P.fy[gy] - UY0;
+        S.wy1[i] = P.wy[gy];
+    }
+    for (int i = tid; i < 4 * 3 * DBY * DBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
+    __syncthreads();
+
+    const int items = 3 * nby * nbx;
+    int next = BZ0;  // next node plane to store
+    const float twoh = (float)(2.0 * P.hbar);
+
+    for (int zf = z0 - 1; zf <= z1; ++zf) {
+        const bool fe = (zf >= 0) && (zf < P.m2);
+        if (fe) {
+            const int fzz = P.fz[zf];
+            const float wzz = P.wz[zf];
+            const long long plane = (long long)P.n0 * P.n1;
+            const long long pl0 = (long long)fzz * plane;
+            const int box = UXn * UYn;
+            for (int i = tid; i < 3 * box; i += NT) {
+                const int c = i / box;
+                const int rem = i - c * box;
+                const int by = rem / UXn, bx = rem - by * UXn;
+                const float* src = P.u + c * P.N;
+                const long long o = pl0 + (UX0 + bx) + (long long)P.n0 * (UY0 + by);
+                const float a = __ldg(src + o), b = __ldg(src + o + plane);
+                S.Uz[c][by][bx] = fmaf(wzz, b - a, a);
+            }
+        }
+        __syncthreads();
+        if (fe) {
+            const int slot = zf % 3;
+            for (int k = tid; k < NT + ring_size(1); k += NT) {
+                int lx, ly;
+                if (k < NT) { lx = k % TX; ly = k / TX; }
+                else ring_coord(k - NT, 1, lx, ly);
+                const int gx = xs + lx, gy = ys + ly;
+                if (gx < 0 || gx >= P.m0 || gy < 0 || gy >= P.m1) continue;
+                const int li = (ly + 1) * SX1 + (lx + 1);
+                const int ax = S.fx1[lx + 1], ay = S.fy1[ly + 1];
+                const float wxv = S.wx1[lx + 1], wyv = S.wy1[ly + 1];
+                float uh[3];
+                for (int c = 0; c < 3; ++c) {
+                    const float v00 = S.Uz[c][ay][ax], v10 = S.Uz[c][ay][ax + 1];
+                    const float v01 = S.Uz[c][ay + 1][ax], v11 = S.Uz[c][ay + 1][ax + 1];
+                    const float a0 = fmaf(wxv, v10 - v00, v00), a1 = fmaf(wxv, v11 - v01, v01);
+                    uh[c] = fmaf(wyv, a1 - a0, a0);
+                }
+                float g0, g1, g2;
+                const float tw = warp_sample(P, gx, gy, zf, uh[0] * P.ih[0], uh[1] * P.ih[1], uh[2] * P.ih[2],
+                                             g0, g1, g2);
+                const long long gi = (long long)gx + (long long)P.m0 * (gy + (long long)P.m1 * zf);
+                S.R[slot][li] = __ldg(P.R + gi);
+                S.Tw[slot][li] = tw;
+                S.dT[slot][0][li] = g0;
+                S.dT[slot][1][li] = g1;
+                S.dT[slot][2][li] = g2;
+            }
+        }
+        __syncthreads();
+        const int zq = zf - 1;
+        if (zq >= z0 && zq < z1) {
+            const int lx = tid % TX, ly = tid / TX;
+            if (lx < txe && ly < tye) {
+                const int gx = xs + lx, gy = ys + ly;
+                const int sc = zq % 3;
+                const int szm = (zq > 0 ? zq - 1 : zq) % 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) % 3;
+                const int li = (ly + 1) * SX1 + (lx + 1);
+                const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
+                const int ym = (gy > 0) ? li - SX1 : li, yp = (gy < P.m1 - 1) ? li + SX1 : li;
+                const float r0 = S.R[sc][li], t0 = S.Tw[sc][li];
+                const float dR[6] = {S.R[szm][li] - r0, S.R[sc][ym] - r0, S.R[sc][xm] - r0,
+                                     S.R[sc][xp] - r0, S.R[sc][yp] - r0, S.R[szp][li] - r0};
+                const float dTv[6] = {S.Tw[szm][li] - t0, S.Tw[sc][ym] - t0, S.Tw[sc][xm] - t0,
+                                      S.Tw[sc][xp] - t0, S.Tw[sc][yp] - t0, S.Tw[szp][li] - t0};
+                const float ihs[6] = {P.ihs[2], P.ihs[1], P.ihs[0], P.ihs[0], P.ihs[1], P.ihs[2]};
+                float nn = 0.f, a2 = 0.f, b2 = 0.f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    nn = fmaf(dTv[j] * dR[j], ihs[j], nn);
+                    a2 = fmaf(dTv[j] * dTv[j], ihs[j], a2);
+                    b2 = fmaf(dR[j] * dR[j], ihs[j], b2);
+                }
+                nn = fmaf(0.5f, nn, P.tr);
+                a2 = fmaf(0.5f, a2, P.tau2);
+                b2 = fmaf(0.5f, b2, P.rho2);
+                const float c1 = rsqrtf(a2 * b2);
+                const float c2 = nn * c1 / a2;
+                const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
+                float rh[6], rs = 0.f;
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    rh[j] = hh[j] * fmaf(dR[j], c1, -dTv[j] * c2);
+                    rs += rh[j];
+                }
+                const float rh0 = -rs;
+                // node floors and weights of the stencil entries' voxels (clamped)
+                const int vzm = max(zq - 1, 0), vzp = min(zq + 1, P.m2 - 1);
+                const int fxm = S.fx1[lx], fxc = S.fx1[lx + 1], fxp = S.fx1[lx + 2];
+                const float wxm = S.wx1[lx], wxc = S.wx1[lx + 1], wxp = S.wx1[lx + 2];
+                const int fym = S.fy1[ly], fyc = S.fy1[ly + 1], fyp = S.fy1[ly + 2];
+                const float wym = S.wy1[ly], wyc = S.wy1[ly + 1], wyp = S.wy1[ly + 2];
+                const int fzm = P.fz[vzm] - BZ0, fzc = P.fz[zq] - BZ0, fzp = P.fz[vzp] - BZ0;
+                const float wzm = P.wz[vzm], wzc = P.wz[zq], wzp = P.wz[vzp];
+                const int bxm = fxm, bym = fym, bzm = fzm;  // lowest node touched per axis
+#pragma unroll 1
+                for (int d = 0; d < 3; ++d) {
+                    const float* dTd[3] = {S.dT[szm][d], S.dT[sc][d], S.dT[szp][d]};
+                    const float cc = rh0 * dTd[1][li];
+                    const float cxm = rh[2] * dTd[1][xm], cxp = rh[3] * dTd[1][xp];
+                    const float cym = rh[1] * dTd[1][ym], cyp = rh[4] * dTd[1][yp];
+                    const float czm = rh[0] * dTd[0][li], czp = rh[5] * dTd[2][li];
+                    float ax[4], ex[4], by[4], ey[4], cz[4], ez[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int nxl = bxm + a, nyl = bym + a, nzl = bzm + a;
+                        ex[a] = pw_weight(fxc, wxc, nxl);
+                        ax[a] = cc * ex[a] + cxm * pw_weight(fxm, wxm, nxl) + cxp * pw_weight(fxp, wxp, nxl);
+                        ey[a] = pw_weight(fyc, wyc, nyl);
+                        by[a] = cym * pw_weight(fym, wym, nyl) + cyp * pw_weight(fyp, wyp, nyl);
+                        ez[a] = pw_weight(fzc, wzc, nzl);
+                        cz[a] = czm * pw_weight(fzm, wzm, nzl) + czp * pw_weight(fzp, wzp, nzl);
+                    }
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                        for (int a = 0; a < 4; ++a) {
+                            const float xy1 = fmaf(ey[b], ax[a], by[b] * ex[a]);
+                            const float xy2 = ey[b] * ex[a];
+                            if (xy1 == 0.f && xy2 == 0.f) continue;
+                            const int bxl = bxm + a, byl = bym + b;
+                            if (bxl >= nbx || byl >= nby) continue;
+#pragma unroll
+                            for (int g = 0; g < 4; ++g) {
+                                const float J = fmaf(ez[g], xy1, cz[g] * xy2);
+                                if (J == 0.f) continue;
+                                const int bzl = bzm + g;
+                                atomicAdd(&S.Acc[(bzl + BZ0) & 3][d][byl][bxl], twoh * J * J);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // node planes below fz[zq] receive nothing more from this chunk
+        if (zq >= z0 && zq < z1) {
+            const int limit = (zq == z1 - 1) ? BZ1 + 1 : P.fz[zq];
+            while (next < limit) {
+                for (int i = tid; i < items; i += NT) {
+                    const int c = i / (nby * nbx), rem = i % (nby * nbx), byy = rem / nbx, bxx = rem % nbx;
+                    float& a = S.Acc[next & 3][c][byy][bxx];
+                    P.partial[((tile * 3 + c) * P.pbz + (next - BZ0)) * (long long)(P.pby * P.pbx) + byy * P.pbx + bxx] = a;
+                    a = 0.f;
+                }
+                ++next;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// nodal kernels
+// ---------------------------------------------------------------------------
+
+// L = Lap x per component (Eq. laplace_discretized, clamped Neumann
+// neighbours); optional S = scale * sum L^2 (deterministic float64).
+__global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L,
+                                            double* part, unsigned int* count, double* out, double scale) {
+    __shared__ double red[NT];
+    double acc = 0.0;
+    const long long total = 3 * G.N;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
+        const long long c = i / G.N, n = i - c * G.N;
+        const int ix = (int)(n % G.n0), iy = (int)((n / G.n0) % G.n1), iz = (int)(n / ((long long)G.n0 * G.n1));
+        const float* xc = x + c * G.N;
+        const float v = xc[n];
+        const long long sy = G.n0, sz = (long long)G.n0 * G.n1;
+        const float xm = xc[ix > 0 ? n - 1 : n], xp = xc[ix < G.n0 - 1 ? n + 1 : n];
+        const float ym = xc[iy > 0 ? n - sy : n], yp = xc[iy < G.n1 - 1 ? n + sy : n];
+        const float zm = xc[iz > 0 ? n - sz : n], zp = xc[iz < G.n2 - 1 ? n + sz : n];
+        const float l = (xm - 2.f * v + xp) * G.ihy2[0] + (ym - 2.f * v + yp) * G.ihy2[1] + (zm - 2.f * v + zp) * G.ihy2[2];
+        L[i] = l;
+        acc += (double)l * (double)l;
+    }
+    if (out) {
+        const double bs = block_sum(acc, red);
+        grid_sum_finish(bs, part, count, out, scale, red, gridDim.x, blockIdx.x);
+    }
+}
+
+// out_{c,n} = sum of the tile partials containing node n (fixed order)
+//           + alpha 2 hbar^y (Lap L)_{c,n}   or   + alpha 2 hbar^y cdiag_n
+__global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
+    __shared__ double red[NT];
+    double acc = 0.0;
+    const NodeGeom& G = P.G;
+    const long long total = 3 * G.N;
+    const long long box = (long long)P.pbx * P.pby * P.pbz;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
+        const long long c = i / G.N, n = i - c * G.N;
+        const int ix = (int)(n % G.n0), iy = (int)((n / G.n0) % G.n1), iz = (int)(n / ((long long)G.n0 * G.n1));
+        float s = 0.f;
+        for (int tz = P.zlo[iz]; tz <= P.zhi[iz]; ++tz) {
+            const int bz = iz - P.zb0[tz];
+            for (int ty = P.ylo[iy]; ty <= P.yhi[iy]; ++ty) {
+                const int by = iy - P.yb0[ty];
+                for (int tx = P.xlo[ix]; tx <= P.xhi[ix]; ++tx) {
+                    const int bx = ix - P.xb0[tx];
+                    const long long t = ((long long)tz * P.nty + ty) * P.ntx + tx;
+                    s += __ldg(P.partial + (t * 3 + c) * box + ((long long)bz * P.pby + by) * P.pbx + bx);
+                }
+            }
+        }
+        if (P.L) {
+            const float* Lc = P.L + c * G.N;
+            const long long sy = G.n0, sz = (long long)G.n0 * G.n1;
+            const float v = Lc[n];
+            const float xm = Lc[ix > 0 ? n - 1 : n], xp = Lc[ix < G.n0 - 1 ? n + 1 : n];
+            const float ym = Lc[iy > 0 ? n - sy : n], yp = Lc[iy < G.n1 - 1 ? n + sy : n];
+            const float zm = Lc[iz > 0 ? n - sz : n], zp = Lc[iz < G.n2 - 1 ? n + sz : n];
+            const float l2 = (xm - 2.f * v + xp) * G.ihy2[0] + (ym - 2.f * v + yp) * G.ihy2[1] +
+                             (zm - 2.f * v + zp) * G.ihy2[2];
+            s = fmaf(P.cscale, l2, s);
+        }
+        if (P.cdiag) s = fmaf(P.cscale, P.cdiag[n], s);
+        P.out[i] = s;
+        if (P.dotw) acc += (double)s * (double)P.dotw[i];
+    }
+    if (P.dout) {
+        const double bs = block_sum(acc, red);
+        grid_sum_finish(bs, P.dpart, P.dcount, P.dout, 1.0, red, gridDim.x, blockIdx.x);
+    }
+}
+
+// q = scale * Lap(L) with L = Lap p, no partials (curvature_apply)
+__global__ void __launch_bounds__(NT) k_lap2(NodeGeom G, const float* __restrict__ L, float* __restrict__ q,
+                                             float scale) {
+    const long long total = 3 * G.N;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
+        const long long c = i / G.N, n = i - c * G.N;
+        const int ix = (int)(n % G.n0), iy = (int)((n / G.n0) % G.n1), iz = (int)(n / ((long long)G.n0 * G.n1));
+        const float* Lc = L + c * G.N;
+        const long long sy = G.n0, sz = (long long)G.n0 * G.n1;
+        const float v = Lc[n];
+        const float xm = Lc[ix > 0 ? n - 1 : n], xp = Lc[ix < G.n0 - 1 ? n + 1 : n];
+        const float ym = Lc[iy > 0 ? n - sy : n], yp = Lc[iy < G.n1 - 1 ? n + sy : n];
+        const float zm = Lc[iz > 0 ? n - sz : n], zp = Lc[iz < G.n2 - 1 ? n + sz : n];
+        q[i] = scale * ((xm - 2.f * v + xp) * G.ihy2[0] + (ym - 2.f * v + yp) * G.ihy2[1] + (zm - 2.f * v + zp) * G.ihy2[2]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PCG (Sec. 2.3.1)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float minv(const float* diag, long long i) {
+    const float dv = diag[i];
+    return dv > 0.f ? 1.f / dv : 0.f;
+}
+
+// two deterministic float64 sums (e.g. r.z and r.r) finished by the last CTA;
+// returns true in thread 0 of the last CTA, with A and B set there
+__device__ __forceinline__ bool grid_sum2(double a, double b, double* part, unsigned int* count, double* red,
+                                          double& A, double& B) {
+    __shared__ int is_last;
+    const double sa = block_sum(a, red);
+    __syncthreads();
+    const double sb = block_sum(b, red);
+    const int nb = gridDim.x;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sa;
+        part[nb + blockIdx.x] = sb;
+        __threadfence();
+        is_last = (atomicAdd(count, 1u) == (unsigned int)(nb - 1));
+    }
+    __syncthreads();
+    if (!is_last) return false;
+    __threadfence();
+    double x = 0.0, y = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        x += ((volatile double*)part)[i];
+        y += ((volatile double*)part)[nb + i];
+    }
+    A = block_sum(x, red);
+    __syncthreads();
+    B = block_sum(y, red);
+    if (threadIdx.x == 0) *count = 0u;
+    return threadIdx.x == 0;
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_init(PcgParams P) {
+    __shared__ double red[NT];
+    double a = 0.0, b = 0.0;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < P.n; i += (long long)gridDim.x * NT) {
+        const float rv = P.rhs[i];
+        const float zv = rv * minv(P.diag, i);
+        P.x[i] = 0.f;
+        P.r[i] = rv;
+        P.z[i] = zv;
+        P.d[i] = zv;
+        a += (double)rv * (double)zv;
+        b += (double)rv * (double)rv;
+    }
+    double A, B;
+    if (grid_sum2(a, b, P.part, P.count, red, A, B)) {
+        P.sc[PS_DELTA] = A;
+        P.sc[PS_RR] = B;
+        P.sc[PS_BB] = B;
+        P.sc[PS_DQ] = 0.0;
+        P.sc[PS_ALPHA] = 0.0;
+        P.sc[PS_BETA] = 0.0;
+        P.sc[PS_ITERS] = 0.0;
+        double st = 0.0;
+        if (A == 0.0) st = 1.0;
+        else if (P.rtol > 0.0 && sqrt(B) <= P.rtol * sqrt(B)) st = 3.0;
+        P.sc[PS_STATUS] = st;
+    }
+}
+
+// after q = A d and sc[PS_DQ] = d.q: x += a d, r -= a q, z = M^-1 r, new delta
+__global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
+    __shared__ double red[NT];
+    const double st = P.sc[PS_STATUS];
+    const double dq = P.sc[PS_DQ];
+    const double delta = P.sc[PS_DELTA];
+    const bool active = (st == 0.0) && (dq > 0.0) && isfinite(dq);
+    const float a = active ? (float)(delta / dq) : 0.f;
+    double sa = 0.0, sb = 0.0;
+    if (active) {
+        for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < P.n; i += (long long)gridDim.x * NT) {
+            const float dv = P.d[i];
+            P.x[i] = fmaf(a, dv, P.x[i]);
+            const float rv = fmaf(-a, P.q[i], P.r[i]);
+            P.r[i] = rv;
+            const float zv = rv * minv(P.diag, i);
+            P.z[i] = zv;
+            sa += (double)rv * (double)zv;
+            sb += (double)rv * (double)rv;
+        }
+    }
+    double A, B;
+    if (grid_sum2(sa, sb, P.part, P.count, red, A, B)) {
+        if (st != 0.0) return;
+        if (!active) {
+            P.sc[PS_STATUS] = 2.0;
+            return;
+        }
+        P.sc[PS_ALPHA] = delta / dq;
+        P.sc[PS_BETA] = A / delta;
+        P.sc[PS_DELTA] = A;
+        P.sc[PS_RR] = B;
+        P.sc[PS_ITERS] += 1.0;
+        if (A == 0.0) P.sc[PS_STATUS] = 1.0;
+        else if (P.rtol > 0.0 && sqrt(B) <= P.rtol * sqrt(P.sc[PS_BB])) P.sc[PS_STATUS] = 3.0;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) {
+    if (P.sc[PS_STATUS] != 0.0) return;
+    const float beta = (float)P.sc[PS_BETA];
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < P.n; i += (long long)gridDim.x * NT)
+        P.d[i] = fmaf(beta, P.d[i], P.z[i]);
+}
+
+// ---------------------------------------------------------------------------
+// small vector kernels and multilevel helpers
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_dot(long long n, const float* __restrict__ a, const float* __restrict__ b,
+                                            double* part, unsigned int* count, double* out) {
+    __shared__ double red[NT];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
+        acc += (double)a[i] * (double)b[i];
+    const double bs = block_sum(acc, red);
+    grid_sum_finish(bs, part, count, out, 1.0, red, gridDim.x, blockIdx.x);
+}
+
+// y = x + eta * s (eta as float)
+__global__ void __launch_bounds__(NT) k_axpy(long long n, float eta, const float* __restrict__ x,
+                                             const float* __restrict__ s, float* __restrict__ y) {
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
+        y[i] = fmaf(eta, s[i], x[i]);
+}
+
+__global__ void __launch_bounds__(NT) k_scale(long long n, float a, const float* __restrict__ x, float* __restrict__ y) {
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT) y[i] = a * x[i];
+}
+
+// count of non-finite values (float64 so the deterministic sum can be reused)
+__global__ void __launch_bounds__(NT) k_nonfinite(long long n, const float* __restrict__ a, double* part,
+                                                  unsigned int* count, double* out) {
+    __shared__ double red[NT];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
+        acc += isfinite(a[i]) ? 0.0 : 1.0;
+    const double bs = block_sum(acc, red);
+    grid_sum_finish(bs, part, count, out, 1.0, red, gridDim.x, blockIdx.x);
+}
+
+// image pyramid: coarse cell = mean of its existing children (<= 8)
+__global__ void __launch_bounds__(NT) k_restrict(int m0, int m1, int m2, const float* __restrict__ img,
+                                                 float* __restrict__ out) {
+    const int c0 = (m0 + 1) / 2, c1 = (m1 + 1) / 2, c2 = (m2 + 1) / 2;
+    const long long total = (long long)c0 * c1 * c2;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
+        const int x = (int)(i % c0), y = (int)((i / c0) % c1), z = (int)(i / ((long long)c0 * c1));
+        float s = 0.f;
+        int cnt = 0;
+        for (int c = 0; c < 2; ++c)
+            for (int b = 0; b < 2; ++b)
+                for (int a = 0; a < 2; ++a) {
+                    const int fx = 2 * x + a, fy = 2 * y + b, fz = 2 * z + c;
+                    if (fx >= m0 || fy >= m1 || fz >= m2) continue;
+                    s += img[fx + (long long)m0 * (fy + (long long)m1 * fz)];
+                    ++cnt;
+                }
+        out[i] = s / (float)cnt;
+    }
+}
+
+// trilinear prolongation between node grids over the same domain; per-axis
+// tables (floor, weight) are built on the host
+__global__ void __launch_bounds__(NT) k_prolong(int f0, int f1, int f2, int c0, int c1, long long Nc,
+                                                const int* __restrict__ tf, const float* __restrict__ tw,
+                                                const float* __restrict__ uc, float* __restrict__ uf) {
+    const long long Nf = (long long)f0 * f1 * f2;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < 3 * Nf; i += (long long)gridDim.x * NT) {
+        const long long d = i / Nf, n = i - d * Nf;
+        const int x = (int)(n % f0), y = (int)((n / f0) % f1), z = (int)(n / ((long long)f0 * f1));
+        const int bx = tf[x], by = tf[f0 + y], bz = tf[f0 + f1 + z];
+        const float wx = tw[x], wy = tw[f0 + y], wz = tw[f0 + f1 + z];
+        const float* u = uc + d * Nc;
+        const long long o = bx + (long long)c0 * (by + (long long)c1 * bz);
+        const long long sy = c0, sz = (long long)c0 * c1;
+        const float e00 = fmaf(wx, u[o + 1] - u[o], u[o]);
+        const float e10 = fmaf(wx, u[o + sy + 1] - u[o + sy], u[o + sy]);
+        const float e01 = fmaf(wx, u[o + sz + 1] - u[o + sz], u[o + sz]);
+        const float e11 = fmaf(wx, u[o + sz + sy + 1] - u[o + sz + sy], u[o + sz + sy]);
+        const float a0 = fmaf(wy, e10 - e00, e00), a1 = fmaf(wy, e11 - e01, e01);
+        uf[i] = fmaf(wz, a1 - a0, a0);
+    }
+}
+
+}  // namespace ngf

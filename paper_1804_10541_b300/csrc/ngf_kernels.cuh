@@ -1,0 +1,161 @@
+// Shared definitions of the device code of libngf_b300: the fused image-grid
+// pass (objective, gradient, Gauss-Newton Hessian-vector product), the exact
+// Jacobi diagonal, the nodal kernels (curvature, deterministic combination of
+// tile partials, PCG vector updates, reductions) and the multilevel helpers.
+// Kernel bodies are in ngf_kernels.cu.
+//
+// Index conventions (Sec. 2.2): 0-based, x fastest; voxel (x,y,z) is cell
+// centre (x+1/2)h; node (i,j,k) sits at (i,j,k) hy.  Grid conversion P
+// (Eq. grid_conversion) uses per-axis tables f[v] = floor(c_v), w[v] = c_v -
+// floor(c_v) with c_v = (v+1/2)(n-1)/m, built in double on the host.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ngf_launch.cuh"
+
+namespace ngf {
+
+// ---------------------------------------------------------------------------
+// tiling of the image pass: a CTA owns a TX x TY column tile and a z-chunk and
+// marches through its planes; every voxel's warp, residual and stencil is
+// evaluated once per plane in shared memory (halo 2 for the front end, halo 1
+// for the residual Jacobian), nothing is stored in global memory.
+// ---------------------------------------------------------------------------
+constexpr int TX = 32, TY = 16, NT = TX * TY;  // 512 threads, one per output column
+constexpr int SX2 = TX + 4, SY2 = TY + 4, R2N = SX2 * SY2;  // front-end region (halo 2)
+constexpr int SX1 = TX + 2, SY1 = TY + 2, R1N = SX1 * SY1;  // Jacobian region (halo 1)
+constexpr int R0N = TX * TY;
+constexpr int UBX = TX + 5, UBY = TY + 5;       // node box of the halo-2 region (ratio >= 1)
+constexpr int NBX = TX + 1, NBY = TY + 1;       // node box of the owned columns
+constexpr int DBX = TX + 3, DBY = TY + 3;       // node box of the halo-1 region (diagonal)
+
+enum Mode { MODE_OBJ = 0, MODE_GRAD = 1, MODE_HESS = 2 };
+
+struct ImgParams {
+    int m0, m1, m2, n0, n1, n2;
+    long long M, N;
+    float ih[3];    // 1/h
+    float ihs[3];   // 1/h^2
+    float hh[3];    // 1/(2 h^2)  (h_hat of Eq. hatRho)
+    float tau, rho, tr, tau2, rho2;
+    float qscale;   // -2 hbar (gradient) or 2 hbar (Hessian)
+    double hbar;
+    const float* R;
+    const float* T;
+    const float* u;
+    const float* p;
+    const int* fx;
+    const int* fy;
+    const int* fz;
+    const float* wx;
+    const float* wy;
+    const float* wz;
+    int zc;                     // planes per z-chunk
+    int pbx, pby, pbz;          // partial box strides of this geometry
+    float* partial;             // [tile][3][pbz][pby][pbx]
+    double* dpart;              // per-CTA float64 partial sums (D)
+    unsigned int* dcount;       // last-CTA ticket
+    double* dout;               // D (hbar * sum(1 - r^2))
+};
+
+struct ImgSmem {
+    float R[3][R2N];
+    float Tw[3][R2N];
+    float S[3][R2N];
+    float Pi[2][4][R1N];        // pi(-x), pi(+x), pi(-y), pi(+y) of the halo-1 region
+    float Uz[6][UBY][UBX];      // u (and p) interpolated to the current plane in z
+    float Q[3][R0N];            // q_hat of the owned columns
+    float Acc[2][3][NBY][NBX];  // node-plane accumulators of P^T (two live planes)
+    float wx2[SX2], wy2[SY2];
+    int fx2[SX2], fy2[SY2];     // node floor relative to the Uz box
+    int fxb[TX], fyb[TY];       // node floor relative to the partial box
+    int xr_lo[NBX], xr_hi[NBX], yr_lo[NBY], yr_hi[NBY];
+    double red[NT];
+};
+
+struct DiagSmem {
+    float R[3][R1N];
+    float Tw[3][R1N];
+    float dT[3][3][R1N];        // [plane slot][component][column]
+    float Uz[3][UBY][UBX];
+    float Acc[4][3][DBY][DBX];
+    float wx1[SX1], wy1[SY1];
+    int fx1[SX1], fy1[SY1];     // node floor relative to the Uz (= partial) box
+};
+
+struct NodeGeom {
+    int n0, n1, n2;
+    long long N;
+    float ihy2[3];  // 1/hy^2
+};
+
+struct CombineParams {
+    NodeGeom G;
+    const float* partial;
+    int pbx, pby, pbz, ntx, nty;
+    const int* xlo;
+    const int* xhi;
+    const int* ylo;
+    const int* yhi;
+    const int* zlo;
+    const int* zhi;
+    const int* xb0;
+    const int* yb0;
+    const int* zb0;
+    const float* L;      // Lap(input) for the curvature term (nullable)
+    const float* cdiag;  // curvature diagonal (nullable)
+    float cscale;        // alpha 2 hbar^y
+    float* out;
+    const float* dotw;   // optional: out . dotw into dout
+    double* dpart;
+    unsigned int* dcount;
+    double* dout;
+};
+
+// PCG scalars: 0 delta, 1 dAd, 2 alpha, 3 beta, 4 rr, 5 bb, 6 status
+// (0 running, 1 converged, 2 breakdown, 3 rtol), 7 iterations.
+enum { PS_DELTA = 0, PS_DQ = 1, PS_ALPHA = 2, PS_BETA = 3, PS_RR = 4, PS_BB = 5, PS_STATUS = 6, PS_ITERS = 7 };
+
+struct PcgParams {
+    long long n;
+    float* x;
+    float* r;
+    float* z;
+    float* d;
+    const float* q;
+    const float* diag;
+    const float* rhs;
+    double* sc;
+    double* part;       // 2 * nblocks
+    unsigned int* count;
+    double rtol;
+};
+
+__host__ __device__ constexpr int ring_size(int halo) { return 2 * halo * (TX + 2 * halo) + 2 * halo * TY; }
+
+// ---- kernels (defined in ngf_kernels.cu) ----------------------------------
+__global__ void k_image_obj(const ImgParams P);   // D only
+__global__ void k_image_grad(const ImgParams P);  // D and gradient tile partials
+__global__ void k_image_hess(const ImgParams P);  // Hessian-vector tile partials
+__global__ void k_diag(const ImgParams P);        // Jacobi-diagonal tile partials
+__global__ void k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L, double* part,
+                      unsigned int* count, double* out, double scale);
+__global__ void k_node_combine(const CombineParams P);
+__global__ void k_lap2(NodeGeom G, const float* __restrict__ L, float* __restrict__ q, float scale);
+__global__ void k_pcg_init(PcgParams P);
+__global__ void k_pcg_update(PcgParams P);
+__global__ void k_pcg_dir(PcgParams P);
+__global__ void k_dot(long long n, const float* __restrict__ a, const float* __restrict__ b, double* part,
+                      unsigned int* count, double* out);
+__global__ void k_axpy(long long n, float eta, const float* __restrict__ x, const float* __restrict__ s,
+                       float* __restrict__ y);
+__global__ void k_scale(long long n, float a, const float* __restrict__ x, float* __restrict__ y);
+__global__ void k_nonfinite(long long n, const float* __restrict__ a, double* part, unsigned int* count,
+                            double* out);
+__global__ void k_restrict(int m0, int m1, int m2, const float* __restrict__ img, float* __restrict__ out);
+__global__ void k_prolong(int f0, int f1, int f2, int c0, int c1, long long Nc, const int* __restrict__ tf,
+                          const float* __restrict__ tw, const float* __restrict__ uc, float* __restrict__ uf);
+
+}  // namespace ngf

@@ -1,0 +1,83 @@
+// Internal plan structure shared by the C-ABI implementation files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "ngf.h"
+#include "ngf_kernels.cuh"
+
+namespace ngf {
+
+// Tile-partial geometry of the transposed grid conversion for one halo:
+// per tile its node-box origin, per node the first/last tile whose box
+// contains it (device arrays, one allocation).
+struct Geometry {
+    int ntx = 0, nty = 0, ntz = 0;
+    int pbx = 0, pby = 0, pbz = 0;
+    int* xlo = nullptr;
+    int* xhi = nullptr;
+    int* ylo = nullptr;
+    int* yhi = nullptr;
+    int* zlo = nullptr;
+    int* zhi = nullptr;
+    int* xb0 = nullptr;
+    int* yb0 = nullptr;
+    int* zb0 = nullptr;
+    int* mem = nullptr;
+    long long tiles() const { return (long long)ntx * nty * ntz; }
+    long long partial_floats() const { return tiles() * 3 * pbz * pby * pbx; }
+};
+
+struct Plan {
+    ngf_level_desc desc{};
+    cudaStream_t stream = nullptr;
+    int m[3]{}, n[3]{};
+    long long M = 0, N = 0;
+    double hbar = 0, hbary = 0, hy[3]{};
+    int zc = 0;
+    int img_blocks = 0, diag_blocks = 0, node_blocks = 0;
+    // device workspace
+    int* ftab = nullptr;    // fx | fy | fz
+    float* wtab = nullptr;  // wx | wy | wz
+    Geometry g0, g1;        // halo 0 (gradient, Hessian), halo 1 (diagonal)
+    float* partial = nullptr;
+    float* L = nullptr;      // Laplacian scratch, 3N
+    float* cdiag = nullptr;  // curvature diagonal, N
+    double* dsc = nullptr;   // scalars: 0 D, 1 S, 2 dot, 3 nonfinite count
+    double* dpart = nullptr;
+    unsigned int* dcount = nullptr;
+    size_t dpart_len = 0;
+    std::string err;
+    // cached PCG graph
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const void*> graph_key;
+    int graph_iters = 0;
+    long long graph_kernels = 0;
+};
+
+// helpers implemented in ngf_api.cu
+ngf_status set_error(Plan* p, ngf_status s, const std::string& msg);
+ngf_status cuda_check(Plan* p, cudaError_t e, const char* what);
+ngf_status validate_desc(const ngf_level_desc* d, std::string& why);
+bool is_device_ptr(const void* ptr);
+ImgParams img_params(const Plan* p, const float* R, const float* T, const float* u, const float* p_,
+                     int mode, const Geometry& g, double* dout);
+CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const float* L, const float* cdiag,
+                             const float* dotw, double* dout);
+NodeGeom node_geom(const Plan* p);
+ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u, const float* pv, float* q,
+                        const float* dotw, double* dout);
+ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* u, double* dD, double* dS);
+ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u, float* g, double* dD,
+                         double* dS);
+ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag);
+ngf_status dot_impl(Plan* p, long long n, const float* a, const float* b, double* dout);
+int grid_for(long long n, int max_blocks);
+
+}  // namespace ngf
+
+struct ngf_plan {
+    ngf::Plan impl;
+};

@@ -1,0 +1,261 @@
+"""Thin ctypes binding of the C ABI in include/ngf.h (libngf_b300.so).
+
+Argument marshalling only: every operator runs in the library's CUDA kernels
+for sm_103a.  Importing this module loads the in-tree library and raises if it
+is missing; there is no other code path.  Functions carry the ABI's names;
+tensors are passed as torch CUDA tensors (float32, contiguous) or as raw
+integer device pointers, streams as torch.cuda.Stream, raw cudaStream_t
+integers or None (the legacy default stream).
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libngf_b300.so")
+
+NGF_OK = 0
+STATUS = {0: "NGF_OK", -1: "NGF_EINVAL", -2: "NGF_ECUDA", -3: "NGF_ENOMEM", -4: "NGF_ENONFINITE",
+          -5: "NGF_EBREAKDOWN", -6: "NGF_ELINESEARCH", -7: "NGF_EMAXITER", -8: "NGF_EBOUNDS"}
+NGF_PCG_NSCALARS = 8
+
+# every function include/ngf.h declares
+EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_last_error", "ngf_objective",
+           "ngf_objective_dev", "ngf_gradient", "ngf_gradient_dev", "gn_hessvec", "curvature_apply",
+           "ngf_gn_diagonal", "pcg_init", "pcg_step", "pcg_solve", "pcg_read", "register_multilevel",
+           "ngf_launch_count"]
+
+
+class LevelDesc(C.Structure):
+    _fields_ = [("m", C.c_int32 * 3), ("h", C.c_double * 3), ("n", C.c_int32 * 3),
+                ("alpha", C.c_double), ("tau", C.c_double), ("rho", C.c_double)]
+
+
+class PcgState(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("r", C.c_void_p), ("z", C.c_void_p), ("d", C.c_void_p),
+                ("q", C.c_void_p), ("diag", C.c_void_p), ("dev_scalars", C.c_void_p), ("rtol", C.c_double)]
+
+
+class PcgInfo(C.Structure):
+    _fields_ = [("iters_done", C.c_int32), ("status", C.c_int32), ("delta", C.c_double), ("rr", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("gn_iters", C.c_int32), ("pcg_iters", C.c_int32), ("ls_max", C.c_int32),
+                ("armijo_c1", C.c_double), ("pcg_rtol", C.c_double), ("start_level", C.c_int32),
+                ("u_init", C.c_void_p), ("use_graph", C.c_int32)]
+
+
+class Report(C.Structure):
+    _fields_ = [("J", C.c_double), ("D", C.c_double), ("S", C.c_double), ("gn_done", C.c_int32),
+                ("pcg_total", C.c_int32), ("ls_trials", C.c_int32), ("ls_fail", C.c_int32),
+                ("status", C.c_int32), ("seconds", C.c_double), ("hessvec_voxels", C.c_int64)]
+
+
+class NGFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def declare(lib):
+    """Attach argument/return types of every exported function to `lib`."""
+    P, D, I32, VP = C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_void_p
+    sig = {
+        "ngf_plan_create": [C.POINTER(C.c_void_p), C.POINTER(LevelDesc), VP],
+        "ngf_plan_destroy": [P],
+        "ngf_plan_set_stream": [P, VP],
+        "ngf_objective": [P, VP, VP, VP, D, D],
+        "ngf_objective_dev": [P, VP, VP, VP, VP],
+        "ngf_gradient": [P, VP, VP, VP, VP, D, D],
+        "ngf_gradient_dev": [P, VP, VP, VP, VP, VP],
+        "gn_hessvec": [P, VP, VP, VP, VP, VP],
+        "curvature_apply": [P, VP, VP, D],
+        "ngf_gn_diagonal": [P, VP, VP, VP, VP],
+        "pcg_init": [P, C.POINTER(PcgState), VP],
+        "pcg_step": [P, C.POINTER(PcgState), VP, VP, VP],
+        "pcg_solve": [P, C.POINTER(PcgState), VP, VP, VP, I32, I32],
+        "pcg_read": [P, C.POINTER(PcgState), C.POINTER(PcgInfo)],
+        "register_multilevel": [C.POINTER(LevelDesc), C.POINTER(Options), VP, VP, VP, C.POINTER(Report), VP],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.ngf_last_error.argtypes = [P]
+    lib.ngf_last_error.restype = C.c_char_p
+    lib.ngf_launch_count.argtypes = []
+    lib.ngf_launch_count.restype = C.c_int64
+    return lib
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libngf_b300.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    return declare(C.CDLL(LIB_PATH))
+
+
+lib = _load()
+
+
+def _check(status, plan=None):
+    if status != NGF_OK:
+        raise NGFError(status, lib.ngf_last_error(plan).decode())
+
+
+def _ptr(x):
+    """Device (or host) address of a tensor / array / integer pointer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def level_desc(m, h, n, alpha=1.0, tau=0.1, rho=0.1):
+    d = LevelDesc()
+    for a in range(3):
+        d.m[a], d.h[a], d.n[a] = int(m[a]), float(h[a]), int(n[a])
+    d.alpha, d.tau, d.rho = float(alpha), float(tau), float(rho)
+    return d
+
+
+# ---- same-name wrappers of the C ABI ---------------------------------------
+
+def ngf_plan_create(desc, stream=None):
+    h = C.c_void_p()
+    _check(lib.ngf_plan_create(C.byref(h), C.byref(desc), _stream(stream)))
+    return h
+
+
+def ngf_plan_destroy(plan):
+    _check(lib.ngf_plan_destroy(plan))
+
+
+def ngf_plan_set_stream(plan, stream):
+    _check(lib.ngf_plan_set_stream(plan, _stream(stream)), plan)
+
+
+def ngf_last_error(plan=None):
+    return lib.ngf_last_error(plan).decode()
+
+
+def ngf_objective(plan, R, T, u):
+    D, S = C.c_double(), C.c_double()
+    _check(lib.ngf_objective(plan, _ptr(R), _ptr(T), _ptr(u), C.byref(D), C.byref(S)), plan)
+    return D.value, S.value
+
+
+def ngf_objective_dev(plan, R, T, u, dev_DS):
+    _check(lib.ngf_objective_dev(plan, _ptr(R), _ptr(T), _ptr(u), _ptr(dev_DS)), plan)
+
+
+def ngf_gradient(plan, R, T, u, grad, want_scalars=True):
+    if not want_scalars:
+        _check(lib.ngf_gradient(plan, _ptr(R), _ptr(T), _ptr(u), _ptr(grad), None, None), plan)
+        return None
+    D, S = C.c_double(), C.c_double()
+    _check(lib.ngf_gradient(plan, _ptr(R), _ptr(T), _ptr(u), _ptr(grad), C.byref(D), C.byref(S)), plan)
+    return D.value, S.value
+
+
+def ngf_gradient_dev(plan, R, T, u, grad, dev_DS=None):
+    _check(lib.ngf_gradient_dev(plan, _ptr(R), _ptr(T), _ptr(u), _ptr(grad), _ptr(dev_DS)), plan)
+
+
+def gn_hessvec(plan, R, T, u, p, q):
+    _check(lib.gn_hessvec(plan, _ptr(R), _ptr(T), _ptr(u), _ptr(p), _ptr(q)), plan)
+
+
+def curvature_apply(plan, p, q=None, want_S=True):
+    Sp = C.c_double()
+    _check(lib.curvature_apply(plan, _ptr(p), _ptr(q), C.byref(Sp) if want_S else None), plan)
+    return Sp.value if want_S else None
+
+
+def ngf_gn_diagonal(plan, R, T, u, diag):
+    _check(lib.ngf_gn_diagonal(plan, _ptr(R), _ptr(T), _ptr(u), _ptr(diag)), plan)
+
+
+def pcg_state(x, r, z, d, q, diag, dev_scalars, rtol=0.0):
+    st = PcgState()
+    st.x, st.r, st.z, st.d, st.q = _ptr(x), _ptr(r), _ptr(z), _ptr(d), _ptr(q)
+    st.diag, st.dev_scalars, st.rtol = _ptr(diag), _ptr(dev_scalars), float(rtol)
+    return st
+
+
+def pcg_init(plan, st, rhs):
+    _check(lib.pcg_init(plan, C.byref(st), _ptr(rhs)), plan)
+
+
+def pcg_step(plan, st, R, T, u):
+    _check(lib.pcg_step(plan, C.byref(st), _ptr(R), _ptr(T), _ptr(u)), plan)
+
+
+def pcg_solve(plan, st, R, T, u, iters, use_graph=True):
+    _check(lib.pcg_solve(plan, C.byref(st), _ptr(R), _ptr(T), _ptr(u), int(iters), 1 if use_graph else 0), plan)
+
+
+def pcg_read(plan, st):
+    info = PcgInfo()
+    _check(lib.pcg_read(plan, C.byref(st), C.byref(info)), plan)
+    return info
+
+
+def options(levels, gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rtol=0.0, u_init=None,
+            start_level=0, use_graph=True):
+    o = Options()
+    o.levels, o.gn_iters, o.pcg_iters, o.ls_max = levels, gn_iters, pcg_iters, ls_max
+    o.armijo_c1, o.pcg_rtol, o.start_level = armijo_c1, pcg_rtol, start_level
+    o.u_init = _ptr(u_init)
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def register_multilevel(desc, opts, R, T, u_out, stream=None):
+    rep = Report()
+    _check(lib.register_multilevel(C.byref(desc), C.byref(opts), _ptr(R), _ptr(T), _ptr(u_out), C.byref(rep),
+                                   _stream(stream)))
+    return rep
+
+
+def ngf_launch_count():
+    return int(lib.ngf_launch_count())
+
+
+class Plan:
+    """Owning wrapper of an ngf_plan."""
+
+    def __init__(self, desc, stream=None):
+        self.desc = desc
+        self.handle = ngf_plan_create(desc, stream)
+
+    def close(self):
+        if self.handle:
+            ngf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
