@@ -1,0 +1,332 @@
+"""Benchmark of the matrix-free NGF + curvature registration on B300.
+
+One step = one full multilevel Gauss-Newton registration (register_multilevel:
+image pyramid, per level 10 Gauss-Newton steps each with gradient, Jacobi
+diagonal, 20 PCG iterations of gn_hessvec and an Armijo line search, and the
+prolongation between levels) of the synthetic 256x256x120 lung-CT workload
+(1x1x2.5 mm, 129x129x61 nodes, 4 levels).  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (a 256 MB write) before every timed step.
+
+value = image voxels processed by gn_hessvec over the whole registration
+(sum over levels of voxels x Hessian-vector products) / step time, in
+Gvoxel/s: the Hessian-vector throughput of the whole job, every other part
+of the registration included.  `ms_per_step` is the full-registration time.
+
+`--impl reference` times the FP64 CPU oracle instead (bounded samples of the
+same workload on the host cores).  Under torchrun every rank runs an
+independent replica (the path has no exchange step); value sums all ranks'
+voxels over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "lung_ct"
+GN_ITERS, PCG_ITERS = 10, 20
+# algorithmic cost of one gn_hessvec image-grid pass per voxel (see design notes):
+# P u and P p (separable) 30, warp + dT 50, 12 differences + N, A, B 40, rho_hat 25,
+# v = dr s and t = dr^T v 28, q_hat 3, P^T 25  ->  200 FP32 flop (FMA = 2 flop)
+HESS_FLOP_PER_VOXEL = 200.0
+FP32_LANES_PER_SM = 128
+METRIC = "gn_hessvec Gvoxel/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+def reduce_max_sum(values_max, values_sum, ws):
+    """(max over ranks of values_max, sum over ranks of values_sum)."""
+    if ws == 1:
+        return values_max, values_sum
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    a = torch.tensor([float(values_max)], dtype=torch.float64, device=dev)
+    b = torch.tensor([float(values_sum)], dtype=torch.float64, device=dev)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline_leg(R, T, w, seconds_budget=20.0, max_calls=3):
+    """Time the FP64 oracle's gn_hessvec (as it stands) on the host cores on a
+    bounded sample of the same workload: whole calls on the full lung-CT grid."""
+    import numpy as np
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    from paper_1804_10541_b300 import synth
+    m, h, n = w["m"], w["h"], w["n"]
+    L = O.level(m, h, n, w["alpha"], w["tau"], w["rho"])
+    N = n[0] * n[1] * n[2]
+    u, p = synth.random_fields(N, 5, amp=0.5 * min(h))
+    Rh = R.double().cpu().numpy()
+    Th = T.double().cpu().numpy()
+    uh, ph = u.double().numpy(), p.double().numpy()
+    O.hessvec(L, Rh, Th, uh, ph)  # first call pages the arrays in; not timed
+    calls, t0 = 0, time.perf_counter()
+    while calls < max_calls:
+        O.hessvec(L, Rh, Th, uh, ph)
+        calls += 1
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+    dt = time.perf_counter() - t0
+    M = m[0] * m[1] * m[2]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": M * calls / dt / 1e9, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
+            "sample": f"{calls} FP64 oracle gn_hessvec calls on the full {m[0]}x{m[1]}x{m[2]} lung-CT grid "
+                      f"({dt:.1f} s, OpenMP over z)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host."""
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    import torch
+    from paper_1804_10541_b300 import synth
+    R, T, _, w = synth.make(WORKLOAD, device="cuda" if torch.cuda.is_available() else "cpu")
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    m, h, n = w["m"], w["h"], w["n"]
+    L = O.level(m, h, n, w["alpha"], w["tau"], w["rho"])
+    N = n[0] * n[1] * n[2]
+    u, p = synth.random_fields(N, 5, amp=0.5 * min(h))
+    Rh, Th, uh, ph = R.double().cpu().numpy(), T.double().cpu().numpy(), u.double().numpy(), p.double().numpy()
+    for _ in range(args.warmup):
+        O.hessvec(L, Rh, Th, uh, ph)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.hessvec(L, Rh, Th, uh, ph)
+        times.append(time.perf_counter() - t0)
+    M = m[0] * m[1] * m[2]
+    total = sum(times)
+    value = M * args.steps / total / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{WORKLOAD} {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes "
+                                   f"{n[0]}x{n[1]}x{n[2]}; one step = one FP64 oracle gn_hessvec",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} timed FP64 oracle gn_hessvec calls on the full grid"},
+            "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    from paper_1804_10541_b300 import ngf, synth
+
+    R, T, _, w = synth.make(WORKLOAD, device=dev)
+    m, h, n, levels = w["m"], w["h"], w["n"], w["levels"]
+    M = m[0] * m[1] * m[2]
+    N = n[0] * n[1] * n[2]
+    desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"])
+    opts = ngf.options(levels=levels, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True)
+    stream = torch.cuda.Stream(device=dev)
+    u = torch.empty(3 * N, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, device=dev, dtype=torch.float32)  # 256 MB > 126 MB L2
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            rep = ngf.register_multilevel(desc, opts, R, T, u, stream)
+    stream.synchronize()
+
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = ngf.ngf_launch_count()
+    voxels = 0
+    reps = []
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            rep = ngf.register_multilevel(desc, opts, R, T, u, stream)
+            ev[k][1].record(stream)
+            voxels += rep.hessvec_voxels
+            reps.append(rep)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    launches = ngf.ngf_launch_count() - launches0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    t_max, vox_all = reduce_max_sum(t_local, voxels, ws)
+    value = vox_all / t_max / 1e9
+
+    # ---- end to end through the public API with host buffers (pinned)
+    Rp = torch.empty(M, dtype=torch.float32, pin_memory=True)
+    Tp = torch.empty(M, dtype=torch.float32, pin_memory=True)
+    Up = torch.empty(3 * N, dtype=torch.float32, pin_memory=True)
+    Rp.copy_(R.cpu())
+    Tp.copy_(T.cpu())
+    e2e_times, e2e_vox = [], 0
+    for k in range(max(1, args.steps)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = ngf.register_multilevel(desc, opts, Rp, Tp, Up, stream)
+        e2e_times.append(time.perf_counter() - t0)
+        e2e_vox += rep.hessvec_voxels
+    e2e_t, e2e_v = reduce_max_sum(sum(e2e_times), e2e_vox, ws)
+    e2e = {"value": e2e_v / e2e_t / 1e9, "unit": "Gvoxel/s", "h2d_bytes_per_step": 2 * M * 4,
+           "d2h_bytes_per_step": 3 * N * 4}
+
+    # ---- live roofline of the dominant kernel (Hessian image pass) at the
+    # finest level, same plan configuration and inputs as inside the step
+    gen = torch.Generator(device="cpu").manual_seed(11)
+    uu = (0.5 * min(h) * torch.randn(3 * N, generator=gen)).to(dev)
+    pp = torch.randn(3 * N, generator=gen).to(dev)
+    q = torch.empty(3 * N, device=dev)
+    nh = GN_ITERS * PCG_ITERS
+    with torch.cuda.stream(stream), ngf.Plan(desc, stream) as pl:
+        for _ in range(20):
+            ngf.gn_hessvec(pl.handle, R, T, uu, pp, q)
+        ngf.ngf_profile_enable(pl.handle, True)
+        ngf.ngf_profile_read(pl.handle, ngf.NGF_K_HESSVEC)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nh):
+            ngf.gn_hessvec(pl.handle, R, T, uu, pp, q)
+        e1.record(stream)
+        ms_img, nl = ngf.ngf_profile_read(pl.handle, ngf.NGF_K_HESSVEC)
+        stream.synchronize()
+        ms_call = e0.elapsed_time(e1) / nh
+    t_launch = ms_img / nl / 1e3
+    peaks = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12  # TFLOP/s
+    achieved = HESS_FLOP_PER_VOXEL * M / t_launch / 1e12
+    bytes_per_voxel = 8.0 + 36.0 * N / M  # R, T + u, p read and q written, per voxel
+    roofline = {"bound": "alu", "kernel": "k_image_hess", "achieved": achieved, "peak": alu_peak,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
+                "flop_per_voxel": HESS_FLOP_PER_VOXEL, "launch_us": t_launch * 1e6,
+                "hessvec_call_us": ms_call * 1e3,
+                "hbm": {"algorithmic_bytes": bytes_per_voxel * M,
+                        "achieved_gbs": bytes_per_voxel * M / t_launch / 1e9,
+                        "peak_gbs": peaks.get("hbm_gbs"),
+                        "frac": (bytes_per_voxel * M / t_launch / 1e9) / peaks["hbm_gbs"] if "hbm_gbs" in peaks else None},
+                "kernel_gvoxel_s": M / t_launch / 1e9}
+
+    if rank == 0:
+        cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline_leg(R, T, w)
+        r0 = reps[-1]
+        line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"{WORKLOAD} {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes "
+                                       f"{n[0]}x{n[1]}x{n[2]}, {levels} levels, {GN_ITERS} GN x {PCG_ITERS} PCG; "
+                                       f"one step = one full register_multilevel",
+                           "parallelism": f"replicas x{ws}", "l2": "flushed before every step (256 MB write)",
+                           "registration_ms": 1e3 * t_max / args.steps, "final_J": r0.J,
+                           "gn_done": r0.gn_done, "pcg_total": r0.pcg_total, "ls_trials": r0.ls_trials},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(launches)}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -199,6 +199,16 @@ ngf_status register_multilevel(const ngf_level_desc* finest, const ngf_options* 
                                const float* R, const float* T, float* u_out,
                                ngf_report* report, void* cuda_stream);
 
+/* ---- measurement ------------------------------------------------------
+ * When enabled, the plan records a CUDA event pair on its stream around every
+ * launch of its image-grid kernels issued outside stream capture.
+ * ngf_profile_read synchronises, returns the summed milliseconds and the
+ * launch count of kernel `which` (NGF_K_OBJECTIVE ... NGF_K_DIAGONAL) since
+ * the last read, and clears that record. */
+enum { NGF_K_OBJECTIVE = 0, NGF_K_GRADIENT = 1, NGF_K_HESSVEC = 2, NGF_K_DIAGONAL = 3 };
+ngf_status ngf_profile_enable(ngf_plan* plan, int32_t enable);
+ngf_status ngf_profile_read(ngf_plan* plan, int32_t which, double* ms, int64_t* launches);
+
 /* Kernels launched by this library in this process so far. */
 int64_t ngf_launch_count(void);
 

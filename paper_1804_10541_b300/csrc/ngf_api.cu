@@ -162,7 +162,27 @@ static ngf_status build_geometry(Plan* p, int halo, const std::vector<int>* f, G
     return NGF_OK;
 }
 
+// Record one event on the plan's stream for kernel `which` (called before and
+// after each image-kernel launch) when timing is enabled and the stream is not
+// being captured.
+cudaError_t prof_mark(Plan* p, int which) {
+    if (!p->prof) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(p->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return cudaSuccess;
+    cudaEvent_t e;
+    cudaError_t err = cudaEventCreate(&e);
+    if (err != cudaSuccess) return err;
+    p->prof_ev[which].push_back(e);
+    return cudaEventRecord(e, p->stream);
+}
+
+static void clear_prof(Plan* p, int which) {
+    for (cudaEvent_t e : p->prof_ev[which]) cudaEventDestroy(e);
+    p->prof_ev[which].clear();
+}
+
 static void free_plan(Plan* p) {
+    for (int k = 0; k < 4; ++k) clear_prof(p, k);
     cudaFree(p->ftab);
     cudaFree(p->wtab);
     cudaFree(p->g0.mem);
@@ -376,7 +396,9 @@ static dim3 img_grid(const Geometry& g) { return dim3(g.ntx, g.nty, g.ntz); }
 
 ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* u, double* dD, double* dS) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_OBJ, p->g0, dD);
+    NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
     NGF_CU(p, launch(k_image_obj, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_obj");
+    NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
     NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
                      p->dcount, dS, p->hbary),
            "k_lap");
@@ -386,7 +408,9 @@ ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* 
 ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u, float* g, double* dD,
                          double* dS) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_GRAD, p->g0, dD);
+    NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
     NGF_CU(p, launch(k_image_grad, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_grad");
+    NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
     NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
                      p->dcount, dS, p->hbary),
            "k_lap");
@@ -401,7 +425,9 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
                      p->dcount, (double*)nullptr, 0.0),
            "k_lap");
     ImgParams P = img_params(p, R, T, u, pv, MODE_HESS, p->g0, nullptr);
+    NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
     NGF_CU(p, launch(k_image_hess, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_hess");
+    NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g0, q, p->L, nullptr, dotw, dout);
     NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
@@ -409,7 +435,9 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
 
 ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g1, nullptr);
+    NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     NGF_CU(p, launch(k_diag, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P), "k_diag");
+    NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g1, diag, nullptr, p->cdiag, nullptr, nullptr);
     NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
@@ -657,6 +685,30 @@ ngf_status pcg_read(ngf_plan* plan, const ngf_pcg_state* st, ngf_pcg_info* info)
     info->status = (int32_t)h[PS_STATUS];
     info->delta = h[PS_DELTA];
     info->rr = h[PS_RR];
+    return NGF_OK;
+}
+
+ngf_status ngf_profile_enable(ngf_plan* plan, int32_t enable) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    plan->impl.prof = enable != 0;
+    return NGF_OK;
+}
+
+ngf_status ngf_profile_read(ngf_plan* plan, int32_t which, double* ms, int64_t* launches) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    if (which < 0 || which > 3 || !ms || !launches) return set_error(p, NGF_EINVAL, "bad kernel index or output");
+    NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    double total = 0.0;
+    const auto& ev = p->prof_ev[which];
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+        float t = 0.f;
+        NGF_CU(p, cudaEventElapsedTime(&t, ev[i], ev[i + 1]), "cudaEventElapsedTime");
+        total += t;
+    }
+    *ms = total;
+    *launches = (int64_t)(ev.size() / 2);
+    clear_prof(p, which);
     return NGF_OK;
 }
 

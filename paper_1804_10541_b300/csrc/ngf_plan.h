@@ -50,6 +50,9 @@ struct Plan {
     unsigned int* dcount = nullptr;
     size_t dpart_len = 0;
     std::string err;
+    // kernel timing (measurement only)
+    bool prof = false;
+    std::vector<cudaEvent_t> prof_ev[4];  // start/stop pairs per image kernel
     // cached PCG graph
     cudaGraphExec_t graph = nullptr;
     std::vector<const void*> graph_key;
@@ -73,6 +76,7 @@ ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* 
 ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u, float* g, double* dD,
                          double* dS);
 ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag);
+cudaError_t prof_mark(Plan* p, int which);
 ngf_status dot_impl(Plan* p, long long n, const float* a, const float* b, double* dout);
 int grid_for(long long n, int max_blocks);
 

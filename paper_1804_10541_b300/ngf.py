@@ -22,7 +22,7 @@ NGF_PCG_NSCALARS = 8
 EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_last_error", "ngf_objective",
            "ngf_objective_dev", "ngf_gradient", "ngf_gradient_dev", "gn_hessvec", "curvature_apply",
            "ngf_gn_diagonal", "pcg_init", "pcg_step", "pcg_solve", "pcg_read", "register_multilevel",
-           "ngf_launch_count"]
+           "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count"]
 
 
 class LevelDesc(C.Structure):
@@ -76,6 +76,8 @@ def declare(lib):
         "pcg_solve": [P, C.POINTER(PcgState), VP, VP, VP, I32, I32],
         "pcg_read": [P, C.POINTER(PcgState), C.POINTER(PcgInfo)],
         "register_multilevel": [C.POINTER(LevelDesc), C.POINTER(Options), VP, VP, VP, C.POINTER(Report), VP],
+        "ngf_profile_enable": [P, I32],
+        "ngf_profile_read": [P, I32, D, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -230,6 +232,19 @@ def register_multilevel(desc, opts, R, T, u_out, stream=None):
     _check(lib.register_multilevel(C.byref(desc), C.byref(opts), _ptr(R), _ptr(T), _ptr(u_out), C.byref(rep),
                                    _stream(stream)))
     return rep
+
+
+NGF_K_OBJECTIVE, NGF_K_GRADIENT, NGF_K_HESSVEC, NGF_K_DIAGONAL = 0, 1, 2, 3
+
+
+def ngf_profile_enable(plan, enable=True):
+    _check(lib.ngf_profile_enable(plan, 1 if enable else 0), plan)
+
+
+def ngf_profile_read(plan, which):
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib.ngf_profile_read(plan, int(which), C.byref(ms), C.byref(n)), plan)
+    return ms.value, n.value
 
 
 def ngf_launch_count():

@@ -1,0 +1,70 @@
+"""The C-ABI library loads and exports every function include/ngf.h declares;
+host-side validation rejects bad arguments before any CUDA call (CPU only)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "ngf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*([A-Za-z_][A-Za-z0-9_]*)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "return")))
+
+
+@pytest.fixture(scope="module")
+def ngf():
+    from paper_1804_10541_b300 import build
+    build.build()
+    from paper_1804_10541_b300 import ngf as m
+    return m
+
+
+def test_every_declared_symbol_is_exported(ngf):
+    decl = _declared_functions()
+    assert len(decl) >= 17
+    for name in decl:
+        assert hasattr(ngf.lib, name), name
+    assert sorted(ngf.EXPORTS) == decl
+
+
+def test_struct_layouts_match_header(ngf):
+    # sizes implied by the header's field order on x86-64
+    assert C.sizeof(ngf.LevelDesc) == 12 + 4 + 24 + 12 + 4 + 24
+    assert C.sizeof(ngf.PcgState) == 8 * 8
+    assert C.sizeof(ngf.Report) == 24 + 20 + 4 + 8 + 8
+
+
+@pytest.mark.parametrize("m,n,tau,rho,alpha,what", [
+    ((8, 8, 8), (10, 5, 5), 0.1, 0.1, 1.0, "finer than the image grid"),
+    ((8, 8, 8), (1, 5, 5), 0.1, 0.1, 1.0, "nodes n must be >= 2"),
+    ((0, 8, 8), (2, 5, 5), 0.1, 0.1, 1.0, "cells m must be >= 1"),
+    ((8, 8, 8), (5, 5, 5), 0.0, 0.1, 1.0, "tau and rho"),
+    ((8, 8, 8), (5, 5, 5), 0.1, 0.1, -1.0, "alpha"),
+])
+def test_plan_validation_rejects_before_any_launch(ngf, m, n, tau, rho, alpha, what):
+    d = ngf.level_desc(m, (1, 1, 1), n, alpha=alpha, tau=tau, rho=rho)
+    h = C.c_void_p()
+    st = ngf.lib.ngf_plan_create(C.byref(h), C.byref(d), None)
+    assert st == -1 and not h.value
+    assert what in ngf.ngf_last_error(None)
+
+
+def test_null_plan_is_an_error(ngf):
+    D, S = C.c_double(), C.c_double()
+    assert ngf.lib.ngf_objective(None, None, None, None, C.byref(D), C.byref(S)) == -1
+    assert "plan is NULL" in ngf.ngf_last_error(None)
+    assert ngf.lib.ngf_plan_destroy(None) == 0
+
+
+def test_register_multilevel_validates_options(ngf):
+    d = ngf.level_desc((8, 8, 8), (1, 1, 1), (5, 5, 5))
+    o = ngf.options(levels=0)
+    rep = ngf.Report()
+    buf = (C.c_float * 512)()
+    st = ngf.lib.register_multilevel(C.byref(d), C.byref(o), buf, buf, buf, C.byref(rep), None)
+    assert st == -1 and "levels" in ngf.ngf_last_error(None)

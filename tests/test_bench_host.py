@@ -1,0 +1,65 @@
+"""Host logic of bench.py without a GPU: the max-over-ranks / sum-over-ranks
+aggregation of independent replicas (two gloo ranks on CPU) and the parsing
+of sampled nvidia-smi clock lines."""
+import os
+import socket
+
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, ws, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(ws))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    t, v = bench.reduce_max_sum(1.5 + rank, 1000 * (rank + 1), ws)
+    q.put((rank, t, v))
+    dist.destroy_process_group()
+
+
+def test_reduce_max_sum_two_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for _, t, v in out:
+        assert t == 2.5 and v == 3000.0
+
+
+def test_reduce_single_rank_is_identity():
+    assert bench.reduce_max_sum(3.0, 7, 1) == (3.0, 7)
+
+
+class _FakeProc:
+    def __init__(self, text):
+        self.text = text
+
+    def terminate(self):
+        pass
+
+    def communicate(self, timeout=None):
+        return self.text, ""
+
+
+def test_clock_sampler_parses_reasons():
+    s = bench.ClockSampler(0)
+    s.proc = _FakeProc("0, 1900, 2032, 700.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                       "0, 1800, 2032, 1099.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                       "0, 2000, 2032, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    c = s.stop()
+    assert c["sm_mhz"] == 1900 and c["sm_max_mhz"] == 2032 and c["reasons"] == ["sw_power_cap"]

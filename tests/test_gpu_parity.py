@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Element-by-element comparisons on seeded inputs: tiny odd grids where every
+voxel is a boundary voxel, a full-resolution deformation grid, non-integer
+voxels-per-cell ratios, several tiles with ragged tails, the 32^3 blob
+workload, and the full-size 256x256x120 lung-CT workload in the launch
+configuration the benchmark times.  The 512x512x900 workload is checked by
+properties that hold at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+import gpu_util as G  # noqa: E402
+
+CASES = [
+    ((5, 4, 3), (1.0, 1.0, 1.0), (3, 3, 2)),       # every voxel on the boundary
+    ((6, 5, 4), (1.0, 0.8, 2.5), (4, 3, 3)),       # anisotropic, non-integer ratio
+    ((4, 3, 3), (0.7, 1.3, 1.1), (5, 4, 4)),       # deformation grid at full resolution
+    ((37, 19, 11), (1.0, 1.0, 1.0), (19, 10, 6)),  # 2 x 2 tiles, ragged
+    ((70, 35, 21), (1.0, 1.0, 2.5), (36, 18, 11)), # 3 x 3 tiles, ragged, z-chunks
+    ((40, 20, 10), (1.0, 1.0, 1.0), (41, 21, 11)), # ratio 1 on every axis
+    ((65, 33, 40), (0.8, 0.8, 1.0), (17, 9, 11)),  # ratio 4, non-integer in z
+]
+
+
+@pytest.fixture(scope="module")
+def ngf():
+    from paper_1804_10541_b300 import ngf as m
+    assert torch.cuda.is_available()
+    return m
+
+
+def _all_ops(ngf, c):
+    import oracle as O
+    out = {}
+    with ngf.Plan(c.desc) as pl:
+        D, S = ngf.ngf_objective(pl.handle, c.R, c.T, c.u)
+        g = c.empty()
+        Dg, Sg = ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g)
+        q = c.empty()
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q)
+        dg = c.empty()
+        ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, dg)
+        cq = c.empty()
+        Sp = ngf.curvature_apply(pl.handle, c.p, cq)
+        torch.cuda.synchronize()
+    Do, So = O.objective(c.L, c.Rh, c.Th, c.uh)
+    go, _, _ = O.gradient(c.L, c.Rh, c.Th, c.uh)
+    qo = O.hessvec(c.L, c.Rh, c.Th, c.uh, c.ph)
+    dgo = O.gn_diagonal(c.L, c.Rh, c.Th, c.uh)
+    cqo, Spo = O.curvature_apply(c.L, c.ph)
+    out["D"] = abs(D - Do) / abs(Do)
+    out["Dg"] = abs(Dg - Do) / abs(Do)
+    out["S"] = abs(S - So) / max(abs(So), 1e-300)
+    out["grad"] = G.rel(G.f64(g), go)
+    out["hess"] = G.rel(G.f64(q), qo)
+    out["diag"] = G.rel(G.f64(dg), dgo)
+    out["curv"] = G.rel(G.f64(cq), cqo)
+    out["Sp"] = abs(Sp - Spo) / max(abs(Spo), 1e-300)
+    return out
+
+
+def _assert_ok(r):
+    assert r["D"] < G.TOL_OBJ and r["Dg"] < G.TOL_OBJ and r["S"] < G.TOL_OBJ, r
+    assert r["grad"] < G.TOL_GRAD, r
+    assert r["hess"] < G.TOL_HESS, r
+    assert r["diag"] < G.TOL_DIAG, r
+    assert r["curv"] < G.TOL_CURV and r["Sp"] < G.TOL_OBJ, r
+
+
+@pytest.mark.parametrize("m,h,n", CASES)
+def test_operators_match_oracle_small(ngf, m, h, n):
+    c = G.random_case(m, h, n, seed=sum(m))
+    _assert_ok(_all_ops(ngf, c))
+
+
+def test_operators_match_oracle_blobs32(ngf):
+    c, _ = G.workload_case("blobs_32")
+    _assert_ok(_all_ops(ngf, c))
+
+
+def test_operators_match_oracle_lung_full_size(ngf):
+    """256x256x120 lung-CT workload, the benchmark's configuration."""
+    import oracle as O
+    c, w = G.workload_case("lung_ct", amp_vox=0.7)
+    with ngf.Plan(c.desc) as pl:
+        D, S = ngf.ngf_objective(pl.handle, c.R, c.T, c.u)
+        g = c.empty()
+        ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g, want_scalars=False)
+        q = c.empty()
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q)
+        torch.cuda.synchronize()
+    Do, So = O.objective(c.L, c.Rh, c.Th, c.uh)
+    assert abs(D - Do) / abs(Do) < G.TOL_OBJ and abs(S - So) / So < G.TOL_OBJ
+    go, _, _ = O.gradient(c.L, c.Rh, c.Th, c.uh)
+    assert G.rel(G.f64(g), go) < G.TOL_GRAD
+    qo = O.hessvec(c.L, c.Rh, c.Th, c.uh, c.ph)
+    assert G.rel(G.f64(q), qo) < G.TOL_HESS
+
+
+def test_hessvec_is_deterministic(ngf):
+    c, _ = G.workload_case("blobs_32")
+    with ngf.Plan(c.desc) as pl:
+        q1, q2 = c.empty(), c.empty()
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q2)
+        g1, g2 = c.empty(), c.empty()
+        ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g1)
+        ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g2)
+        torch.cuda.synchronize()
+    assert torch.equal(q1, q2) and torch.equal(g1, g2)
+
+
+def test_identity_and_identical_images(ngf):
+    """T = R, u = 0, tau = rho: D = 0 and grad D = 0 (r = 1 everywhere)."""
+    m, h, n = (40, 24, 12), (1.0, 1.0, 1.5), (21, 13, 7)
+    c = G.random_case(m, h, n, alpha=0.0, tau=0.2, rho=0.2, seed=3)
+    c.T = c.R.clone()
+    c.u.zero_()
+    with ngf.Plan(c.desc) as pl:
+        g = c.empty()
+        D, S = ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g)
+    assert abs(D) < 1e-9 * c.M and S == 0.0
+    assert float(g.abs().max()) < 1e-6
+
+
+def test_thorax_full_size_properties(ngf):
+    """512x512x900 workload: symmetric PSD Hessian and a finite gradient."""
+    c, w = G.workload_case("thorax_abd", amp_vox=0.5)
+    gq = torch.Generator(device="cpu").manual_seed(77)
+    p2 = torch.randn(3 * c.N, generator=gq).to("cuda")
+    with ngf.Plan(c.desc) as pl:
+        q1, q2 = c.empty(), c.empty()
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, p2, q2)
+        g = c.empty()
+        D, S = ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g)
+        torch.cuda.synchronize()
+    a = float(torch.dot(p2.double(), q1.double()))
+    b = float(torch.dot(c.p.double(), q2.double()))
+    assert abs(a - b) <= 1e-4 * (abs(a) + abs(b))
+    assert float(torch.dot(c.p.double(), q1.double())) > 0
+    assert torch.isfinite(g).all() and np.isfinite(D) and D > 0
+
+
+def test_pcg_matches_oracle_and_graph(ngf):
+    import oracle as O
+    c, _ = G.workload_case("blobs_32")
+    iters = 8
+    res = {}
+    stream = torch.cuda.Stream()
+    for use_graph in (False, True):
+        with torch.cuda.stream(stream), ngf.Plan(c.desc, stream) as pl:
+            g = c.empty()
+            ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g, want_scalars=False)
+            dg = c.empty()
+            ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, dg)
+            vec = [c.empty() for _ in range(5)]
+            sc = torch.zeros(8, device="cuda", dtype=torch.float64)
+            st = ngf.pcg_state(*vec, dg, sc)
+            rhs = (-g).contiguous()
+            ngf.pcg_init(pl.handle, st, rhs)
+            ngf.pcg_solve(pl.handle, st, c.R, c.T, c.u, iters, use_graph=use_graph)
+            info = ngf.pcg_read(pl.handle, st)
+            stream.synchronize()
+            res[use_graph] = (vec[0].clone(), G.f64(rhs), G.f64(dg), info)
+    assert torch.equal(res[False][0], res[True][0])
+    x, rhs, dg, info = res[True]
+    assert info.iters_done == iters and info.status == 0
+    xo, _ = O.pcg(c.L, c.Rh, c.Th, c.uh, rhs, dg, iters)
+    assert G.rel(G.f64(x), xo) < G.TOL_PCG
+
+
+def test_register_multilevel_matches_oracle_blobs32(ngf):
+    """Config 0: 2 levels, 10 Gauss-Newton x 20 PCG; final u within 0.01
+    voxel of the oracle's, final J within 1e-4."""
+    import oracle as O
+    from paper_1804_10541_b300 import synth
+    R, T, _, w = synth.make("blobs_32", device="cuda")
+    desc = ngf.level_desc(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"])
+    N = int(np.prod(w["n"]))
+    u = torch.empty(3 * N, device="cuda")
+    opts = ngf.options(levels=w["levels"], gn_iters=10, pcg_iters=20)
+    stream = torch.cuda.Stream()
+    rep = ngf.register_multilevel(desc, opts, R, T, u, stream)
+    L = O.level(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"])
+    uo, ro = O.register_multilevel(L, w["levels"], O.gn_options(gn_iters=10, pcg_iters=20), G.f64(R), G.f64(T))
+    assert rep.status == 0 and ro.status == 0
+    assert abs(rep.J - ro.J) / ro.J < 1e-4
+    assert np.max(np.abs(G.f64(u) - uo)) / min(w["h"]) < 0.01
+    assert rep.gn_done == ro.gn_done and rep.pcg_total == ro.pcg_total
+
+
+def test_register_multilevel_host_pointers_equal_device(ngf):
+    from paper_1804_10541_b300 import synth
+    R, T, _, w = synth.make("blobs_32", device="cuda")
+    desc = ngf.level_desc(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"])
+    N = int(np.prod(w["n"]))
+    opts = ngf.options(levels=2, gn_iters=3, pcg_iters=5)
+    ud = torch.empty(3 * N, device="cuda")
+    ngf.register_multilevel(desc, opts, R, T, ud)
+    Rh, Th = R.cpu().numpy(), T.cpu().numpy()
+    uh = np.empty(3 * N, dtype=np.float32)
+    rep = ngf.register_multilevel(desc, opts, Rh, Th, uh)
+    assert rep.gn_done > 0
+    np.testing.assert_array_equal(uh, ud.cpu().numpy())
+
+
+def test_nonfinite_input_is_rejected(ngf):
+    from paper_1804_10541_b300 import synth
+    R, T, _, w = synth.make("blobs_32", device="cuda")
+    R[123] = float("nan")
+    desc = ngf.level_desc(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"])
+    u = torch.empty(3 * int(np.prod(w["n"])), device="cuda")
+    with pytest.raises(ngf.NGFError) as e:
+        ngf.register_multilevel(desc, ngf.options(levels=2, gn_iters=1, pcg_iters=1), R, T, u)
+    assert e.value.status == -4
+
+
+def test_host_pointer_rejected_by_plan_ops(ngf):
+    c = G.random_case((8, 8, 8), (1, 1, 1), (5, 5, 5))
+    with ngf.Plan(c.desc) as pl:
+        with pytest.raises(ngf.NGFError) as e:
+            ngf.gn_hessvec(pl.handle, c.R.cpu(), c.T, c.u, c.p, c.empty())
+        assert e.value.status == -1 and "device" in str(e.value)
+
+
+def test_launch_counter_counts_kernels(ngf):
+    c = G.random_case((8, 8, 8), (1, 1, 1), (5, 5, 5))
+    with ngf.Plan(c.desc) as pl:
+        before = ngf.ngf_launch_count()
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, c.empty())
+        assert ngf.ngf_launch_count() - before == 3
