@@ -315,6 +315,33 @@ def run_ours(args):
     return 0
 
 
+def run_kernel_case(args):
+    """Kernel-only driver (for profiling): `calls` gn_hessvec products on the
+    finest level of a workload, timed with CUDA events."""
+    import torch
+    from paper_1804_10541_b300 import ngf, synth
+    R, T, _, w = synth.make(args.kernel_case, device="cuda")
+    m, h, n = w["m"], w["h"], w["n"]
+    N = n[0] * n[1] * n[2]
+    desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"])
+    u, p = synth.random_fields(N, 5, amp=0.5 * min(h), device="cuda")
+    q = torch.empty(3 * N, device="cuda")
+    with ngf.Plan(desc) as pl:
+        ngf.gn_hessvec(pl.handle, R, T, u, p, q)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.calls):
+            ngf.gn_hessvec(pl.handle, R, T, u, p, q)
+        e1.record()
+        torch.cuda.synchronize()
+    M = m[0] * m[1] * m[2]
+    ms = e0.elapsed_time(e1) / args.calls
+    print(json.dumps({"kernel_case": args.kernel_case, "calls": args.calls, "ms_per_hessvec": ms,
+                      "gvoxel_s": M / ms / 1e6}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,7 +349,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", default=None, help="profile driver: gn_hessvec only on this workload")
+    ap.add_argument("--calls", type=int, default=3)
     args = ap.parse_args()
+    if args.kernel_case:
+        return run_kernel_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
