@@ -56,7 +56,10 @@ ngf_status validate_desc(const ngf_level_desc* d, std::string& why) {
     if (!(d->alpha >= 0.0) || !std::isfinite(d->alpha)) { why = "alpha must be finite and >= 0"; return NGF_EINVAL; }
     const long long M = (long long)d->m[0] * d->m[1] * d->m[2];
     const long long N = (long long)d->n[0] * d->n[1] * d->n[2];
-    if (M > (1LL << 40) || 3 * N > (1LL << 31) - 1) { why = "grid too large"; return NGF_EBOUNDS; }
+    if (M > (1LL << 31) - 1 || 3 * N > (1LL << 31) - 1) {
+        why = "grid too large: image voxels and 3 x nodes must be < 2^31";
+        return NGF_EBOUNDS;
+    }
     return NGF_OK;
 }
 

@@ -70,7 +70,8 @@ __device__ __forceinline__ void grid_sum_finish(double blocksum, double* part, u
 // Trilinear sample of T at continuous voxel coordinate (g + d) per axis, zero
 // outside; returns the value and dT/dx_l in physical units.  The cell is
 // floor(d) relative to g (displacement form), so exact knots take the forward
-// cell and an identity warp reproduces T exactly.
+// cell and an identity warp reproduces T exactly.  Voxel counts are < 2^31
+// (checked at plan creation), so offsets are 32-bit.
 __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy, int gz, float d0, float d1,
                                              float d2, float& g0, float& g1, float& g2) {
     g0 = g1 = g2 = 0.f;
@@ -79,20 +80,35 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
     const int cx = gx + (int)f0, cy = gy + (int)f1, cz = gz + (int)f2;
     if (cx < -1 || cx > P.m0 - 1 || cy < -1 || cy > P.m1 - 1 || cz < -1 || cz > P.m2 - 1) return 0.f;
     const float tx = d0 - f0, ty = d1 - f1, tz = d2 - f2;
-    const bool x0ok = cx >= 0, x1ok = cx + 1 <= P.m0 - 1;
-    const bool y0ok = cy >= 0, y1ok = cy + 1 <= P.m1 - 1;
-    const bool z0ok = cz >= 0, z1ok = cz + 1 <= P.m2 - 1;
-    const long long sy = P.m0, sz = (long long)P.m0 * P.m1;
-    const long long b = (long long)cx + sy * cy + sz * cz;
-    const float* T = P.T;
-    const float v000 = (x0ok && y0ok && z0ok) ? __ldg(T + b) : 0.f;
-    const float v100 = (x1ok && y0ok && z0ok) ? __ldg(T + b + 1) : 0.f;
-    const float v010 = (x0ok && y1ok && z0ok) ? __ldg(T + b + sy) : 0.f;
-    const float v110 = (x1ok && y1ok && z0ok) ? __ldg(T + b + sy + 1) : 0.f;
-    const float v001 = (x0ok && y0ok && z1ok) ? __ldg(T + b + sz) : 0.f;
-    const float v101 = (x1ok && y0ok && z1ok) ? __ldg(T + b + sz + 1) : 0.f;
-    const float v011 = (x0ok && y1ok && z1ok) ? __ldg(T + b + sz + sy) : 0.f;
-    const float v111 = (x1ok && y1ok && z1ok) ? __ldg(T + b + sz + sy + 1) : 0.f;
+    const int sy = P.m0, sz = P.m0 * P.m1;
+    float v000, v100, v010, v110, v001, v101, v011, v111;
+    if (cx >= 0 && cx + 1 < P.m0 && cy >= 0 && cy + 1 < P.m1 && cz >= 0 && cz + 1 < P.m2) {
+        const float* t = P.T + (cx + sy * cy + sz * cz);  // all eight corners inside
+        v000 = __ldg(t);
+        v100 = __ldg(t + 1);
+        v010 = __ldg(t + sy);
+        v110 = __ldg(t + sy + 1);
+        v001 = __ldg(t + sz);
+        v101 = __ldg(t + sz + 1);
+        v011 = __ldg(t + sz + sy);
+        v111 = __ldg(t + sz + sy + 1);
+    } else {
+        const bool x0ok = cx >= 0, x1ok = cx + 1 <= P.m0 - 1;
+        const bool y0ok = cy >= 0, y1ok = cy + 1 <= P.m1 - 1;
+        const bool z0ok = cz >= 0, z1ok = cz + 1 <= P.m2 - 1;
+        const int xa = max(cx, 0), xb = min(cx + 1, P.m0 - 1);
+        const int ya = max(cy, 0) * sy, yb = min(cy + 1, P.m1 - 1) * sy;
+        const int za = max(cz, 0) * sz, zb = min(cz + 1, P.m2 - 1) * sz;
+        const float* T = P.T;
+        v000 = (x0ok && y0ok && z0ok) ? __ldg(T + xa + ya + za) : 0.f;
+        v100 = (x1ok && y0ok && z0ok) ? __ldg(T + xb + ya + za) : 0.f;
+        v010 = (x0ok && y1ok && z0ok) ? __ldg(T + xa + yb + za) : 0.f;
+        v110 = (x1ok && y1ok && z0ok) ? __ldg(T + xb + yb + za) : 0.f;
+        v001 = (x0ok && y0ok && z1ok) ? __ldg(T + xa + ya + zb) : 0.f;
+        v101 = (x1ok && y0ok && z1ok) ? __ldg(T + xb + ya + zb) : 0.f;
+        v011 = (x0ok && y1ok && z1ok) ? __ldg(T + xa + yb + zb) : 0.f;
+        v111 = (x1ok && y1ok && z1ok) ? __ldg(T + xb + yb + zb) : 0.f;
+    }
     // lerp along x on the four (y,z) edges
     const float e00 = fmaf(tx, v100 - v000, v000);
     const float e10 = fmaf(tx, v110 - v010, v010);
@@ -116,25 +132,33 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
 //   MODE_HESS: tile partials of P^T[2 hbar dT dr^T dr (dT . P p)]       (Eq. hessMult)
 // The transposed grid conversion is completed by k_node_combine.
 //
-// Pipeline per z-step zf (one __syncthreads between stages):
-//   stage 0: node values of u (and p) interpolated in z to plane zf;
-//   stage 1: warp T and dT (and s = dT . P p) on the front-end region of zf;
-//   stage 2: residual Jacobian row rho_hat (Eqs. rho, hatRho) on plane zf-1
-//            for the halo-1 region and the products pi_i(k) = rho_hat_i(k) w_i
-//            with w = r (gradient) or w = dr s (Hessian);
-//   stage 3: on plane zf-2, t_j = sum_k pi_{j+k}(-k) over true neighbours
-//            (column j of dr^T), q_hat = qscale dT_j t_j, and its P^T
-//            contribution accumulated into two live node planes.
+// Stages (plane indices relative to the march variable zf):
+//   S0(zf+1): node values of u (and p) interpolated in z to the next plane;
+//   S1(zf)  : warp T and dT (and s = dT . P p) on the front-end region;
+//   S2(zf-1): residual Jacobian row rho_hat (Eqs. rho, hatRho) on the halo-1
+//             region and the products pi_i(k) = rho_hat_i(k) w_i with w = r
+//             (gradient) or w = dr s (Hessian): in-plane ones to shared
+//             memory, pi(0) and pi(+-z) of the owned column in registers;
+//   S3(zf-2): t_j = sum_k pi_{j+k}(-k) over true neighbours (column j of
+//             dr^T), q_hat = qscale dT_j t_j to shared memory;
+//   A(zf-3) : x-reduction of q_hat onto node columns (separable P^T);
+//   B(zf-3) : y-reduction and accumulation into two live node planes; a
+//             completed node plane is stored as this tile's partial.
+// Two barriers per plane: {S1, A} | {S2, S3, S0, B}.  S3 needs pi(-z) of
+// the next plane from S2 of the same owned column, which the same thread has
+// just computed, so it shares S2's interval.
 // ---------------------------------------------------------------------------
 template <int MODE>
 __device__ __forceinline__ void image_pass(const ImgParams& P) {
     NGF_DYNAMIC_SMEM(smraw);
     ImgSmem& S = *reinterpret_cast<ImgSmem*>(smraw);
+    constexpr bool OBJ = (MODE == MODE_OBJ), HESS = (MODE == MODE_HESS);
+    constexpr int FH = OBJ ? 1 : 2;  // front-end halo
+    constexpr int NVEC = HESS ? 6 : 3;
     const int tid = threadIdx.x;
     const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
     const int z0 = blockIdx.z * P.zc, z1 = min(P.m2, z0 + P.zc);
     const int txe = min(TX, P.m0 - xs), tye = min(TY, P.m1 - ys);
-    const int FH = (MODE == MODE_OBJ) ? 1 : 2;  // front-end halo
 
     // node box of the front-end region (z-interpolated node planes)
     const int UX0 = P.fx[max(xs - 2, 0)], UY0 = P.fy[max(ys - 2, 0)];
@@ -156,7 +180,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
         S.fy2[i] = P.fy[gy] - UY0;
         S.wy2[i] = P.wy[gy];
     }
-    if (MODE != MODE_OBJ) {
+    if (!OBJ) {
         for (int i = tid; i < TX; i += NT) S.fxb[i] = P.fx[min(xs + i, P.m0 - 1)] - BX0;
         for (int i = tid; i < TY; i += NT) S.fyb[i] = P.fy[min(ys + i, P.m1 - 1)] - BY0;
         for (int b = tid; b < nbx; b += NT) {
@@ -179,232 +203,282 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
         }
         for (int i = tid; i < 2 * 3 * NBY * NBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
     }
-    __syncthreads();
 
-    const int lx0 = tid % TX, ly0 = tid / TX;  // this thread's owned column
-    const bool own_ok = (lx0 < txe) && (ly0 < tye);
+    // ---- per-thread work descriptors, fixed for the whole march
+    const int lx0 = tid % TX, ly0 = tid / TX;  // owned column
     const int gx0 = xs + lx0, gy0 = ys + ly0;
+    const bool own_ok = (lx0 < txe) && (ly0 < tye);
+    const int box = UXn * UYn;  // S0 items: node columns of the front-end box (<= 2 per thread)
+    int s0_g[2], s0_s[2];
+    for (int k = 0; k < 2; ++k) {
+        const int i = tid + k * NT;
+        if (i < box) {
+            const int by = i / UXn, bx = i - by * UXn;
+            s0_g[k] = (UX0 + bx) + P.n0 * (UY0 + by);
+            s0_s[k] = by * UBX + bx;
+        } else {
+            s0_g[k] = 0;
+            s0_s[k] = -1;
+        }
+    }
+    int a_it[2], b_it[2];  // A items (ly, bx) and B items (by, bx), packed as row*64 + col
+    for (int k = 0; k < 2; ++k) {
+        const int i = tid + k * NT;
+        a_it[k] = (!OBJ && i < TY * nbx) ? ((i / nbx) << 6) + (i % nbx) : -1;
+        b_it[k] = (!OBJ && i < nby * nbx) ? ((i / nbx) << 6) + (i % nbx) : -1;
+    }
+    const int plane_n = P.n0 * P.n1;
+    __syncthreads();
 
     // register queues of the owned column
     float dq0[3] = {0.f, 0.f, 0.f}, dq1[3] = {0.f, 0.f, 0.f}, dq2[3] = {0.f, 0.f, 0.f};  // dT at zf, zf-1, zf-2
-    float pm_cur = 0.f, p0_cur = 0.f, pp_cur = 0.f;  // pi(-z), pi(0), pi(+z) of plane zq
-    float p0_last = 0.f, pp_last = 0.f, pp_last2 = 0.f;
+    float pm_c = 0.f, p0_c = 0.f, pp_c = 0.f;        // pi(-z), pi(0), pi(+z) of plane zf-1
+    float p0_prev = 0.f, pp_prev = 0.f, pp_prev2 = 0.f;
     double dacc = 0.0;
     int cur = BZ0;  // lower live node plane of the P^T accumulators
 
-    const int nvec = (MODE == MODE_HESS) ? 6 : 3;
-    const int zbeg = z0 - FH, zend = (MODE == MODE_OBJ) ? z1 : z1 + 1;
+    const int zbeg = z0 - FH;
+    const int fe_last = OBJ ? z1 : z1 + 1;   // last front-end plane needed
+    const int zend = OBJ ? z1 : z1 + 2;      // B of the last owned plane runs at zf = z1 + 2
 
-    for (int zf = zbeg; zf <= zend; ++zf) {
-        // ---- stage 0: node values interpolated in z to plane zf
-        const bool fe = (zf >= 0) && (zf < P.m2);
-        if (fe) {
-            const int fzz = P.fz[zf];
-            const float wzz = P.wz[zf];
-            const long long plane = (long long)P.n0 * P.n1;
-            const long long pl0 = (long long)fzz * plane;
-            const int box = UXn * UYn;
-            for (int i = tid; i < nvec * box; i += NT) {
-                const int c = i / box;
-                const int rem = i - c * box;
-                const int by = rem / UXn, bx = rem - by * UXn;
+    // S0: node values of plane zf interpolated in z into Uz
+    auto stage0 = [&](int zf) {
+        const int fzz = P.fz[zf];
+        const float wzz = P.wz[zf];
+        const int pl0 = fzz * plane_n;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (s0_s[k] < 0) continue;
+            const int o = pl0 + s0_g[k];
+#pragma unroll
+            for (int c = 0; c < NVEC; ++c) {
                 const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
-                const long long o = pl0 + (UX0 + bx) + (long long)P.n0 * (UY0 + by);
-                const float a = __ldg(src + o), b = __ldg(src + o + plane);
-                S.Uz[c][by][bx] = fmaf(wzz, b - a, a);
+                const float a = __ldg(src + o), b = __ldg(src + o + plane_n);
+                (&S.Uz[c][0][0])[s0_s[k]] = fmaf(wzz, b - a, a);
             }
         }
-        __syncthreads();
-        // ---- stage 1: warp (and s = dT . P p) on the front-end region of plane zf
+    };
+    // S1 on one column of plane zf; returns dT
+    auto stage1 = [&](int lx, int ly, int zf, float& g0, float& g1, float& g2) {
+        const int gx = xs + lx, gy = ys + ly;
+        const int li = (ly + 2) * SX2 + (lx + 2);
+        const int ax = S.fx2[lx + 2], ay = S.fy2[ly + 2];
+        const float wxv = S.wx2[lx + 2], wyv = S.wy2[ly + 2];
+        float uh[NVEC];
+#pragma unroll
+        for (int c = 0; c < NVEC; ++c) {
+            const float v00 = S.Uz[c][ay][ax], v10 = S.Uz[c][ay][ax + 1];
+            const float v01 = S.Uz[c][ay + 1][ax], v11 = S.Uz[c][ay + 1][ax + 1];
+            const float a0 = fmaf(wxv, v10 - v00, v00), a1 = fmaf(wxv, v11 - v01, v01);
+            uh[c] = fmaf(wyv, a1 - a0, a0);
+        }
+        const float tw = warp_sample(P, gx, gy, zf, uh[0] * P.ih[0], uh[1] * P.ih[1], uh[2] * P.ih[2], g0, g1, g2);
+        const int slot = zf % 3;
+        S.R[slot][li] = __ldg(P.R + (gx + P.m0 * (gy + P.m1 * zf)));
+        S.Tw[slot][li] = tw;
+        if (HESS) S.S[slot][li] = fmaf(g0, uh[NVEC - 3], fmaf(g1, uh[NVEC - 2], g2 * uh[NVEC - 1]));
+    };
+    // S2 on one column of plane zq; owned columns also return pi(-z, 0, +z)
+    auto stage2 = [&](int lx, int ly, int zq, bool owned) {
+        const int gx = xs + lx, gy = ys + ly;
+        const int li = (ly + 2) * SX2 + (lx + 2);
+        const int sc = zq % 3;
+        const int szm = (zq > 0 ? zq - 1 : zq) % 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) % 3;
+        // clamped neighbours (Eq. boundary_conditions), K order -z,-y,-x,+x,+y,+z
+        const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
+        const int ym = (gy > 0) ? li - SX2 : li, yp = (gy < P.m1 - 1) ? li + SX2 : li;
+        const float r0 = S.R[sc][li], t0 = S.Tw[sc][li];
+        const float dR[6] = {S.R[szm][li] - r0, S.R[sc][ym] - r0, S.R[sc][xm] - r0,
+                             S.R[sc][xp] - r0, S.R[sc][yp] - r0, S.R[szp][li] - r0};
+        const float dT[6] = {S.Tw[szm][li] - t0, S.Tw[sc][ym] - t0, S.Tw[sc][xm] - t0,
+                             S.Tw[sc][xp] - t0, S.Tw[sc][yp] - t0, S.Tw[szp][li] - t0};
+        const float ihs[6] = {P.ihs[2], P.ihs[1], P.ihs[0], P.ihs[0], P.ihs[1], P.ihs[2]};
+        float nn = 0.f, a2 = 0.f, b2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            nn = fmaf(dT[j] * dR[j], ihs[j], nn);
+            a2 = fmaf(dT[j] * dT[j], ihs[j], a2);
+            b2 = fmaf(dR[j] * dR[j], ihs[j], b2);
+        }
+        nn = fmaf(0.5f, nn, P.tr);   // N   = 1/2 <grad T, grad R> + tau rho
+        a2 = fmaf(0.5f, a2, P.tau2); // A^2 = ||grad T||_tau^2
+        b2 = fmaf(0.5f, b2, P.rho2); // B^2 = ||grad R||_rho^2
+        const float c1 = rsqrtf(a2 * b2);  // 1/(A B)
+        if (!HESS && owned && zq >= z0 && zq < z1) {
+            // 1 - r^2 = (A^2 B^2 - N^2)/(A^2 B^2), numerator by the Lagrange identity
+            float a[6], b[6];
+            const float ih6[6] = {P.ih[2], P.ih[1], P.ih[0], P.ih[0], P.ih[1], P.ih[2]};
+#pragma unroll
+            for (int j = 0; j < 6; ++j) { a[j] = dT[j] * ih6[j]; b[j] = dR[j] * ih6[j]; }
+            float cross = 0.f, sq = 0.f;
+#pragma unroll
+            for (int pj = 0; pj < 6; ++pj) {
+#pragma unroll
+                for (int qj = pj + 1; qj < 6; ++qj) {
+                    const float t = fmaf(a[pj], b[qj], -a[qj] * b[pj]);
+                    cross = fmaf(t, t, cross);
+                }
+                const float t = fmaf(P.rho, a[pj], -P.tau * b[pj]);
+                sq = fmaf(t, t, sq);
+            }
+            dacc += (double)(fmaf(0.25f, cross, 0.5f * sq) / (a2 * b2));
+        }
+        if (OBJ) return;
+        const float c2 = nn * c1 / a2;     // N/(A^3 B)
+        const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
+        float rh[6], rs = 0.f;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {       // Eqs. (rho), (hatRho)
+            rh[j] = hh[j] * fmaf(dR[j], c1, -dT[j] * c2);
+            rs += rh[j];
+        }
+        const float rh0 = -rs;
+        float w;
+        if (!HESS) {
+            w = nn * c1;  // r_i
+        } else {          // v_i = (dr s)_i
+            w = rh0 * S.S[sc][li];
+            w = fmaf(rh[0], S.S[szm][li], w);
+            w = fmaf(rh[1], S.S[sc][ym], w);
+            w = fmaf(rh[2], S.S[sc][xm], w);
+            w = fmaf(rh[3], S.S[sc][xp], w);
+            w = fmaf(rh[4], S.S[sc][yp], w);
+            w = fmaf(rh[5], S.S[szp][li], w);
+        }
+        const int l1 = (ly + 1) * SX1 + (lx + 1);
+        const int pb = zq & 1;
+        S.Pi[pb][0][l1] = rh[2] * w;  // pi(-x)
+        S.Pi[pb][1][l1] = rh[3] * w;  // pi(+x)
+        S.Pi[pb][2][l1] = rh[1] * w;  // pi(-y)
+        S.Pi[pb][3][l1] = rh[4] * w;  // pi(+y)
+        if (owned) { pm_c = rh[0] * w; p0_c = rh0 * w; pp_c = rh[5] * w; }
+    };
+    auto store_plane = [&](int pl) {  // node plane `pl` of this tile -> partials
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (b_it[k] < 0) continue;
+            const int by = b_it[k] >> 6, bx = b_it[k] & 63;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float& a = S.Acc[pl & 1][c][by][bx];
+                P.partial[((tile * 3 + c) * P.pbz + (pl - BZ0)) * (long long)(P.pby * P.pbx) + by * P.pbx + bx] = a;
+                a = 0.f;
+            }
+        }
+    };
+
+    if (zbeg >= 0 && zbeg < P.m2) stage0(zbeg);
+    __syncthreads();
+
+    for (int zf = zbeg; zf <= zend; ++zf) {
+        // ================= interval 1: S1(zf), A(zf-3)
         dq2[0] = dq1[0]; dq2[1] = dq1[1]; dq2[2] = dq1[2];
         dq1[0] = dq0[0]; dq1[1] = dq0[1]; dq1[2] = dq0[2];
         dq0[0] = dq0[1] = dq0[2] = 0.f;
-        if (fe) {
-            const int slot = zf % 3;
-            const int nring = ring_size(FH);
-            for (int k = tid; k < NT + nring; k += NT) {
+        if (zf >= 0 && zf < P.m2 && zf <= fe_last) {
+            if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
+            if (tid < ring_size(FH)) {
                 int lx, ly;
-                if (k < NT) { lx = k % TX; ly = k / TX; }
-                else ring_coord(k - NT, FH, lx, ly);
+                ring_coord(tid, FH, lx, ly);
                 const int gx = xs + lx, gy = ys + ly;
-                if (gx < 0 || gx >= P.m0 || gy < 0 || gy >= P.m1) continue;
-                const int li = (ly + 2) * SX2 + (lx + 2);
-                const int ax = S.fx2[lx + 2], ay = S.fy2[ly + 2];
-                const float wxv = S.wx2[lx + 2], wyv = S.wy2[ly + 2];
-                float uh[6];
-                for (int c = 0; c < nvec; ++c) {
-                    const float v00 = S.Uz[c][ay][ax], v10 = S.Uz[c][ay][ax + 1];
-                    const float v01 = S.Uz[c][ay + 1][ax], v11 = S.Uz[c][ay + 1][ax + 1];
-                    const float a0 = fmaf(wxv, v10 - v00, v00), a1 = fmaf(wxv, v11 - v01, v01);
-                    uh[c] = fmaf(wyv, a1 - a0, a0);
-                }
                 float g0, g1, g2;
-                const float tw = warp_sample(P, gx, gy, zf, uh[0] * P.ih[0], uh[1] * P.ih[1], uh[2] * P.ih[2],
-                                             g0, g1, g2);
-                const long long gi = (long long)gx + (long long)P.m0 * (gy + (long long)P.m1 * zf);
-                S.R[slot][li] = __ldg(P.R + gi);
-                S.Tw[slot][li] = tw;
-                if (MODE == MODE_HESS) S.S[slot][li] = fmaf(g0, uh[3], fmaf(g1, uh[4], g2 * uh[5]));
-                if (k < NT) { dq0[0] = g0; dq0[1] = g1; dq0[2] = g2; }
+                if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage1(lx, ly, zf, g0, g1, g2);
+            }
+        }
+        const int za = zf - 3;
+        if (!OBJ && za >= z0 && za < z1) {  // A: x-reduction of q_hat(za)
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (a_it[k] < 0) continue;
+                const int ly = a_it[k] >> 6, bx = a_it[k] & 63;
+                float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+                for (int lx = S.xr_lo[bx]; lx <= S.xr_hi[bx]; ++lx) {
+                    const float wxl = S.wx2[lx + 2];
+                    const float wx = (S.fxb[lx] == bx) ? 1.f - wxl : wxl;
+                    const int q = ly * TX + lx;
+                    r0 = fmaf(wx, S.Q[0][q], r0);
+                    r1 = fmaf(wx, S.Q[1][q], r1);
+                    r2 = fmaf(wx, S.Q[2][q], r2);
+                }
+                S.Qx[0][ly][bx] = r0;
+                S.Qx[1][ly][bx] = r1;
+                S.Qx[2][ly][bx] = r2;
             }
         }
         __syncthreads();
-        // ---- stage 2: residual Jacobian rows on plane zq = zf - 1
+        // ================= interval 2: S2(zf-1), S3(zf-2), S0(zf+1), B(zf-3)
         const int zq = zf - 1;
-        const bool st2 = (zq >= 0) && (zq < P.m2) &&
-                         ((MODE == MODE_OBJ) ? (zq >= z0 && zq < z1) : (zq >= z0 - 1 && zq <= z1));
-        pm_cur = p0_cur = pp_cur = 0.f;
-        if (st2) {
-            const int sc = zq % 3;
-            const int szm = (zq > 0 ? zq - 1 : zq) % 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) % 3;
-            const int nring = (MODE == MODE_OBJ) ? 0 : ring_size(1);
-            for (int k = tid; k < NT + nring; k += NT) {
+        pm_c = p0_c = pp_c = 0.f;
+        if (zq >= 0 && zq < P.m2 && (OBJ ? (zq >= z0 && zq < z1) : (zq >= z0 - 1 && zq <= z1))) {
+            if (gx0 < P.m0 && gy0 < P.m1) stage2(lx0, ly0, zq, true);
+            if (!OBJ && tid < ring_size(1)) {
                 int lx, ly;
-                if (k < NT) { lx = k % TX; ly = k / TX; }
-                else ring_coord(k - NT, 1, lx, ly);
+                ring_coord(tid, 1, lx, ly);
                 const int gx = xs + lx, gy = ys + ly;
-                if (gx < 0 || gx >= P.m0 || gy < 0 || gy >= P.m1) continue;
-                const int li = (ly + 2) * SX2 + (lx + 2);
-                // clamped neighbours (Eq. boundary_conditions), K order -z,-y,-x,+x,+y,+z
-                const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
-                const int ym = (gy > 0) ? li - SX2 : li, yp = (gy < P.m1 - 1) ? li + SX2 : li;
-                const float r0 = S.R[sc][li], t0 = S.Tw[sc][li];
-                const float dR[6] = {S.R[szm][li] - r0, S.R[sc][ym] - r0, S.R[sc][xm] - r0,
-                                     S.R[sc][xp] - r0, S.R[sc][yp] - r0, S.R[szp][li] - r0};
-                const float dT[6] = {S.Tw[szm][li] - t0, S.Tw[sc][ym] - t0, S.Tw[sc][xm] - t0,
-                                     S.Tw[sc][xp] - t0, S.Tw[sc][yp] - t0, S.Tw[szp][li] - t0};
-                const float ihs[6] = {P.ihs[2], P.ihs[1], P.ihs[0], P.ihs[0], P.ihs[1], P.ihs[2]};
-                float nn = 0.f, a2 = 0.f, b2 = 0.f;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    nn = fmaf(dT[j] * dR[j], ihs[j], nn);
-                    a2 = fmaf(dT[j] * dT[j], ihs[j], a2);
-                    b2 = fmaf(dR[j] * dR[j], ihs[j], b2);
-                }
-                nn = fmaf(0.5f, nn, P.tr);   // N   = 1/2 <grad T, grad R> + tau rho
-                a2 = fmaf(0.5f, a2, P.tau2); // A^2 = ||grad T||_tau^2
-                b2 = fmaf(0.5f, b2, P.rho2); // B^2 = ||grad R||_rho^2
-                const float c1 = rsqrtf(a2 * b2);  // 1/(A B)
-                if (MODE != MODE_HESS && k < NT && zq >= z0 && zq < z1) {
-                    // 1 - r^2 = (A^2 B^2 - N^2)/(A^2 B^2), numerator by the Lagrange identity
-                    float a[6], b[6];
-                    const float ih6[6] = {P.ih[2], P.ih[1], P.ih[0], P.ih[0], P.ih[1], P.ih[2]};
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) { a[j] = dT[j] * ih6[j]; b[j] = dR[j] * ih6[j]; }
-                    float cross = 0.f, sq = 0.f;
-#pragma unroll
-                    for (int pj = 0; pj < 6; ++pj) {
-#pragma unroll
-                        for (int qj = pj + 1; qj < 6; ++qj) {
-                            const float t = fmaf(a[pj], b[qj], -a[qj] * b[pj]);
-                            cross = fmaf(t, t, cross);
-                        }
-                        const float t = fmaf(P.rho, a[pj], -P.tau * b[pj]);
-                        sq = fmaf(t, t, sq);
-                    }
-                    dacc += (double)(fmaf(0.25f, cross, 0.5f * sq) / (a2 * b2));
-                }
-                if (MODE == MODE_OBJ) continue;
-                const float c2 = nn * c1 / a2;     // N/(A^3 B)
-                const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
-                float rh[6], rs = 0.f;
-#pragma unroll
-                for (int j = 0; j < 6; ++j) {       // Eqs. (rho), (hatRho)
-                    rh[j] = hh[j] * fmaf(dR[j], c1, -dT[j] * c2);
-                    rs += rh[j];
-                }
-                const float rh0 = -rs;
-                float w;
-                if (MODE == MODE_GRAD) {
-                    w = nn * c1;  // r_i
-                } else {          // v_i = (dr s)_i
-                    const float s0 = S.S[sc][li];
-                    const float sn[6] = {S.S[szm][li], S.S[sc][ym], S.S[sc][xm], S.S[sc][xp], S.S[sc][yp],
-                                         S.S[szp][li]};
-                    w = rh0 * s0;
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) w = fmaf(rh[j], sn[j], w);
-                }
-                const int l1 = (ly + 1) * SX1 + (lx + 1);
-                const int pb = zq & 1;
-                S.Pi[pb][0][l1] = rh[2] * w;  // pi(-x)
-                S.Pi[pb][1][l1] = rh[3] * w;  // pi(+x)
-                S.Pi[pb][2][l1] = rh[1] * w;  // pi(-y)
-                S.Pi[pb][3][l1] = rh[4] * w;  // pi(+y)
-                if (k < NT) { pm_cur = rh[0] * w; p0_cur = rh0 * w; pp_cur = rh[5] * w; }
+                if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage2(lx, ly, zq, false);
             }
         }
-        if (MODE == MODE_OBJ) continue;
-        __syncthreads();
-        // ---- stage 3: column sums of dr^T (masked to true neighbours), q_hat, P^T
-        const int zo = zf - 2;
-        if (zo >= z0 && zo < z1) {
-            float t = 0.f;
-            if (own_ok) {
-                const int l1 = (ly0 + 1) * SX1 + (lx0 + 1);
-                const int pb = zo & 1;
-                t = p0_last;
-                if (gx0 > 0) t += S.Pi[pb][1][l1 - 1];
-                if (gx0 < P.m0 - 1) t += S.Pi[pb][0][l1 + 1];
-                if (gy0 > 0) t += S.Pi[pb][3][l1 - SX1];
-                if (gy0 < P.m1 - 1) t += S.Pi[pb][2][l1 + SX1];
-                if (zo > 0) t += pp_last2;
-                if (zo < P.m2 - 1) t += pm_cur;
-                t *= P.qscale;
-            }
-            S.Q[0][tid] = own_ok ? dq2[0] * t : 0.f;
-            S.Q[1][tid] = own_ok ? dq2[1] * t : 0.f;
-            S.Q[2][tid] = own_ok ? dq2[2] * t : 0.f;
-            __syncthreads();
-            const int fzo = P.fz[zo] - BZ0;
-            const float wzo = P.wz[zo];
-            const int items = 3 * nby * nbx;
-            if (fzo + BZ0 > cur) {  // node plane `cur` is complete: store its partial
-                for (int i = tid; i < items; i += NT) {
-                    const int c = i / (nby * nbx), rem = i % (nby * nbx), by = rem / nbx, bx = rem % nbx;
-                    float& a = S.Acc[cur & 1][c][by][bx];
-                    P.partial[((tile * 3 + c) * P.pbz + (cur - BZ0)) * (long long)(P.pby * P.pbx) + by * P.pbx + bx] = a;
-                    a = 0.f;
+        if (!OBJ) {
+            const int zo = zf - 2;
+            if (zo >= z0 && zo < z1) {  // S3: column sums of dr^T over true neighbours
+                float t = 0.f;
+                if (own_ok) {
+                    const int l1 = (ly0 + 1) * SX1 + (lx0 + 1);
+                    const int pb = zo & 1;
+                    t = p0_prev;
+                    if (gx0 > 0) t += S.Pi[pb][1][l1 - 1];
+                    if (gx0 < P.m0 - 1) t += S.Pi[pb][0][l1 + 1];
+                    if (gy0 > 0) t += S.Pi[pb][3][l1 - SX1];
+                    if (gy0 < P.m1 - 1) t += S.Pi[pb][2][l1 + SX1];
+                    if (zo > 0) t += pp_prev2;
+                    if (zo < P.m2 - 1) t += pm_c;
+                    t *= P.qscale;
                 }
-                cur = fzo + BZ0;
+                S.Q[0][tid] = own_ok ? dq2[0] * t : 0.f;
+                S.Q[1][tid] = own_ok ? dq2[1] * t : 0.f;
+                S.Q[2][tid] = own_ok ? dq2[2] * t : 0.f;
             }
-            for (int i = tid; i < items; i += NT) {
-                const int c = i / (nby * nbx), rem = i % (nby * nbx), by = rem / nbx, bx = rem % nbx;
-                float qv = 0.f;
+            pp_prev2 = pp_prev;
+            pp_prev = pp_c;
+            p0_prev = p0_c;
+        }
+        if (zf + 1 >= 0 && zf + 1 < P.m2 && zf + 1 <= fe_last) stage0(zf + 1);
+        if (!OBJ && za >= z0 && za < z1) {  // B: y-reduction and z accumulation of plane za
+            const int fzo = P.fz[za];
+            const float wzo = P.wz[za];
+            if (fzo > cur) {  // node plane `cur` is complete
+                store_plane(cur);
+                cur = fzo;
+            }
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (b_it[k] < 0) continue;
+                const int by = b_it[k] >> 6, bx = b_it[k] & 63;
+                float q0 = 0.f, q1 = 0.f, q2 = 0.f;
                 for (int ly = S.yr_lo[by]; ly <= S.yr_hi[by]; ++ly) {
                     const float wyl = S.wy2[ly + 2];
                     const float wy = (S.fyb[ly] == by) ? 1.f - wyl : wyl;
-                    float row = 0.f;
-                    for (int lx = S.xr_lo[bx]; lx <= S.xr_hi[bx]; ++lx) {
-                        const float wxl = S.wx2[lx + 2];
-                        const float wx = (S.fxb[lx] == bx) ? 1.f - wxl : wxl;
-                        row = fmaf(wx, S.Q[c][ly * TX + lx], row);
-                    }
-                    qv = fmaf(wy, row, qv);
+                    q0 = fmaf(wy, S.Qx[0][ly][bx], q0);
+                    q1 = fmaf(wy, S.Qx[1][ly][bx], q1);
+                    q2 = fmaf(wy, S.Qx[2][ly][bx], q2);
                 }
-                S.Acc[cur & 1][c][by][bx] = fmaf(1.f - wzo, qv, S.Acc[cur & 1][c][by][bx]);
-                S.Acc[(cur + 1) & 1][c][by][bx] = fmaf(wzo, qv, S.Acc[(cur + 1) & 1][c][by][bx]);
+                const int lo = cur & 1, hi = (cur + 1) & 1;
+                S.Acc[lo][0][by][bx] = fmaf(1.f - wzo, q0, S.Acc[lo][0][by][bx]);
+                S.Acc[lo][1][by][bx] = fmaf(1.f - wzo, q1, S.Acc[lo][1][by][bx]);
+                S.Acc[lo][2][by][bx] = fmaf(1.f - wzo, q2, S.Acc[lo][2][by][bx]);
+                S.Acc[hi][0][by][bx] = fmaf(wzo, q0, S.Acc[hi][0][by][bx]);
+                S.Acc[hi][1][by][bx] = fmaf(wzo, q1, S.Acc[hi][1][by][bx]);
+                S.Acc[hi][2][by][bx] = fmaf(wzo, q2, S.Acc[hi][2][by][bx]);
             }
         }
-        // advance the z queues of pi
-        pp_last2 = pp_last;
-        pp_last = pp_cur;
-        p0_last = p0_cur;
+        __syncthreads();
     }
 
-    if (MODE != MODE_OBJ) {
-        // store the two live node planes
-        const int items = 3 * nby * nbx;
-        for (int pl = cur; pl <= cur + 1; ++pl) {
-            for (int i = tid; i < items; i += NT) {
-                const int c = i / (nby * nbx), rem = i % (nby * nbx), by = rem / nbx, bx = rem % nbx;
-                P.partial[((tile * 3 + c) * P.pbz + (pl - BZ0)) * (long long)(P.pby * P.pbx) + by * P.pbx + bx] =
-                    S.Acc[pl & 1][c][by][bx];
-            }
-        }
+    if (!OBJ) {  // store the two live node planes
+        store_plane(cur);
+        store_plane(cur + 1);
     }
-    if (MODE != MODE_HESS) {
-        __syncthreads();
+    if (!HESS) {
         const double bs = block_sum(dacc, S.red);
         const int nblocks = gridDim.x * gridDim.y * gridDim.z;
         grid_sum_finish(bs, P.dpart, P.dcount, P.dout, P.hbar, S.red, nblocks, (int)tile);

@@ -67,6 +67,7 @@ struct ImgSmem {
     float Pi[2][4][R1N];        // pi(-x), pi(+x), pi(-y), pi(+y) of the halo-1 region
     float Uz[6][UBY][UBX];      // u (and p) interpolated to the current plane in z
     float Q[3][R0N];            // q_hat of the owned columns
+    float Qx[3][TY][NBX];       // q_hat reduced onto node columns in x
     float Acc[2][3][NBY][NBX];  // node-plane accumulators of P^T (two live planes)
     float wx2[SX2], wy2[SY2];
     int fx2[SX2], fy2[SY2];     // node floor relative to the Uz box

@@ -164,17 +164,23 @@ class _Lung:
             lung = lung + _step(_ellipsoid_depth(X, Y, Z, c, a), w)
         v = v - 890.0 * lung
         ves = torch.zeros_like(v)
-        for p, q, rad in self.segs:
-            bl = np.minimum(p, q) - rad - 2.0
-            bh = np.maximum(p, q) + rad + 2.0
-            if np.any(bh < lo) or np.any(bl > hi):
-                continue
-            d = q - p
-            L2 = float(d @ d)
-            t = ((X - p[0]) * d[0] + (Y - p[1]) * d[1] + (Z - p[2]) * d[2]) / L2
-            t = t.clamp(0.0, 1.0)
-            dist = torch.sqrt((X - p[0] - t * d[0]) ** 2 + (Y - p[1] - t * d[1]) ** 2 + (Z - p[2] - t * d[2]) ** 2)
-            ves = torch.maximum(ves, _step(rad - dist, 0.3))
+        sel = [sg for sg in self.segs
+               if not (np.any(np.maximum(sg[0], sg[1]) + sg[2] + 2.0 < lo) or
+                       np.any(np.minimum(sg[0], sg[1]) - sg[2] - 2.0 > hi))]
+        if sel:
+            dev, dt = v.device, v.dtype
+            P0 = torch.tensor(np.stack([sg[0] for sg in sel]), device=dev, dtype=dt)
+            Dv = torch.tensor(np.stack([sg[1] - sg[0] for sg in sel]), device=dev, dtype=dt)
+            rad = torch.tensor([sg[2] for sg in sel], device=dev, dtype=dt)
+            L2 = (Dv * Dv).sum(1)
+            Xe, Ye, Ze = X.unsqueeze(0), Y.unsqueeze(0), Z.unsqueeze(0)
+            for c0 in range(0, len(sel), 32):  # segments in batches: one capsule distance each
+                sl = slice(c0, c0 + 32)
+                px, py, pz = (P0[sl, a].view(-1, 1, 1, 1) for a in range(3))
+                dx, dy, dz = (Dv[sl, a].view(-1, 1, 1, 1) for a in range(3))
+                t = (((Xe - px) * dx + (Ye - py) * dy + (Ze - pz) * dz) / L2[sl].view(-1, 1, 1, 1)).clamp(0.0, 1.0)
+                dist = torch.sqrt((Xe - px - t * dx) ** 2 + (Ye - py - t * dy) ** 2 + (Ze - pz - t * dz) ** 2)
+                ves = torch.maximum(ves, _step(rad[sl].view(-1, 1, 1, 1) - dist, 0.3).amax(0))
         v = v + 890.0 * ves * lung
         return v.clamp(-1000.0, 400.0)
 
