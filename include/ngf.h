@@ -199,6 +199,32 @@ ngf_status register_multilevel(const ngf_level_desc* finest, const ngf_options* 
                                const float* R, const float* T, float* u_out,
                                ngf_report* report, void* cuda_stream);
 
+/* ---- objective without any allocation ----------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: code whose device memory is owned
+ * by a framework's pool, real-time loops in which an allocation (which can
+ * synchronise the device) is not allowed, plugins that must leave the host
+ * process's allocator alone.  It computes the same D and S as ngf_objective
+ * without a plan and calls no cudaMalloc, cudaFree or allocating routine:
+ * its grid-conversion tables and float64 reduction partials live in one
+ * fixed file-scope device array of about 225 KB, which every GPU that loads
+ * this library holds until the process exits.
+ *  - The first call on a device looks up that array's device address and
+ *    raises the image kernel's shared-memory limit; make this first call
+ *    before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents (every
+ *    call clears what must start at zero); calls that overlap on the GPU, on
+ *    one device, race and give wrong results.
+ *  - Limits: at most NGF_NOALLOC_MAX_AXIS image cells per axis and at most
+ *    NGF_NOALLOC_MAX_BLOCKS thread blocks of the image pass (about 6e8
+ *    voxels); larger problems return NGF_EBOUNDS with a message.
+ * R, T, u: device arrays as for ngf_objective; dev_DS: device, 2 doubles
+ * (D, S); enqueued on cuda_stream, no synchronisation. */
+#define NGF_NOALLOC_MAX_AXIS 4096
+#define NGF_NOALLOC_MAX_BLOCKS 16384
+ngf_status ngf_objective_noalloc(const ngf_level_desc* desc, const float* R, const float* T,
+                                 const float* u, double* dev_DS, void* cuda_stream);
+
 /* ---- measurement ------------------------------------------------------
  * When enabled, the plan records a CUDA event pair on its stream around every
  * launch of its image-grid kernels issued outside stream capture.

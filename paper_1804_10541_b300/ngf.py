@@ -22,7 +22,7 @@ NGF_PCG_NSCALARS = 8
 EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_last_error", "ngf_objective",
            "ngf_objective_dev", "ngf_gradient", "ngf_gradient_dev", "gn_hessvec", "curvature_apply",
            "ngf_gn_diagonal", "pcg_init", "pcg_step", "pcg_solve", "pcg_read", "register_multilevel",
-           "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count"]
+           "ngf_objective_noalloc", "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count"]
 
 
 class LevelDesc(C.Structure):
@@ -76,6 +76,7 @@ def declare(lib):
         "pcg_solve": [P, C.POINTER(PcgState), VP, VP, VP, I32, I32],
         "pcg_read": [P, C.POINTER(PcgState), C.POINTER(PcgInfo)],
         "register_multilevel": [C.POINTER(LevelDesc), C.POINTER(Options), VP, VP, VP, C.POINTER(Report), VP],
+        "ngf_objective_noalloc": [C.POINTER(LevelDesc), VP, VP, VP, VP, VP],
         "ngf_profile_enable": [P, I32],
         "ngf_profile_read": [P, I32, D, C.POINTER(C.c_int64)],
     }
@@ -163,6 +164,12 @@ def ngf_objective(plan, R, T, u):
 
 def ngf_objective_dev(plan, R, T, u, dev_DS):
     _check(lib.ngf_objective_dev(plan, _ptr(R), _ptr(T), _ptr(u), _ptr(dev_DS)), plan)
+
+
+def ngf_objective_noalloc(desc, R, T, u, dev_DS, stream=None):
+    """D, S into dev_DS (device, 2 doubles) without a plan and without any
+    device allocation (see include/ngf.h for who needs this and its limits)."""
+    _check(lib.ngf_objective_noalloc(C.byref(desc), _ptr(R), _ptr(T), _ptr(u), _ptr(dev_DS), _stream(stream)))
 
 
 def ngf_gradient(plan, R, T, u, grad, want_scalars=True):
