@@ -317,6 +317,9 @@ NodeGeom node_geom(const Plan* p) {
     G.n2 = p->n[2];
     G.N = p->N;
     for (int a = 0; a < 3; ++a) G.ihy2[a] = (float)(1.0 / (p->hy[a] * p->hy[a]));
+    G.fN = make_fastdiv((unsigned int)p->N);
+    G.fplane = make_fastdiv((unsigned int)(p->n[0] * p->n[1]));
+    G.fn0 = make_fastdiv((unsigned int)p->n[0]);
     return G;
 }
 

@@ -221,12 +221,19 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
             s0_s[k] = -1;
         }
     }
-    int a_it[2], b_it[2];  // A items (ly, bx) and B items (by, bx), packed as row*64 + col
+    // A items (ly, bx) and B items (by, bx), packed as row*64 + col.  Optional
+    // work is spread over disjoint thread ranges so that both barrier intervals
+    // stay balanced: A from thread 0 while the front-end ring sits on the last
+    // threads; B right after the S0 items while the Jacobian ring sits on the
+    // last threads.
+    int a_it[2], b_it[2];
+    const int b_rot = (tid + NT - (box % NT)) % NT;
     for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * NT;
+        const int i = tid + k * NT, j = b_rot + k * NT;
         a_it[k] = (!OBJ && i < TY * nbx) ? ((i / nbx) << 6) + (i % nbx) : -1;
-        b_it[k] = (!OBJ && i < nby * nbx) ? ((i / nbx) << 6) + (i % nbx) : -1;
+        b_it[k] = (!OBJ && j < nby * nbx) ? ((j / nbx) << 6) + (j % nbx) : -1;
     }
+    constexpr int RING1 = ring_size(FH), RING2 = ring_size(1);
     const int plane_n = P.n0 * P.n1;
     __syncthreads();
 
@@ -377,9 +384,9 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
         dq0[0] = dq0[1] = dq0[2] = 0.f;
         if (zf >= 0 && zf < P.m2 && zf <= fe_last) {
             if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
-            if (tid < ring_size(FH)) {
+            if (tid >= NT - RING1) {
                 int lx, ly;
-                ring_coord(tid, FH, lx, ly);
+                ring_coord(tid - (NT - RING1), FH, lx, ly);
                 const int gx = xs + lx, gy = ys + ly;
                 float g0, g1, g2;
                 if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage1(lx, ly, zf, g0, g1, g2);
@@ -411,9 +418,9 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
         pm_c = p0_c = pp_c = 0.f;
         if (zq >= 0 && zq < P.m2 && (OBJ ? (zq >= z0 && zq < z1) : (zq >= z0 - 1 && zq <= z1))) {
             if (gx0 < P.m0 && gy0 < P.m1) stage2(lx0, ly0, zq, true);
-            if (!OBJ && tid < ring_size(1)) {
+            if (!OBJ && tid >= NT - RING2) {
                 int lx, ly;
-                ring_coord(tid, 1, lx, ly);
+                ring_coord(tid - (NT - RING2), 1, lx, ly);
                 const int gx = xs + lx, gy = ys + ly;
                 if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage2(lx, ly, zq, false);
             }
@@ -690,28 +697,43 @@ __global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) {
 // nodal kernels
 // ---------------------------------------------------------------------------
 
+// coordinates of element i of a 3 x N nodal field (component-major, x fastest)
+__device__ __forceinline__ void node_coords(unsigned int i, const NodeGeom& G, int& c, int& n, int& ix, int& iy,
+                                            int& iz) {
+    c = (int)fdiv(i, G.fN);
+    n = (int)(i - (unsigned int)c * (unsigned int)G.N);
+    iz = (int)fdiv((unsigned int)n, G.fplane);
+    const int rem = n - iz * G.n0 * G.n1;
+    iy = (int)fdiv((unsigned int)rem, G.fn0);
+    ix = rem - iy * G.n0;
+}
+
+// clamped 7-point Laplacian of component array xc at node (ix, iy, iz)
+__device__ __forceinline__ float lap_at(const float* __restrict__ xc, const NodeGeom& G, int n, int ix, int iy, int iz) {
+    const int sy = G.n0, sz = G.n0 * G.n1;
+    const float v = xc[n];
+    const float xm = xc[ix > 0 ? n - 1 : n], xp = xc[ix < G.n0 - 1 ? n + 1 : n];
+    const float ym = xc[iy > 0 ? n - sy : n], yp = xc[iy < G.n1 - 1 ? n + sy : n];
+    const float zm = xc[iz > 0 ? n - sz : n], zp = xc[iz < G.n2 - 1 ? n + sz : n];
+    return (xm - 2.f * v + xp) * G.ihy2[0] + (ym - 2.f * v + yp) * G.ihy2[1] + (zm - 2.f * v + zp) * G.ihy2[2];
+}
+
 // L = Lap x per component (Eq. laplace_discretized, clamped Neumann
-// neighbours); optional S = scale * sum L^2 (deterministic float64).
+// neighbours); optional S = scale * sum L^2 (deterministic).
 __global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L,
                                             double* part, unsigned int* count, double* out, double scale) {
     __shared__ double red[NT];
-    double acc = 0.0;
-    const long long total = 3 * G.N;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
-        const long long c = i / G.N, n = i - c * G.N;
-        const int ix = (int)(n % G.n0), iy = (int)((n / G.n0) % G.n1), iz = (int)(n / ((long long)G.n0 * G.n1));
-        const float* xc = x + c * G.N;
-        const float v = xc[n];
-        const long long sy = G.n0, sz = (long long)G.n0 * G.n1;
-        const float xm = xc[ix > 0 ? n - 1 : n], xp = xc[ix < G.n0 - 1 ? n + 1 : n];
-        const float ym = xc[iy > 0 ? n - sy : n], yp = xc[iy < G.n1 - 1 ? n + sy : n];
-        const float zm = xc[iz > 0 ? n - sz : n], zp = xc[iz < G.n2 - 1 ? n + sz : n];
-        const float l = (xm - 2.f * v + xp) * G.ihy2[0] + (ym - 2.f * v + yp) * G.ihy2[1] + (zm - 2.f * v + zp) * G.ihy2[2];
+    DFAcc acc;
+    const unsigned int total = 3u * (unsigned int)G.N;
+    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < total; i += gridDim.x * NT) {
+        int c, n, ix, iy, iz;
+        node_coords(i, G, c, n, ix, iy, iz);
+        const float l = lap_at(x + (size_t)c * G.N, G, n, ix, iy, iz);
         L[i] = l;
-        acc += (double)l * (double)l;
+        acc.add_prod(l, l);
     }
     if (out) {
-        const double bs = block_sum(acc, red);
+        const double bs = block_sum(acc.value(), red);
         grid_sum_finish(bs, part, count, out, scale, red, gridDim.x, blockIdx.x);
     }
 }
@@ -720,13 +742,13 @@ __global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict_
 //           + alpha 2 hbar^y (Lap L)_{c,n}   or   + alpha 2 hbar^y cdiag_n
 __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
     __shared__ double red[NT];
-    double acc = 0.0;
+    DFAcc acc;
     const NodeGeom& G = P.G;
-    const long long total = 3 * G.N;
+    const unsigned int total = 3u * (unsigned int)G.N;
     const long long box = (long long)P.pbx * P.pby * P.pbz;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
-        const long long c = i / G.N, n = i - c * G.N;
-        const int ix = (int)(n % G.n0), iy = (int)((n / G.n0) % G.n1), iz = (int)(n / ((long long)G.n0 * G.n1));
+    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < total; i += gridDim.x * NT) {
+        int c, n, ix, iy, iz;
+        node_coords(i, G, c, n, ix, iy, iz);
         float s = 0.f;
         for (int tz = P.zlo[iz]; tz <= P.zhi[iz]; ++tz) {
             const int bz = iz - P.zb0[tz];
@@ -735,27 +757,17 @@ __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
                 for (int tx = P.xlo[ix]; tx <= P.xhi[ix]; ++tx) {
                     const int bx = ix - P.xb0[tx];
                     const long long t = ((long long)tz * P.nty + ty) * P.ntx + tx;
-                    s += __ldg(P.partial + (t * 3 + c) * box + ((long long)bz * P.pby + by) * P.pbx + bx);
+                    s += __ldg(P.partial + (t * 3 + c) * box + (bz * P.pby + by) * P.pbx + bx);
                 }
             }
         }
-        if (P.L) {
-            const float* Lc = P.L + c * G.N;
-            const long long sy = G.n0, sz = (long long)G.n0 * G.n1;
-            const float v = Lc[n];
-            const float xm = Lc[ix > 0 ? n - 1 : n], xp = Lc[ix < G.n0 - 1 ? n + 1 : n];
-            const float ym = Lc[iy > 0 ? n - sy : n], yp = Lc[iy < G.n1 - 1 ? n + sy : n];
-            const float zm = Lc[iz > 0 ? n - sz : n], zp = Lc[iz < G.n2 - 1 ? n + sz : n];
-            const float l2 = (xm - 2.f * v + xp) * G.ihy2[0] + (ym - 2.f * v + yp) * G.ihy2[1] +
-                             (zm - 2.f * v + zp) * G.ihy2[2];
-            s = fmaf(P.cscale, l2, s);
-        }
+        if (P.L) s = fmaf(P.cscale, lap_at(P.L + (size_t)c * G.N, G, n, ix, iy, iz), s);
         if (P.cdiag) s = fmaf(P.cscale, P.cdiag[n], s);
         P.out[i] = s;
-        if (P.dotw) acc += (double)s * (double)P.dotw[i];
+        if (P.dotw) acc.add_prod(s, P.dotw[i]);
     }
     if (P.dout) {
-        const double bs = block_sum(acc, red);
+        const double bs = block_sum(acc.value(), red);
         grid_sum_finish(bs, P.dpart, P.dcount, P.dout, 1.0, red, gridDim.x, blockIdx.x);
     }
 }
@@ -763,24 +775,18 @@ __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
 // q = scale * Lap(L) with L = Lap p, no partials (curvature_apply)
 __global__ void __launch_bounds__(NT) k_lap2(NodeGeom G, const float* __restrict__ L, float* __restrict__ q,
                                              float scale) {
-    const long long total = 3 * G.N;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
-        const long long c = i / G.N, n = i - c * G.N;
-        const int ix = (int)(n % G.n0), iy = (int)((n / G.n0) % G.n1), iz = (int)(n / ((long long)G.n0 * G.n1));
-        const float* Lc = L + c * G.N;
-        const long long sy = G.n0, sz = (long long)G.n0 * G.n1;
-        const float v = Lc[n];
-        const float xm = Lc[ix > 0 ? n - 1 : n], xp = Lc[ix < G.n0 - 1 ? n + 1 : n];
-        const float ym = Lc[iy > 0 ? n - sy : n], yp = Lc[iy < G.n1 - 1 ? n + sy : n];
-        const float zm = Lc[iz > 0 ? n - sz : n], zp = Lc[iz < G.n2 - 1 ? n + sz : n];
-        q[i] = scale * ((xm - 2.f * v + xp) * G.ihy2[0] + (ym - 2.f * v + yp) * G.ihy2[1] + (zm - 2.f * v + zp) * G.ihy2[2]);
+    const unsigned int total = 3u * (unsigned int)G.N;
+    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < total; i += gridDim.x * NT) {
+        int c, n, ix, iy, iz;
+        node_coords(i, G, c, n, ix, iy, iz);
+        q[i] = scale * lap_at(L + (size_t)c * G.N, G, n, ix, iy, iz);
     }
 }
 
 // ---------------------------------------------------------------------------
 // PCG (Sec. 2.3.1)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float minv(const float* diag, long long i) {
+__device__ __forceinline__ float minv(const float* diag, unsigned int i) {
     const float dv = diag[i];
     return dv > 0.f ? 1.f / dv : 0.f;
 }
@@ -817,19 +823,20 @@ __device__ __forceinline__ bool grid_sum2(double a, double b, double* part, unsi
 
 __global__ void __launch_bounds__(NT) k_pcg_init(PcgParams P) {
     __shared__ double red[NT];
-    double a = 0.0, b = 0.0;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < P.n; i += (long long)gridDim.x * NT) {
+    DFAcc a, b;
+    const unsigned int n = (unsigned int)P.n;
+    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
         const float rv = P.rhs[i];
         const float zv = rv * minv(P.diag, i);
         P.x[i] = 0.f;
         P.r[i] = rv;
         P.z[i] = zv;
         P.d[i] = zv;
-        a += (double)rv * (double)zv;
-        b += (double)rv * (double)rv;
+        a.add_prod(rv, zv);
+        b.add_prod(rv, rv);
     }
     double A, B;
-    if (grid_sum2(a, b, P.part, P.count, red, A, B)) {
+    if (grid_sum2(a.value(), b.value(), P.part, P.count, red, A, B)) {
         P.sc[PS_DELTA] = A;
         P.sc[PS_RR] = B;
         P.sc[PS_BB] = B;
@@ -852,21 +859,22 @@ __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
     const double delta = P.sc[PS_DELTA];
     const bool active = (st == 0.0) && (dq > 0.0) && isfinite(dq);
     const float a = active ? (float)(delta / dq) : 0.f;
-    double sa = 0.0, sb = 0.0;
+    DFAcc sa, sb;
     if (active) {
-        for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < P.n; i += (long long)gridDim.x * NT) {
+        const unsigned int n = (unsigned int)P.n;
+        for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
             const float dv = P.d[i];
             P.x[i] = fmaf(a, dv, P.x[i]);
             const float rv = fmaf(-a, P.q[i], P.r[i]);
             P.r[i] = rv;
             const float zv = rv * minv(P.diag, i);
             P.z[i] = zv;
-            sa += (double)rv * (double)zv;
-            sb += (double)rv * (double)rv;
+            sa.add_prod(rv, zv);
+            sb.add_prod(rv, rv);
         }
     }
     double A, B;
-    if (grid_sum2(sa, sb, P.part, P.count, red, A, B)) {
+    if (grid_sum2(sa.value(), sb.value(), P.part, P.count, red, A, B)) {
         if (st != 0.0) return;
         if (!active) {
             P.sc[PS_STATUS] = 2.0;
@@ -885,8 +893,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
 __global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) {
     if (P.sc[PS_STATUS] != 0.0) return;
     const float beta = (float)P.sc[PS_BETA];
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < P.n; i += (long long)gridDim.x * NT)
-        P.d[i] = fmaf(beta, P.d[i], P.z[i]);
+    const unsigned int n = (unsigned int)P.n;
+    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) P.d[i] = fmaf(beta, P.d[i], P.z[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -895,10 +903,10 @@ __global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) {
 __global__ void __launch_bounds__(NT) k_dot(long long n, const float* __restrict__ a, const float* __restrict__ b,
                                             double* part, unsigned int* count, double* out) {
     __shared__ double red[NT];
-    double acc = 0.0;
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
-        acc += (double)a[i] * (double)b[i];
-    const double bs = block_sum(acc, red);
+    DFAcc acc;
+    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < (unsigned int)n; i += gridDim.x * NT)
+        acc.add_prod(a[i], b[i]);
+    const double bs = block_sum(acc.value(), red);
     grid_sum_finish(bs, part, count, out, 1.0, red, gridDim.x, blockIdx.x);
 }
 

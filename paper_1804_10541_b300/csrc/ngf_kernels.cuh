@@ -86,10 +86,51 @@ struct DiagSmem {
     int fx1[SX1], fy1[SY1];     // node floor relative to the Uz (= partial) box
 };
 
+// Division by an invariant 32-bit divisor d >= 1 by multiply and shift
+// (Granlund-Montgomery): n / d = (t + ((n - t) >> 1)) >> s, t = umulhi(n, m).
+struct FastDiv {
+    unsigned int d, m, s;
+};
+
+inline FastDiv make_fastdiv(unsigned int d) {
+    FastDiv f{d, 0u, 0u};
+    if (d <= 1) return f;
+    unsigned int l = 0;
+    while ((1ull << l) < d) ++l;  // smallest l with 2^l >= d
+    f.m = (unsigned int)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s = l - 1;
+    return f;
+}
+
+__device__ __forceinline__ unsigned int fdiv(unsigned int n, const FastDiv& f) {
+    if (f.d <= 1) return n;
+    const unsigned int t = __umulhi(n, f.m);
+    return (t + ((n - t) >> 1)) >> f.s;
+}
+
 struct NodeGeom {
     int n0, n1, n2;
     long long N;
-    float ihy2[3];  // 1/hy^2
+    float ihy2[3];         // 1/hy^2
+    FastDiv fN, fplane, fn0;  // division by N, n0*n1, n0
+};
+
+// Per-thread accumulator of a sum of float products: each product is split
+// exactly into p + e (p = a*b rounded, e = fma(a, b, -p)) and p is added with
+// an error-free two-sum, so the pair (hi, lo) carries about twice float
+// precision; thread results are then combined in float64.
+struct DFAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        const float s = __fadd_rn(hi, p);
+        const float bb = __fsub_rn(s, hi);
+        const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+        hi = s;
+        lo = __fadd_rn(lo, __fadd_rn(err, e));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 struct CombineParams {
