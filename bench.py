@@ -239,6 +239,18 @@ def run_ours(args):
     t_max, vox_all = reduce_max_sum(t_local, voxels, ws)
     value = vox_all / t_max / 1e9
 
+    # fixed cost of a registration call (allocations, plans, pyramid, objective
+    # evaluations): the same call with zero Gauss-Newton steps
+    opts0 = ngf.options(levels=levels, gn_iters=0, pcg_iters=PCG_ITERS, use_graph=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ngf.register_multilevel(desc, opts0, R, T, u, stream)
+        e0.record(stream)
+        ngf.register_multilevel(desc, opts0, R, T, u, stream)
+        e1.record(stream)
+    stream.synchronize()
+    fixed_ms = e0.elapsed_time(e1)
+
     # ---- end to end through the public API with host buffers (pinned)
     Rp = torch.empty(M, dtype=torch.float32, pin_memory=True)
     Tp = torch.empty(M, dtype=torch.float32, pin_memory=True)
@@ -306,7 +318,8 @@ def run_ours(args):
                                        f"one step = one full register_multilevel",
                            "parallelism": f"replicas x{ws}", "l2": "flushed before every step (256 MB write)",
                            "registration_ms": 1e3 * t_max / args.steps, "final_J": r0.J,
-                           "gn_done": r0.gn_done, "pcg_total": r0.pcg_total, "ls_trials": r0.ls_trials},
+                           "gn_done": r0.gn_done, "pcg_total": r0.pcg_total, "ls_trials": r0.ls_trials,
+                           "fixed_ms_per_registration": fixed_ms},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)

@@ -295,8 +295,9 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
 
     p->img_blocks = (int)p->g0.tiles();
     p->diag_blocks = (int)p->g1.tiles();
-    p->node_blocks = grid_for(3 * p->N, 4 * sms);
-    p->dpart_len = 2 * (size_t)std::max({p->img_blocks, p->diag_blocks, p->node_blocks, 8 * sms});
+    p->node_blocks = grid_for(3 * p->N, 4 * sms);   // element-wise vector kernels
+    p->node1_blocks = grid_for(p->N, 16 * sms);     // one thread per node
+    p->dpart_len = 2 * (size_t)std::max({p->img_blocks, p->diag_blocks, p->node_blocks, p->node1_blocks, 8 * sms});
     NGF_CU(p, cudaMalloc(&p->dsc, 16 * sizeof(double)), "cudaMalloc(scalars)");
     NGF_CU(p, cudaMemset(p->dsc, 0, 16 * sizeof(double)), "cudaMemset(scalars)");
     NGF_CU(p, cudaMalloc(&p->dpart, p->dpart_len * sizeof(double)), "cudaMalloc(partials64)");
@@ -405,7 +406,7 @@ ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* 
     NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
     NGF_CU(p, launch(k_image_obj, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_obj");
     NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
-    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
+    NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
                      p->dcount, dS, p->hbary),
            "k_lap");
     return NGF_OK;
@@ -417,17 +418,17 @@ ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u
     NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
     NGF_CU(p, launch(k_image_grad, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_grad");
     NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
-    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
+    NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
                      p->dcount, dS, p->hbary),
            "k_lap");
     CombineParams C = combine_params(p, p->g0, g, p->L, nullptr, nullptr, nullptr);
-    NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+    NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
 }
 
 ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u, const float* pv, float* q,
                         const float* dotw, double* dout) {
-    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), pv, p->L, p->dpart,
+    NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), pv, p->L, p->dpart,
                      p->dcount, (double*)nullptr, 0.0),
            "k_lap");
     ImgParams P = img_params(p, R, T, u, pv, MODE_HESS, p->g0, nullptr);
@@ -435,7 +436,7 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
     NGF_CU(p, launch(k_image_hess, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_hess");
     NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g0, q, p->L, nullptr, dotw, dout);
-    NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+    NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
 }
 
@@ -445,7 +446,7 @@ ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u
     NGF_CU(p, launch(k_diag, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P), "k_diag");
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g1, diag, nullptr, p->cdiag, nullptr, nullptr);
-    NGF_CU(p, launch(k_node_combine, dim3(p->node_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+    NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
 }
 
@@ -571,7 +572,7 @@ ngf_status curvature_apply(ngf_plan* plan, const float* pv, float* q, double* Sp
     NGF_TRY(need_dev(p, {{pv, "p"}}));
     if (q && !is_device_ptr(q)) return set_error(p, NGF_EINVAL, "q must be a device pointer");
     if (q && (const void*)q == (const void*)pv) return set_error(p, NGF_EINVAL, "q must not alias p");
-    NGF_CU(p, launch(k_lap, dim3(p->node_blocks), dim3(NT), 0, p->stream, node_geom(p), pv, p->L, p->dpart, p->dcount,
+    NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), pv, p->L, p->dpart, p->dcount,
                      Sp ? p->dsc + 1 : (double*)nullptr, p->hbary),
            "k_lap");
     if (q)

@@ -331,7 +331,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
             dacc += (double)(fmaf(0.25f, cross, 0.5f * sq) / (a2 * b2));
         }
         if (OBJ) return;
-        const float c2 = nn * c1 / a2;     // N/(A^3 B)
+        const float c2 = __fdividef(nn * c1, a2);  // N/(A^3 B)
         const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
         float rh[6], rs = 0.f;
 #pragma unroll
@@ -398,18 +398,16 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
             for (int k = 0; k < 2; ++k) {
                 if (a_it[k] < 0) continue;
                 const int ly = a_it[k] >> 6, bx = a_it[k] & 63;
-                float r0 = 0.f, r1 = 0.f, r2 = 0.f;
+                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int lx = S.xr_lo[bx]; lx <= S.xr_hi[bx]; ++lx) {
                     const float wxl = S.wx2[lx + 2];
                     const float wx = (S.fxb[lx] == bx) ? 1.f - wxl : wxl;
-                    const int q = ly * TX + lx;
-                    r0 = fmaf(wx, S.Q[0][q], r0);
-                    r1 = fmaf(wx, S.Q[1][q], r1);
-                    r2 = fmaf(wx, S.Q[2][q], r2);
+                    const float4 q = *reinterpret_cast<const float4*>(S.Q4[ly * TX + lx]);
+                    r.x = fmaf(wx, q.x, r.x);
+                    r.y = fmaf(wx, q.y, r.y);
+                    r.z = fmaf(wx, q.z, r.z);
                 }
-                S.Qx[0][ly][bx] = r0;
-                S.Qx[1][ly][bx] = r1;
-                S.Qx[2][ly][bx] = r2;
+                *reinterpret_cast<float4*>(S.Qx4[ly][bx]) = r;
             }
         }
         __syncthreads();
@@ -441,9 +439,8 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
                     if (zo < P.m2 - 1) t += pm_c;
                     t *= P.qscale;
                 }
-                S.Q[0][tid] = own_ok ? dq2[0] * t : 0.f;
-                S.Q[1][tid] = own_ok ? dq2[1] * t : 0.f;
-                S.Q[2][tid] = own_ok ? dq2[2] * t : 0.f;
+                *reinterpret_cast<float4*>(S.Q4[tid]) =
+                    own_ok ? make_float4(dq2[0] * t, dq2[1] * t, dq2[2] * t, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             pp_prev2 = pp_prev;
             pp_prev = pp_c;
@@ -465,9 +462,10 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
                 for (int ly = S.yr_lo[by]; ly <= S.yr_hi[by]; ++ly) {
                     const float wyl = S.wy2[ly + 2];
                     const float wy = (S.fyb[ly] == by) ? 1.f - wyl : wyl;
-                    q0 = fmaf(wy, S.Qx[0][ly][bx], q0);
-                    q1 = fmaf(wy, S.Qx[1][ly][bx], q1);
-                    q2 = fmaf(wy, S.Qx[2][ly][bx], q2);
+                    const float4 q = *reinterpret_cast<const float4*>(S.Qx4[ly][bx]);
+                    q0 = fmaf(wy, q.x, q0);
+                    q1 = fmaf(wy, q.y, q1);
+                    q2 = fmaf(wy, q.z, q2);
                 }
                 const int lo = cur & 1, hi = (cur + 1) & 1;
                 S.Acc[lo][0][by][bx] = fmaf(1.f - wzo, q0, S.Acc[lo][0][by][bx]);
@@ -655,10 +653,15 @@ __global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) {
                         ez[a] = pw_weight(fzc, wzc, nzl);
                         cz[a] = czm * pw_weight(fzm, wzm, nzl) + czp * pw_weight(fzp, wzp, nzl);
                     }
+                    // nodes touched per axis: from the lowest floor to the
+                    // last stencil voxel's floor + 1 (span <= 3)
+                    const int sxn = fxp + 1 - bxm, syn = fyp + 1 - bym, szn = fzp + 1 - bzm;
 #pragma unroll
                     for (int b = 0; b < 4; ++b) {
+                        if (b > syn) continue;
 #pragma unroll
                         for (int a = 0; a < 4; ++a) {
+                            if (a > sxn) continue;
                             const float xy1 = fmaf(ey[b], ax[a], by[b] * ex[a]);
                             const float xy2 = ey[b] * ex[a];
                             if (xy1 == 0.f && xy2 == 0.f) continue;
@@ -666,10 +669,10 @@ __global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) {
                             if (bxl >= nbx || byl >= nby) continue;
 #pragma unroll
                             for (int g = 0; g < 4; ++g) {
+                                if (g > szn) continue;
                                 const float J = fmaf(ez[g], xy1, cz[g] * xy2);
                                 if (J == 0.f) continue;
-                                const int bzl = bzm + g;
-                                atomicAdd(&S.Acc[(bzl + BZ0) & 3][d][byl][bxl], twoh * J * J);
+                                atomicAdd(&S.Acc[(bzm + g + BZ0) & 3][d][byl][bxl], twoh * J * J);
                             }
                         }
                     }
@@ -719,18 +722,24 @@ __device__ __forceinline__ float lap_at(const float* __restrict__ xc, const Node
 }
 
 // L = Lap x per component (Eq. laplace_discretized, clamped Neumann
-// neighbours); optional S = scale * sum L^2 (deterministic).
+// neighbours); optional S = scale * sum L^2 (deterministic).  One thread per
+// node handles the three components.
 __global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L,
                                             double* part, unsigned int* count, double* out, double scale) {
     __shared__ double red[NT];
     DFAcc acc;
-    const unsigned int total = 3u * (unsigned int)G.N;
-    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < total; i += gridDim.x * NT) {
-        int c, n, ix, iy, iz;
-        node_coords(i, G, c, n, ix, iy, iz);
-        const float l = lap_at(x + (size_t)c * G.N, G, n, ix, iy, iz);
-        L[i] = l;
-        acc.add_prod(l, l);
+    const unsigned int N = (unsigned int)G.N;
+    for (unsigned int n = blockIdx.x * NT + threadIdx.x; n < N; n += gridDim.x * NT) {
+        const int iz = (int)fdiv(n, G.fplane);
+        const int rem = (int)n - iz * G.n0 * G.n1;
+        const int iy = (int)fdiv((unsigned int)rem, G.fn0);
+        const int ix = rem - iy * G.n0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float l = lap_at(x + (size_t)c * N, G, (int)n, ix, iy, iz);
+            L[(size_t)c * N + n] = l;
+            acc.add_prod(l, l);
+        }
     }
     if (out) {
         const double bs = block_sum(acc.value(), red);
@@ -740,31 +749,54 @@ __global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict_
 
 // out_{c,n} = sum of the tile partials containing node n (fixed order)
 //           + alpha 2 hbar^y (Lap L)_{c,n}   or   + alpha 2 hbar^y cdiag_n
+// One thread per node handles the three components.
 __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
     __shared__ double red[NT];
     DFAcc acc;
     const NodeGeom& G = P.G;
-    const unsigned int total = 3u * (unsigned int)G.N;
+    const unsigned int N = (unsigned int)G.N;
     const long long box = (long long)P.pbx * P.pby * P.pbz;
-    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < total; i += gridDim.x * NT) {
-        int c, n, ix, iy, iz;
-        node_coords(i, G, c, n, ix, iy, iz);
-        float s = 0.f;
-        for (int tz = P.zlo[iz]; tz <= P.zhi[iz]; ++tz) {
+    for (unsigned int n = blockIdx.x * NT + threadIdx.x; n < N; n += gridDim.x * NT) {
+        const int iz = (int)fdiv(n, G.fplane);
+        const int rem = (int)n - iz * G.n0 * G.n1;
+        const int iy = (int)fdiv((unsigned int)rem, G.fn0);
+        const int ix = rem - iy * G.n0;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        const int tz0 = P.zlo[iz], tz1 = P.zhi[iz], ty0 = P.ylo[iy], ty1 = P.yhi[iy];
+        const int tx0 = P.xlo[ix], tx1 = P.xhi[ix];
+        for (int tz = tz0; tz <= tz1; ++tz) {
             const int bz = iz - P.zb0[tz];
-            for (int ty = P.ylo[iy]; ty <= P.yhi[iy]; ++ty) {
+            for (int ty = ty0; ty <= ty1; ++ty) {
                 const int by = iy - P.yb0[ty];
-                for (int tx = P.xlo[ix]; tx <= P.xhi[ix]; ++tx) {
+                for (int tx = tx0; tx <= tx1; ++tx) {
                     const int bx = ix - P.xb0[tx];
                     const long long t = ((long long)tz * P.nty + ty) * P.ntx + tx;
-                    s += __ldg(P.partial + (t * 3 + c) * box + (bz * P.pby + by) * P.pbx + bx);
+                    const float* pp = P.partial + t * 3 * box + (bz * P.pby + by) * P.pbx + bx;
+                    s0 += __ldg(pp);
+                    s1 += __ldg(pp + box);
+                    s2 += __ldg(pp + 2 * box);
                 }
             }
         }
-        if (P.L) s = fmaf(P.cscale, lap_at(P.L + (size_t)c * G.N, G, n, ix, iy, iz), s);
-        if (P.cdiag) s = fmaf(P.cscale, P.cdiag[n], s);
-        P.out[i] = s;
-        if (P.dotw) acc.add_prod(s, P.dotw[i]);
+        if (P.L) {
+            s0 = fmaf(P.cscale, lap_at(P.L, G, (int)n, ix, iy, iz), s0);
+            s1 = fmaf(P.cscale, lap_at(P.L + N, G, (int)n, ix, iy, iz), s1);
+            s2 = fmaf(P.cscale, lap_at(P.L + 2 * (size_t)N, G, (int)n, ix, iy, iz), s2);
+        }
+        if (P.cdiag) {
+            const float cd = P.cscale * P.cdiag[n];
+            s0 += cd;
+            s1 += cd;
+            s2 += cd;
+        }
+        P.out[n] = s0;
+        P.out[N + n] = s1;
+        P.out[2 * (size_t)N + n] = s2;
+        if (P.dotw) {
+            acc.add_prod(s0, P.dotw[n]);
+            acc.add_prod(s1, P.dotw[N + n]);
+            acc.add_prod(s2, P.dotw[2 * (size_t)N + n]);
+        }
     }
     if (P.dout) {
         const double bs = block_sum(acc.value(), red);

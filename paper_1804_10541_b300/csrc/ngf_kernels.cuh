@@ -66,8 +66,8 @@ struct ImgSmem {
     float S[3][R2N];
     float Pi[2][4][R1N];        // pi(-x), pi(+x), pi(-y), pi(+y) of the halo-1 region
     float Uz[6][UBY][UBX];      // u (and p) interpolated to the current plane in z
-    float Q[3][R0N];            // q_hat of the owned columns
-    float Qx[3][TY][NBX];       // q_hat reduced onto node columns in x
+    alignas(16) float Q4[R0N][4];       // q_hat of the owned columns (3 components + pad)
+    alignas(16) float Qx4[TY][NBX][4];  // q_hat reduced onto node columns in x
     float Acc[2][3][NBY][NBX];  // node-plane accumulators of P^T (two live planes)
     float wx2[SX2], wy2[SY2];
     int fx2[SX2], fy2[SY2];     // node floor relative to the Uz box

@@ -37,7 +37,7 @@ struct Plan {
     long long M = 0, N = 0;
     double hbar = 0, hbary = 0, hy[3]{};
     int zc = 0;
-    int img_blocks = 0, diag_blocks = 0, node_blocks = 0;
+    int img_blocks = 0, diag_blocks = 0, node_blocks = 0, node1_blocks = 0;
     // device workspace
     int* ftab = nullptr;    // fx | fy | fz
     float* wtab = nullptr;  // wx | wy | wz
