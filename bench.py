@@ -339,19 +339,26 @@ def run_kernel_case(args):
     desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"])
     u, p = synth.random_fields(N, 5, amp=0.5 * min(h), device="cuda")
     q = torch.empty(3 * N, device="cuda")
+    g = torch.empty(3 * N, device="cuda")
+    dg = torch.empty(3 * N, device="cuda")
+    times = {}
     with ngf.Plan(desc) as pl:
-        ngf.gn_hessvec(pl.handle, R, T, u, p, q)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.calls):
-            ngf.gn_hessvec(pl.handle, R, T, u, p, q)
-        e1.record()
-        torch.cuda.synchronize()
+        ops = {"hessvec": lambda: ngf.gn_hessvec(pl.handle, R, T, u, p, q),
+               "gradient": lambda: ngf.ngf_gradient(pl.handle, R, T, u, g, want_scalars=False),
+               "diagonal": lambda: ngf.ngf_gn_diagonal(pl.handle, R, T, u, dg)}
+        for name, op in ops.items():
+            op()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.calls):
+                op()
+            e1.record()
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1) / args.calls
     M = m[0] * m[1] * m[2]
-    ms = e0.elapsed_time(e1) / args.calls
-    print(json.dumps({"kernel_case": args.kernel_case, "calls": args.calls, "ms_per_hessvec": ms,
-                      "gvoxel_s": M / ms / 1e6}), flush=True)
+    print(json.dumps({"kernel_case": args.kernel_case, "calls": args.calls,
+                      "ms": times, "hessvec_gvoxel_s": M / times["hessvec"] / 1e6}), flush=True)
     return 0
 
 

@@ -331,7 +331,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
             dacc += (double)(fmaf(0.25f, cross, 0.5f * sq) / (a2 * b2));
         }
         if (OBJ) return;
-        const float c2 = __fdividef(nn * c1, a2);  // N/(A^3 B)
+        const float c2 = nn * c1 / a2;     // N/(A^3 B)
         const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
         float rh[6], rs = 0.f;
 #pragma unroll
@@ -509,7 +509,7 @@ __device__ __forceinline__ float pw_weight(int f, float w1, int node) {
     return (node == f) ? 1.f - w1 : ((node == f + 1) ? w1 : 0.f);
 }
 
-__global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) {
+__global__ void __launch_bounds__(NT, 2) k_diag(const ImgParams P) {
     NGF_DYNAMIC_SMEM(smraw);
     DiagSmem& S = *reinterpret_cast<DiagSmem*>(smraw);
     const int tid = threadIdx.x;
