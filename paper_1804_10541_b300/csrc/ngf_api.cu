@@ -4,6 +4,7 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -18,6 +19,36 @@ std::atomic<int64_t>& launch_counter() {
 }
 
 static thread_local std::string g_last_error = "no error";
+
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[256] = {};
+
+cudaError_t dev_alloc(void** ptr, size_t bytes, cudaStream_t stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pools[dev], &props);
+            if (e != cudaSuccess) return e;
+            unsigned long long keep = ~0ull;  // keep freed blocks for the next call
+            cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = g_pools[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes ? bytes : 1, pool, stream);
+}
+
+void dev_free(void* ptr, cudaStream_t stream) {
+    if (ptr) cudaFreeAsync(ptr, stream);
+}
 
 ngf_status set_error(Plan* p, ngf_status s, const std::string& msg) {
     if (p) p->err = msg;
@@ -151,8 +182,9 @@ static ngf_status build_geometry(Plan* p, int halo, const std::vector<int>* f, G
         std::copy(b0[a].begin(), b0[a].end(), h.begin() + o);
         o += nt[a];
     }
-    NGF_CU(p, cudaMalloc(&g.mem, total * sizeof(int)), "cudaMalloc(geometry)");
-    NGF_CU(p, cudaMemcpy(g.mem, h.data(), total * sizeof(int), cudaMemcpyHostToDevice), "cudaMemcpy(geometry)");
+    NGF_CU(p, dev_alloc((void**)&g.mem, total * sizeof(int), p->stream), "allocate geometry");
+    NGF_CU(p, cudaMemcpyAsync(g.mem, h.data(), total * sizeof(int), cudaMemcpyHostToDevice, p->stream), "copy geometry");
+    NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
     g.xlo = g.mem + off[0];
     g.xhi = g.mem + off[1];
     g.ylo = g.mem + off[2];
@@ -186,32 +218,24 @@ static void clear_prof(Plan* p, int which) {
 
 static void free_plan(Plan* p) {
     for (int k = 0; k < 4; ++k) clear_prof(p, k);
-    cudaFree(p->ftab);
-    cudaFree(p->wtab);
-    cudaFree(p->g0.mem);
-    cudaFree(p->g1.mem);
-    cudaFree(p->partial);
-    cudaFree(p->L);
-    cudaFree(p->cdiag);
-    cudaFree(p->dsc);
-    cudaFree(p->dpart);
-    cudaFree(p->dcount);
+    for (void* ptr : {(void*)p->ftab, (void*)p->wtab, (void*)p->g0.mem, (void*)p->g1.mem, (void*)p->partial,
+                      (void*)p->L, (void*)p->ctab, (void*)p->dsc, (void*)p->dpart, (void*)p->dcount})
+        dev_free(ptr, p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
 }
 
-// curvature part of the Jacobi diagonal: diag(Lap^T Lap) per node.  With
-// Lap = sum_a K_a (K_a the 1-D clamped Laplacian along axis a, Kronecker-
-// extended), diag(Lap^2) = sum_a diag(K_a^2) + sum_{a != b} diag(K_a) diag(K_b);
-// the 1-D matrices are symmetric, so diag(K_a^2) is their column sum of squares.
-static void curvature_diagonal(const Plan* p, std::vector<float>& cd) {
-    cd.assign(p->N, 0.f);
-    std::vector<double> d1[3], dg[3];
+// curvature part of the Jacobi diagonal, per axis: for the 1-D clamped
+// Laplacian K (symmetric), d1 = diag(K^2) (column sums of squares) and
+// dg = diag(K); k_node_combine forms diag(Lap^T Lap) from them per node.
+static void curvature_tables(const Plan* p, std::vector<float>& t) {
+    const int tot = p->n[0] + p->n[1] + p->n[2];
+    t.assign(2 * tot, 0.f);
+    int off = 0;
     for (int a = 0; a < 3; ++a) {
         const double ih2 = 1.0 / (p->hy[a] * p->hy[a]);
         const int nn = p->n[a];
-        d1[a].assign(nn, 0.0);
-        dg[a].assign(nn, 0.0);
+        std::vector<double> d1(nn, 0.0);
         for (int i = 0; i < nn; ++i) {
             double row[3] = {0, 0, 0};  // entries at columns i-1, i, i+1 after clamping
             for (int s = -1; s <= 1; s += 2) {
@@ -221,22 +245,13 @@ static void curvature_diagonal(const Plan* p, std::vector<float>& cd) {
             }
             for (int k = 0; k < 3; ++k) {
                 const int j = i + k - 1;
-                if (j >= 0 && j < nn) d1[a][j] += row[k] * row[k] * ih2 * ih2;
+                if (j >= 0 && j < nn) d1[j] += row[k] * row[k] * ih2 * ih2;
             }
-            dg[a][i] = row[1] * ih2;
+            t[tot + off + i] = (float)(row[1] * ih2);
         }
+        for (int i = 0; i < nn; ++i) t[off + i] = (float)d1[i];
+        off += nn;
     }
-    for (int z = 0; z < p->n[2]; ++z)
-        for (int y = 0; y < p->n[1]; ++y)
-            for (int x = 0; x < p->n[0]; ++x) {
-                const int idx[3] = {x, y, z};
-                double s = 0.0;
-                for (int a = 0; a < 3; ++a) s += d1[a][idx[a]];
-                for (int a = 0; a < 3; ++a)
-                    for (int b = 0; b < 3; ++b)
-                        if (a != b) s += dg[a][idx[a]] * dg[b][idx[b]];
-                cd[x + (long long)p->n[0] * (y + (long long)p->n[1] * z)] = (float)s;
-            }
 }
 
 static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t stream) {
@@ -274,23 +289,25 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
         fh.insert(fh.end(), f[a].begin(), f[a].end());
         wh.insert(wh.end(), w[a].begin(), w[a].end());
     }
-    NGF_CU(p, cudaMalloc(&p->ftab, tl * sizeof(int)), "cudaMalloc(tables)");
-    NGF_CU(p, cudaMalloc(&p->wtab, tl * sizeof(float)), "cudaMalloc(tables)");
-    NGF_CU(p, cudaMemcpy(p->ftab, fh.data(), tl * sizeof(int), cudaMemcpyHostToDevice), "cudaMemcpy(tables)");
-    NGF_CU(p, cudaMemcpy(p->wtab, wh.data(), tl * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy(tables)");
+    NGF_CU(p, dev_alloc((void**)&p->ftab, tl * sizeof(int), p->stream), "allocate tables");
+    NGF_CU(p, dev_alloc((void**)&p->wtab, tl * sizeof(float), p->stream), "allocate tables");
+    NGF_CU(p, cudaMemcpyAsync(p->ftab, fh.data(), tl * sizeof(int), cudaMemcpyHostToDevice, p->stream), "copy tables");
+    NGF_CU(p, cudaMemcpyAsync(p->wtab, wh.data(), tl * sizeof(float), cudaMemcpyHostToDevice, p->stream), "copy tables");
 
     NGF_TRY(build_geometry(p, 0, f, p->g0));
     NGF_TRY(build_geometry(p, 1, f, p->g1));
     if (p->g0.pbx > NBX || p->g0.pby > NBY || p->g1.pbx > DBX || p->g1.pby > DBY)
         return set_error(p, NGF_EBOUNDS, "internal: tile node box exceeds the kernel's shared-memory box");
     const long long pf = std::max(p->g0.partial_floats(), p->g1.partial_floats());
-    NGF_CU(p, cudaMalloc(&p->partial, pf * sizeof(float)), "cudaMalloc(partials)");
-    NGF_CU(p, cudaMalloc(&p->L, 3 * p->N * sizeof(float)), "cudaMalloc(L)");
+    NGF_CU(p, dev_alloc((void**)&p->partial, pf * sizeof(float), p->stream), "allocate partials");
+    NGF_CU(p, dev_alloc((void**)&p->L, 3 * p->N * sizeof(float), p->stream), "allocate L");
     {
-        std::vector<float> cd;
-        curvature_diagonal(p, cd);
-        NGF_CU(p, cudaMalloc(&p->cdiag, p->N * sizeof(float)), "cudaMalloc(cdiag)");
-        NGF_CU(p, cudaMemcpy(p->cdiag, cd.data(), p->N * sizeof(float), cudaMemcpyHostToDevice), "cudaMemcpy(cdiag)");
+        std::vector<float> ct;
+        curvature_tables(p, ct);
+        NGF_CU(p, dev_alloc((void**)&p->ctab, ct.size() * sizeof(float), p->stream), "allocate curvature tables");
+        NGF_CU(p, cudaMemcpyAsync(p->ctab, ct.data(), ct.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream),
+               "copy curvature tables");
+        NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
     }
 
     p->img_blocks = (int)p->g0.tiles();
@@ -298,16 +315,17 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     p->node_blocks = grid_for(3 * p->N, 4 * sms);   // element-wise vector kernels
     p->node1_blocks = grid_for(p->N, 16 * sms);     // one thread per node
     p->dpart_len = 2 * (size_t)std::max({p->img_blocks, p->diag_blocks, p->node_blocks, p->node1_blocks, 8 * sms});
-    NGF_CU(p, cudaMalloc(&p->dsc, 16 * sizeof(double)), "cudaMalloc(scalars)");
-    NGF_CU(p, cudaMemset(p->dsc, 0, 16 * sizeof(double)), "cudaMemset(scalars)");
-    NGF_CU(p, cudaMalloc(&p->dpart, p->dpart_len * sizeof(double)), "cudaMalloc(partials64)");
-    NGF_CU(p, cudaMalloc(&p->dcount, 4 * sizeof(unsigned int)), "cudaMalloc(counter)");
-    NGF_CU(p, cudaMemset(p->dcount, 0, 4 * sizeof(unsigned int)), "cudaMemset(counter)");
+    NGF_CU(p, dev_alloc((void**)&p->dsc, 16 * sizeof(double), p->stream), "allocate scalars");
+    NGF_CU(p, cudaMemsetAsync(p->dsc, 0, 16 * sizeof(double), p->stream), "clear scalars");
+    NGF_CU(p, dev_alloc((void**)&p->dpart, p->dpart_len * sizeof(double), p->stream), "allocate partials64");
+    NGF_CU(p, dev_alloc((void**)&p->dcount, 4 * sizeof(unsigned int), p->stream), "allocate counter");
+    NGF_CU(p, cudaMemsetAsync(p->dcount, 0, 4 * sizeof(unsigned int), p->stream), "clear counter");
 
     NGF_CU(p, cudaFuncSetAttribute(k_image_obj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_image_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_image_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
+    NGF_CU(p, cudaFuncSetAttribute(k_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
     return NGF_OK;
 }
 
@@ -369,7 +387,7 @@ ImgParams img_params(const Plan* p, const float* R, const float* T, const float*
     return P;
 }
 
-CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const float* L, const float* cdiag,
+CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const float* L, const float* ctab,
                              const float* dotw, double* dout) {
     CombineParams C;
     C.G = node_geom(p);
@@ -389,7 +407,7 @@ CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const
     C.yb0 = g.yb0;
     C.zb0 = g.zb0;
     C.L = L;
-    C.cdiag = cdiag;
+    C.ctab = ctab;
     C.cscale = (float)(p->desc.alpha * 2.0 * p->hbary);
     C.out = out;
     C.dotw = dotw;
@@ -443,9 +461,10 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
 ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g1, nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
-    NGF_CU(p, launch(k_diag, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P), "k_diag");
+    const bool span3 = 2 * (p->n[0] - 1) <= p->m[0] && 2 * (p->n[1] - 1) <= p->m[1] && 2 * (p->n[2] - 1) <= p->m[2];
+    NGF_CU(p, launch(span3 ? k_diag : k_diag4, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P), "k_diag");
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
-    CombineParams C = combine_params(p, p->g1, diag, nullptr, p->cdiag, nullptr, nullptr);
+    CombineParams C = combine_params(p, p->g1, diag, nullptr, p->ctab, nullptr, nullptr);
     NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
 }

@@ -32,7 +32,8 @@ static ngf_level_desc level_at(const ngf_level_desc& finest, int level) {
 
 struct DevBuf {
     void* ptr = nullptr;
-    ~DevBuf() { cudaFree(ptr); }
+    cudaStream_t stream = nullptr;
+    ~DevBuf() { dev_free(ptr, stream); }
     template <class T>
     T* as() const { return static_cast<T*>(ptr); }
 };
@@ -71,6 +72,10 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
         return set_error(nullptr, NGF_EINVAL, "start_level out of range");
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     ngf_report r{};
+    auto alloc = [stream](DevBuf& b, size_t bytes) {
+        b.stream = stream;
+        return dev_alloc(&b.ptr, bytes, stream);
+    };
 
     const int L = o->levels;
     std::vector<ngf_level_desc> lv(L);
@@ -90,13 +95,13 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
         if (l == 0 && R_dev) {
             Rl[0] = R;
         } else {
-            DRV_CU(cudaMalloc(&imgs[2 * l].ptr, M * sizeof(float)), "cudaMalloc(R level)");
+            DRV_CU(alloc(imgs[2 * l], M * sizeof(float)), "allocate R level");
             Rl[l] = imgs[2 * l].as<float>();
         }
         if (l == 0 && T_dev) {
             Tl[0] = T;
         } else {
-            DRV_CU(cudaMalloc(&imgs[2 * l + 1].ptr, M * sizeof(float)), "cudaMalloc(T level)");
+            DRV_CU(alloc(imgs[2 * l + 1], M * sizeof(float)), "allocate T level");
             Tl[l] = imgs[2 * l + 1].as<float>();
         }
     }
@@ -106,21 +111,21 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
     // work vectors sized for the finest level
     const long long n3 = 3 * N0;
     DevBuf bu, but, bg, bdiag, bx, br, bz, bd, bq, bsc, bpart, bcnt, btab;
-    DRV_CU(cudaMalloc(&bu.ptr, n3 * sizeof(float)), "cudaMalloc(u)");
-    DRV_CU(cudaMalloc(&but.ptr, n3 * sizeof(float)), "cudaMalloc(ut)");
-    DRV_CU(cudaMalloc(&bg.ptr, n3 * sizeof(float)), "cudaMalloc(g)");
-    DRV_CU(cudaMalloc(&bdiag.ptr, n3 * sizeof(float)), "cudaMalloc(diag)");
-    DRV_CU(cudaMalloc(&bx.ptr, n3 * sizeof(float)), "cudaMalloc(x)");
-    DRV_CU(cudaMalloc(&br.ptr, n3 * sizeof(float)), "cudaMalloc(r)");
-    DRV_CU(cudaMalloc(&bz.ptr, n3 * sizeof(float)), "cudaMalloc(z)");
-    DRV_CU(cudaMalloc(&bd.ptr, n3 * sizeof(float)), "cudaMalloc(d)");
-    DRV_CU(cudaMalloc(&bq.ptr, n3 * sizeof(float)), "cudaMalloc(q)");
-    DRV_CU(cudaMalloc(&bsc.ptr, 32 * sizeof(double)), "cudaMalloc(scalars)");
+    DRV_CU(alloc(bu, n3 * sizeof(float)), "allocate u");
+    DRV_CU(alloc(but, n3 * sizeof(float)), "allocate ut");
+    DRV_CU(alloc(bg, n3 * sizeof(float)), "allocate g");
+    DRV_CU(alloc(bdiag, n3 * sizeof(float)), "allocate diag");
+    DRV_CU(alloc(bx, n3 * sizeof(float)), "allocate x");
+    DRV_CU(alloc(br, n3 * sizeof(float)), "allocate r");
+    DRV_CU(alloc(bz, n3 * sizeof(float)), "allocate z");
+    DRV_CU(alloc(bd, n3 * sizeof(float)), "allocate d");
+    DRV_CU(alloc(bq, n3 * sizeof(float)), "allocate q");
+    DRV_CU(alloc(bsc, 32 * sizeof(double)), "allocate scalars");
     DRV_CU(cudaMemsetAsync(bsc.ptr, 0, 32 * sizeof(double), stream), "memset(scalars)");
-    DRV_CU(cudaMalloc(&bpart.ptr, 4096 * sizeof(double)), "cudaMalloc(partials)");
-    DRV_CU(cudaMalloc(&bcnt.ptr, 4 * sizeof(unsigned int)), "cudaMalloc(counter)");
+    DRV_CU(alloc(bpart, 4096 * sizeof(double)), "allocate partials");
+    DRV_CU(alloc(bcnt, 4 * sizeof(unsigned int)), "allocate counter");
     DRV_CU(cudaMemsetAsync(bcnt.ptr, 0, 4 * sizeof(unsigned int), stream), "memset(counter)");
-    DRV_CU(cudaMalloc(&btab.ptr, 3 * 4096 * (sizeof(int) + sizeof(float))), "cudaMalloc(prolongation tables)");
+    DRV_CU(alloc(btab, 3 * 4096 * (sizeof(int) + sizeof(float))), "allocate prolongation tables");
     double* dsc = bsc.as<double>();  // 0 D, 1 S, 2 dot, 3 non-finite count; 8.. PCG state
     double* pcg_sc = dsc + 8;
 

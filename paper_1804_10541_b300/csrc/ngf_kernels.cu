@@ -509,7 +509,8 @@ __device__ __forceinline__ float pw_weight(int f, float w1, int node) {
     return (node == f) ? 1.f - w1 : ((node == f + 1) ? w1 : 0.f);
 }
 
-__global__ void __launch_bounds__(NT, 2) k_diag(const ImgParams P) {
+template <int SPAN>
+__device__ __forceinline__ void diag_pass(const ImgParams& P) {
     NGF_DYNAMIC_SMEM(smraw);
     DiagSmem& S = *reinterpret_cast<DiagSmem*>(smraw);
     const int tid = threadIdx.x;
@@ -642,36 +643,34 @@ __global__ void __launch_bounds__(NT, 2) k_diag(const ImgParams P) {
                     const float cxm = rh[2] * dTd[1][xm], cxp = rh[3] * dTd[1][xp];
                     const float cym = rh[1] * dTd[1][ym], cyp = rh[4] * dTd[1][yp];
                     const float czm = rh[0] * dTd[0][li], czp = rh[5] * dTd[2][li];
-                    float ax[4], ex[4], by[4], ey[4], cz[4], ez[4];
+                    // 1-D weight vectors over the SPAN nodes from the lowest floor:
+                    // e* of the voxel itself, a*/b*/c* coefficient-weighted ones
+                    // of its x / y / z stencil entries
+                    float ax[SPAN], ex[SPAN], byv[SPAN], ey[SPAN], cz[SPAN], ez[SPAN];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) {
+                    for (int a = 0; a < SPAN; ++a) {
                         const int nxl = bxm + a, nyl = bym + a, nzl = bzm + a;
                         ex[a] = pw_weight(fxc, wxc, nxl);
                         ax[a] = cc * ex[a] + cxm * pw_weight(fxm, wxm, nxl) + cxp * pw_weight(fxp, wxp, nxl);
                         ey[a] = pw_weight(fyc, wyc, nyl);
-                        by[a] = cym * pw_weight(fym, wym, nyl) + cyp * pw_weight(fyp, wyp, nyl);
+                        byv[a] = cym * pw_weight(fym, wym, nyl) + cyp * pw_weight(fyp, wyp, nyl);
                         ez[a] = pw_weight(fzc, wzc, nzl);
                         cz[a] = czm * pw_weight(fzm, wzm, nzl) + czp * pw_weight(fzp, wzp, nzl);
                     }
-                    // nodes touched per axis: from the lowest floor to the
-                    // last stencil voxel's floor + 1 (span <= 3)
-                    const int sxn = fxp + 1 - bxm, syn = fyp + 1 - bym, szn = fzp + 1 - bzm;
+                    // J(a,b,g) = ez (ey ax + by ex) + cz ey ex; entries outside the
+                    // support are exactly zero, so only the box bounds are checked
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        if (b > syn) continue;
+                    for (int b = 0; b < SPAN; ++b) {
+                        const int byl = bym + b;
 #pragma unroll
-                        for (int a = 0; a < 4; ++a) {
-                            if (a > sxn) continue;
-                            const float xy1 = fmaf(ey[b], ax[a], by[b] * ex[a]);
-                            const float xy2 = ey[b] * ex[a];
-                            if (xy1 == 0.f && xy2 == 0.f) continue;
-                            const int bxl = bxm + a, byl = bym + b;
+                        for (int a = 0; a < SPAN; ++a) {
+                            const int bxl = bxm + a;
                             if (bxl >= nbx || byl >= nby) continue;
+                            const float xy1 = fmaf(ey[b], ax[a], byv[b] * ex[a]);
+                            const float xy2 = ey[b] * ex[a];
 #pragma unroll
-                            for (int g = 0; g < 4; ++g) {
-                                if (g > szn) continue;
+                            for (int g = 0; g < SPAN; ++g) {
                                 const float J = fmaf(ez[g], xy1, cz[g] * xy2);
-                                if (J == 0.f) continue;
                                 atomicAdd(&S.Acc[(bzm + g + BZ0) & 3][d][byl][bxl], twoh * J * J);
                             }
                         }
@@ -695,6 +694,11 @@ __global__ void __launch_bounds__(NT, 2) k_diag(const ImgParams P) {
         }
     }
 }
+
+// Three nodes per axis suffice when every axis has at least two voxels per
+// deformation cell (2 (n-1) <= m); four otherwise.
+__global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) { diag_pass<3>(P); }
+__global__ void __launch_bounds__(NT, 1) k_diag4(const ImgParams P) { diag_pass<4>(P); }
 
 // ---------------------------------------------------------------------------
 // nodal kernels
@@ -748,7 +752,7 @@ __global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict_
 }
 
 // out_{c,n} = sum of the tile partials containing node n (fixed order)
-//           + alpha 2 hbar^y (Lap L)_{c,n}   or   + alpha 2 hbar^y cdiag_n
+//           + alpha 2 hbar^y (Lap L)_{c,n}   or   + alpha 2 hbar^y diag(Lap^T Lap)_n
 // One thread per node handles the three components.
 __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
     __shared__ double red[NT];
@@ -783,8 +787,13 @@ __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
             s1 = fmaf(P.cscale, lap_at(P.L + N, G, (int)n, ix, iy, iz), s1);
             s2 = fmaf(P.cscale, lap_at(P.L + 2 * (size_t)N, G, (int)n, ix, iy, iz), s2);
         }
-        if (P.cdiag) {
-            const float cd = P.cscale * P.cdiag[n];
+        if (P.ctab) {
+            // diag(Lap^T Lap) = sum_a diag(K_a^2) + sum_{a != b} diag(K_a) diag(K_b)
+            // with K_a the 1-D clamped Laplacian along axis a
+            const int o1 = G.n0, o2 = G.n0 + G.n1, od = G.n0 + G.n1 + G.n2;
+            const float gx = P.ctab[od + ix], gy = P.ctab[od + o1 + iy], gz = P.ctab[od + o2 + iz];
+            const float cd = P.cscale * (P.ctab[ix] + P.ctab[o1 + iy] + P.ctab[o2 + iz] +
+                                         2.f * (gx * gy + gx * gz + gy * gz));
             s0 += cd;
             s1 += cd;
             s2 += cd;

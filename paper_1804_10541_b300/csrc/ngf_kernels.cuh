@@ -147,7 +147,7 @@ struct CombineParams {
     const int* yb0;
     const int* zb0;
     const float* L;      // Lap(input) for the curvature term (nullable)
-    const float* cdiag;  // curvature diagonal (nullable)
+    const float* ctab;   // curvature diagonal per axis, d1 | dg (nullable)
     float cscale;        // alpha 2 hbar^y
     float* out;
     const float* dotw;   // optional: out . dotw into dout
@@ -181,7 +181,8 @@ __host__ __device__ constexpr int ring_size(int halo) { return 2 * halo * (TX + 
 __global__ void k_image_obj(const ImgParams P);   // D only
 __global__ void k_image_grad(const ImgParams P);  // D and gradient tile partials
 __global__ void k_image_hess(const ImgParams P);  // Hessian-vector tile partials
-__global__ void k_diag(const ImgParams P);        // Jacobi-diagonal tile partials
+__global__ void k_diag(const ImgParams P);        // Jacobi-diagonal tile partials (>= 2 voxels per cell)
+__global__ void k_diag4(const ImgParams P);       // same, any voxels-per-cell ratio
 __global__ void k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L, double* part,
                       unsigned int* count, double* out, double scale);
 __global__ void k_node_combine(const CombineParams P);

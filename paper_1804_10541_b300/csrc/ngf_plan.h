@@ -44,7 +44,7 @@ struct Plan {
     Geometry g0, g1;        // halo 0 (gradient, Hessian), halo 1 (diagonal)
     float* partial = nullptr;
     float* L = nullptr;      // Laplacian scratch, 3N
-    float* cdiag = nullptr;  // curvature diagonal, N
+    float* ctab = nullptr;   // curvature diagonal per axis: d1 | dg (2 x (n0+n1+n2))
     double* dsc = nullptr;   // scalars: 0 D, 1 S, 2 dot, 3 nonfinite count
     double* dpart = nullptr;
     unsigned int* dcount = nullptr;
@@ -60,6 +60,12 @@ struct Plan {
     long long graph_kernels = 0;
 };
 
+// Device memory of plans and registrations comes from a library-private
+// stream-ordered pool per device (kept across calls, freed without a device
+// synchronisation).
+cudaError_t dev_alloc(void** ptr, size_t bytes, cudaStream_t stream);
+void dev_free(void* ptr, cudaStream_t stream);
+
 // helpers implemented in ngf_api.cu
 ngf_status set_error(Plan* p, ngf_status s, const std::string& msg);
 ngf_status cuda_check(Plan* p, cudaError_t e, const char* what);
@@ -67,7 +73,7 @@ ngf_status validate_desc(const ngf_level_desc* d, std::string& why);
 bool is_device_ptr(const void* ptr);
 ImgParams img_params(const Plan* p, const float* R, const float* T, const float* u, const float* p_,
                      int mode, const Geometry& g, double* dout);
-CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const float* L, const float* cdiag,
+CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const float* L, const float* ctab,
                              const float* dotw, double* dout);
 NodeGeom node_geom(const Plan* p);
 ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u, const float* pv, float* q,
