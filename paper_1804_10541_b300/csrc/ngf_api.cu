@@ -165,35 +165,34 @@ static ngf_status build_geometry(Plan* p, int halo, const std::vector<int>* f, G
     g.pbx = mb[0];
     g.pby = mb[1];
     g.pbz = mb[2];
-    const size_t total = 2 * (size_t)(p->n[0] + p->n[1] + p->n[2]) + nt[0] + nt[1] + nt[2];
+    if (g.partial_floats() >= INT_MAX) return set_error(p, NGF_EBOUNDS, "tile partials exceed 2^31 floats");
+    const long long box = (long long)g.pbx * g.pby * g.pbz;
+    const long long tile_stride[3] = {3 * box, (long long)g.ntx * 3 * box, (long long)g.ntx * g.nty * 3 * box};
+    const long long in_stride[3] = {1, g.pbx, (long long)g.pbx * g.pby};
+    const size_t total = 2 * (size_t)(p->n[0] + p->n[1] + p->n[2]);
     std::vector<int> h(total);
     size_t o = 0;
-    size_t off[9];
+    size_t off[6];
     for (int a = 0; a < 3; ++a) {
         off[2 * a] = o;
-        std::copy(lo[a].begin(), lo[a].end(), h.begin() + o);
-        o += p->n[a];
-        off[2 * a + 1] = o;
-        std::copy(hi[a].begin(), hi[a].end(), h.begin() + o);
-        o += p->n[a];
-    }
-    for (int a = 0; a < 3; ++a) {
-        off[6 + a] = o;
-        std::copy(b0[a].begin(), b0[a].end(), h.begin() + o);
-        o += nt[a];
+        off[2 * a + 1] = o + p->n[a];
+        for (int k = 0; k < p->n[a]; ++k) {
+            const int t0 = lo[a][k], t1 = hi[a][k];
+            if (t1 - t0 > 1) return set_error(p, NGF_EINVAL, "internal: node covered by more than two tiles");
+            h[o + k] = (int)(t0 * tile_stride[a] + (k - b0[a][t0]) * in_stride[a]);
+            h[o + p->n[a] + k] = (t1 > t0) ? (int)(t1 * tile_stride[a] + (k - b0[a][t1]) * in_stride[a]) : -1;
+        }
+        o += 2 * p->n[a];
     }
     NGF_CU(p, dev_alloc((void**)&g.mem, total * sizeof(int), p->stream), "allocate geometry");
     NGF_CU(p, cudaMemcpyAsync(g.mem, h.data(), total * sizeof(int), cudaMemcpyHostToDevice, p->stream), "copy geometry");
     NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
-    g.xlo = g.mem + off[0];
-    g.xhi = g.mem + off[1];
-    g.ylo = g.mem + off[2];
-    g.yhi = g.mem + off[3];
-    g.zlo = g.mem + off[4];
-    g.zhi = g.mem + off[5];
-    g.xb0 = g.mem + off[6];
-    g.yb0 = g.mem + off[7];
-    g.zb0 = g.mem + off[8];
+    g.ox0 = g.mem + off[0];
+    g.ox1 = g.mem + off[1];
+    g.oy0 = g.mem + off[2];
+    g.oy1 = g.mem + off[3];
+    g.oz0 = g.mem + off[4];
+    g.oz1 = g.mem + off[5];
     return NGF_OK;
 }
 
@@ -392,20 +391,13 @@ CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const
     CombineParams C;
     C.G = node_geom(p);
     C.partial = p->partial;
-    C.pbx = g.pbx;
-    C.pby = g.pby;
-    C.pbz = g.pbz;
-    C.ntx = g.ntx;
-    C.nty = g.nty;
-    C.xlo = g.xlo;
-    C.xhi = g.xhi;
-    C.ylo = g.ylo;
-    C.yhi = g.yhi;
-    C.zlo = g.zlo;
-    C.zhi = g.zhi;
-    C.xb0 = g.xb0;
-    C.yb0 = g.yb0;
-    C.zb0 = g.zb0;
+    C.box = g.pbx * g.pby * g.pbz;
+    C.ox0 = g.ox0;
+    C.ox1 = g.ox1;
+    C.oy0 = g.oy0;
+    C.oy1 = g.oy1;
+    C.oz0 = g.oz0;
+    C.oz1 = g.oz1;
     C.L = L;
     C.ctab = ctab;
     C.cscale = (float)(p->desc.alpha * 2.0 * p->hbary);
@@ -627,6 +619,8 @@ static PcgParams pcg_params(Plan* p, ngf_pcg_state* st, const float* rhs) {
     P.part = p->dpart;
     P.count = p->dcount;
     P.rtol = st->rtol;
+    auto al = [](const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; };
+    P.vec4 = al(P.x) && al(P.r) && al(P.z) && al(P.d) && al(P.q) && al(P.diag);
     return P;
 }
 

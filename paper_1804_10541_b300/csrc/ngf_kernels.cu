@@ -636,6 +636,27 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
                 const int fzm = P.fz[vzm] - BZ0, fzc = P.fz[zq] - BZ0, fzp = P.fz[vzp] - BZ0;
                 const float wzm = P.wz[vzm], wzc = P.wz[zq], wzp = P.wz[vzp];
                 const int bxm = fxm, bym = fym, bzm = fzm;  // lowest node touched per axis
+                // trilinear weights of the stencil voxels (offset -1, 0, +1 per
+                // axis) on the SPAN nodes from the lowest floor; independent of
+                // the component
+                float WX[3][SPAN], WY[3][SPAN], WZ[3][SPAN];
+#pragma unroll
+                for (int a = 0; a < SPAN; ++a) {
+                    WX[0][a] = pw_weight(fxm, wxm, bxm + a);
+                    WX[1][a] = pw_weight(fxc, wxc, bxm + a);
+                    WX[2][a] = pw_weight(fxp, wxp, bxm + a);
+                    WY[0][a] = pw_weight(fym, wym, bym + a);
+                    WY[1][a] = pw_weight(fyc, wyc, bym + a);
+                    WY[2][a] = pw_weight(fyp, wyp, bym + a);
+                    WZ[0][a] = pw_weight(fzm, wzm, bzm + a);
+                    WZ[1][a] = pw_weight(fzc, wzc, bzm + a);
+                    WZ[2][a] = pw_weight(fzp, wzp, bzm + a);
+                }
+                constexpr int PLANE = 3 * DBY * DBX;
+                int po[SPAN];
+#pragma unroll
+                for (int g = 0; g < SPAN; ++g) po[g] = ((bzm + g + BZ0) & 3) * PLANE + bym * DBX + bxm;
+                float* acc = &S.Acc[0][0][0][0];
 #pragma unroll 1
                 for (int d = 0; d < 3; ++d) {
                     const float* dTd[3] = {S.dT[szm][d], S.dT[sc][d], S.dT[szp][d]};
@@ -643,35 +664,30 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
                     const float cxm = rh[2] * dTd[1][xm], cxp = rh[3] * dTd[1][xp];
                     const float cym = rh[1] * dTd[1][ym], cyp = rh[4] * dTd[1][yp];
                     const float czm = rh[0] * dTd[0][li], czp = rh[5] * dTd[2][li];
-                    // 1-D weight vectors over the SPAN nodes from the lowest floor:
-                    // e* of the voxel itself, a*/b*/c* coefficient-weighted ones
-                    // of its x / y / z stencil entries
-                    float ax[SPAN], ex[SPAN], byv[SPAN], ey[SPAN], cz[SPAN], ez[SPAN];
+                    // row entries J(a,b,g) = ez (ey ax + by ex) + cz ey ex with e*
+                    // the voxel's own weights and a*/b*/c* the coefficient-weighted
+                    // weights of its x / y / z stencil entries
+                    float ax[SPAN], byv[SPAN], cz[SPAN];
 #pragma unroll
                     for (int a = 0; a < SPAN; ++a) {
-                        const int nxl = bxm + a, nyl = bym + a, nzl = bzm + a;
-                        ex[a] = pw_weight(fxc, wxc, nxl);
-                        ax[a] = cc * ex[a] + cxm * pw_weight(fxm, wxm, nxl) + cxp * pw_weight(fxp, wxp, nxl);
-                        ey[a] = pw_weight(fyc, wyc, nyl);
-                        byv[a] = cym * pw_weight(fym, wym, nyl) + cyp * pw_weight(fyp, wyp, nyl);
-                        ez[a] = pw_weight(fzc, wzc, nzl);
-                        cz[a] = czm * pw_weight(fzm, wzm, nzl) + czp * pw_weight(fzp, wzp, nzl);
+                        ax[a] = fmaf(cc, WX[1][a], fmaf(cxm, WX[0][a], cxp * WX[2][a]));
+                        byv[a] = fmaf(cym, WY[0][a], cyp * WY[2][a]);
+                        cz[a] = fmaf(czm, WZ[0][a], czp * WZ[2][a]);
                     }
-                    // J(a,b,g) = ez (ey ax + by ex) + cz ey ex; entries outside the
-                    // support are exactly zero, so only the box bounds are checked
+                    float* accd = acc + d * DBY * DBX;
+                    // entries outside the support are exactly zero, so only the
+                    // box bounds are checked; the 2 hbar factor is applied at the store
 #pragma unroll
                     for (int b = 0; b < SPAN; ++b) {
-                        const int byl = bym + b;
 #pragma unroll
                         for (int a = 0; a < SPAN; ++a) {
-                            const int bxl = bxm + a;
-                            if (bxl >= nbx || byl >= nby) continue;
-                            const float xy1 = fmaf(ey[b], ax[a], byv[b] * ex[a]);
-                            const float xy2 = ey[b] * ex[a];
+                            if (bxm + a >= nbx || bym + b >= nby) continue;
+                            const float xy1 = fmaf(WY[1][b], ax[a], byv[b] * WX[1][a]);
+                            const float xy2 = WY[1][b] * WX[1][a];
 #pragma unroll
                             for (int g = 0; g < SPAN; ++g) {
-                                const float J = fmaf(ez[g], xy1, cz[g] * xy2);
-                                atomicAdd(&S.Acc[(bzm + g + BZ0) & 3][d][byl][bxl], twoh * J * J);
+                                const float J = fmaf(WZ[1][g], xy1, cz[g] * xy2);
+                                atomicAdd(accd + po[g] + b * DBX + a, J * J);
                             }
                         }
                     }
@@ -686,7 +702,8 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
                 for (int i = tid; i < items; i += NT) {
                     const int c = i / (nby * nbx), rem = i % (nby * nbx), byy = rem / nbx, bxx = rem % nbx;
                     float& a = S.Acc[next & 3][c][byy][bxx];
-                    P.partial[((tile * 3 + c) * P.pbz + (next - BZ0)) * (long long)(P.pby * P.pbx) + byy * P.pbx + bxx] = a;
+                    P.partial[((tile * 3 + c) * P.pbz + (next - BZ0)) * (long long)(P.pby * P.pbx) + byy * P.pbx + bxx] =
+                        twoh * a;
                     a = 0.f;
                 }
                 ++next;
@@ -759,23 +776,27 @@ __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
     DFAcc acc;
     const NodeGeom& G = P.G;
     const unsigned int N = (unsigned int)G.N;
-    const long long box = (long long)P.pbx * P.pby * P.pbz;
     for (unsigned int n = blockIdx.x * NT + threadIdx.x; n < N; n += gridDim.x * NT) {
         const int iz = (int)fdiv(n, G.fplane);
         const int rem = (int)n - iz * G.n0 * G.n1;
         const int iy = (int)fdiv((unsigned int)rem, G.fn0);
         const int ix = rem - iy * G.n0;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        const int tz0 = P.zlo[iz], tz1 = P.zhi[iz], ty0 = P.ylo[iy], ty1 = P.yhi[iy];
-        const int tx0 = P.xlo[ix], tx1 = P.xhi[ix];
-        for (int tz = tz0; tz <= tz1; ++tz) {
-            const int bz = iz - P.zb0[tz];
-            for (int ty = ty0; ty <= ty1; ++ty) {
-                const int by = iy - P.yb0[ty];
-                for (int tx = tx0; tx <= tx1; ++tx) {
-                    const int bx = ix - P.xb0[tx];
-                    const long long t = ((long long)tz * P.nty + ty) * P.ntx + tx;
-                    const float* pp = P.partial + t * 3 * box + (bz * P.pby + by) * P.pbx + bx;
+        // tile partials in a fixed order: lower tile before upper tile, z outermost
+        const int oz[2] = {__ldg(P.oz0 + iz), __ldg(P.oz1 + iz)};
+        const int oy[2] = {__ldg(P.oy0 + iy), __ldg(P.oy1 + iy)};
+        const int ox[2] = {__ldg(P.ox0 + ix), __ldg(P.ox1 + ix)};
+        const int box = P.box;
+#pragma unroll
+        for (int kz = 0; kz < 2; ++kz) {
+            if (oz[kz] < 0) continue;
+#pragma unroll
+            for (int ky = 0; ky < 2; ++ky) {
+                if (oy[ky] < 0) continue;
+#pragma unroll
+                for (int kx = 0; kx < 2; ++kx) {
+                    if (ox[kx] < 0) continue;
+                    const float* pp = P.partial + (oz[kz] + oy[ky] + ox[kx]);
                     s0 += __ldg(pp);
                     s1 += __ldg(pp + box);
                     s2 += __ldg(pp + 2 * box);
@@ -892,7 +913,15 @@ __global__ void __launch_bounds__(NT) k_pcg_init(PcgParams P) {
     }
 }
 
-// after q = A d and sc[PS_DQ] = d.q: x += a d, r -= a q, z = M^-1 r, new delta
+// after q = A d and sc[PS_DQ] = d.q: x += a d, r -= a q, z = M^-1 r, new delta.
+// With P.vec4 (all vectors 16-byte aligned) the body moves float4 groups;
+// the elements past the last full group are handled one by one.
+__device__ __forceinline__ float pcg_elem(float a, float dv, float qv, float& xv, float& rv, float diag) {
+    xv = fmaf(a, dv, xv);
+    rv = fmaf(-a, qv, rv);
+    return rv * (diag > 0.f ? 1.f / diag : 0.f);
+}
+
 __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
     __shared__ double red[NT];
     const double st = P.sc[PS_STATUS];
@@ -903,12 +932,36 @@ __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
     DFAcc sa, sb;
     if (active) {
         const unsigned int n = (unsigned int)P.n;
-        for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
-            const float dv = P.d[i];
-            P.x[i] = fmaf(a, dv, P.x[i]);
-            const float rv = fmaf(-a, P.q[i], P.r[i]);
+        const unsigned int n4 = P.vec4 ? n / 4 : 0;
+        const unsigned int stride = gridDim.x * NT;
+        for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n4; i += stride) {
+            const float4 dv = reinterpret_cast<const float4*>(P.d)[i];
+            const float4 qv = reinterpret_cast<const float4*>(P.q)[i];
+            const float4 gv = reinterpret_cast<const float4*>(P.diag)[i];
+            float4 xv = reinterpret_cast<const float4*>(P.x)[i];
+            float4 rv = reinterpret_cast<const float4*>(P.r)[i];
+            float4 zv;
+            zv.x = pcg_elem(a, dv.x, qv.x, xv.x, rv.x, gv.x);
+            zv.y = pcg_elem(a, dv.y, qv.y, xv.y, rv.y, gv.y);
+            zv.z = pcg_elem(a, dv.z, qv.z, xv.z, rv.z, gv.z);
+            zv.w = pcg_elem(a, dv.w, qv.w, xv.w, rv.w, gv.w);
+            reinterpret_cast<float4*>(P.x)[i] = xv;
+            reinterpret_cast<float4*>(P.r)[i] = rv;
+            reinterpret_cast<float4*>(P.z)[i] = zv;
+            sa.add_prod(rv.x, zv.x);
+            sa.add_prod(rv.y, zv.y);
+            sa.add_prod(rv.z, zv.z);
+            sa.add_prod(rv.w, zv.w);
+            sb.add_prod(rv.x, rv.x);
+            sb.add_prod(rv.y, rv.y);
+            sb.add_prod(rv.z, rv.z);
+            sb.add_prod(rv.w, rv.w);
+        }
+        for (unsigned int i = 4 * n4 + blockIdx.x * NT + threadIdx.x; i < n; i += stride) {
+            float xv = P.x[i], rv = P.r[i];
+            const float zv = pcg_elem(a, P.d[i], P.q[i], xv, rv, P.diag[i]);
+            P.x[i] = xv;
             P.r[i] = rv;
-            const float zv = rv * minv(P.diag, i);
             P.z[i] = zv;
             sa.add_prod(rv, zv);
             sb.add_prod(rv, rv);
@@ -935,7 +988,18 @@ __global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) {
     if (P.sc[PS_STATUS] != 0.0) return;
     const float beta = (float)P.sc[PS_BETA];
     const unsigned int n = (unsigned int)P.n;
-    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) P.d[i] = fmaf(beta, P.d[i], P.z[i]);
+    const unsigned int n4 = P.vec4 ? n / 4 : 0;
+    const unsigned int stride = gridDim.x * NT;
+    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n4; i += stride) {
+        const float4 zv = reinterpret_cast<const float4*>(P.z)[i];
+        float4 dv = reinterpret_cast<const float4*>(P.d)[i];
+        dv.x = fmaf(beta, dv.x, zv.x);
+        dv.y = fmaf(beta, dv.y, zv.y);
+        dv.z = fmaf(beta, dv.z, zv.z);
+        dv.w = fmaf(beta, dv.w, zv.w);
+        reinterpret_cast<float4*>(P.d)[i] = dv;
+    }
+    for (unsigned int i = 4 * n4 + blockIdx.x * NT + threadIdx.x; i < n; i += stride) P.d[i] = fmaf(beta, P.d[i], P.z[i]);
 }
 
 // ---------------------------------------------------------------------------

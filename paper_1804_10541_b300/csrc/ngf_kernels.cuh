@@ -136,16 +136,13 @@ struct DFAcc {
 struct CombineParams {
     NodeGeom G;
     const float* partial;
-    int pbx, pby, pbz, ntx, nty;
-    const int* xlo;
-    const int* xhi;
-    const int* ylo;
-    const int* yhi;
-    const int* zlo;
-    const int* zhi;
-    const int* xb0;
-    const int* yb0;
-    const int* zb0;
+    int box;             // floats per component of one tile partial
+    const int* ox0;      // per-axis partial offsets of each node (lower tile;
+    const int* ox1;      // upper tile or -1), summed over the axes
+    const int* oy0;
+    const int* oy1;
+    const int* oz0;
+    const int* oz1;
     const float* L;      // Lap(input) for the curvature term (nullable)
     const float* ctab;   // curvature diagonal per axis, d1 | dg (nullable)
     float cscale;        // alpha 2 hbar^y
@@ -173,6 +170,7 @@ struct PcgParams {
     double* part;       // 2 * nblocks
     unsigned int* count;
     double rtol;
+    int vec4;           // every vector 16-byte aligned: float4 body
 };
 
 __host__ __device__ constexpr int ring_size(int halo) { return 2 * halo * (TX + 2 * halo) + 2 * halo * TY; }

@@ -16,15 +16,15 @@ namespace ngf {
 struct Geometry {
     int ntx = 0, nty = 0, ntz = 0;
     int pbx = 0, pby = 0, pbz = 0;
-    int* xlo = nullptr;
-    int* xhi = nullptr;
-    int* ylo = nullptr;
-    int* yhi = nullptr;
-    int* zlo = nullptr;
-    int* zhi = nullptr;
-    int* xb0 = nullptr;
-    int* yb0 = nullptr;
-    int* zb0 = nullptr;
+    // per axis and node: offsets (into the partial array, summed over the
+    // three axes) of the node in the lower and the upper tile that cover it;
+    // the upper one is -1 when a single tile covers the node
+    int* ox0 = nullptr;
+    int* ox1 = nullptr;
+    int* oy0 = nullptr;
+    int* oy1 = nullptr;
+    int* oz0 = nullptr;
+    int* oz1 = nullptr;
     int* mem = nullptr;
     long long tiles() const { return (long long)ntx * nty * ntz; }
     long long partial_floats() const { return tiles() * 3 * pbz * pby * pbx; }
