@@ -169,30 +169,35 @@ static ngf_status build_geometry(Plan* p, int halo, const std::vector<int>* f, G
     const long long box = (long long)g.pbx * g.pby * g.pbz;
     const long long tile_stride[3] = {3 * box, (long long)g.ntx * 3 * box, (long long)g.ntx * g.nty * 3 * box};
     const long long in_stride[3] = {1, g.pbx, (long long)g.pbx * g.pby};
-    const size_t total = 2 * (size_t)(p->n[0] + p->n[1] + p->n[2]);
+    const size_t total = 2 * (size_t)(p->n[0] + p->n[1] + p->n[2]) + nt[0] + nt[1] + nt[2];
     std::vector<int> h(total);
     size_t o = 0;
-    size_t off[6];
+    size_t off[9];
     for (int a = 0; a < 3; ++a) {
         off[2 * a] = o;
-        off[2 * a + 1] = o + p->n[a];
-        for (int k = 0; k < p->n[a]; ++k) {
-            const int t0 = lo[a][k], t1 = hi[a][k];
-            if (t1 - t0 > 1) return set_error(p, NGF_EINVAL, "internal: node covered by more than two tiles");
-            h[o + k] = (int)(t0 * tile_stride[a] + (k - b0[a][t0]) * in_stride[a]);
-            h[o + p->n[a] + k] = (t1 > t0) ? (int)(t1 * tile_stride[a] + (k - b0[a][t1]) * in_stride[a]) : -1;
-        }
-        o += 2 * p->n[a];
+        std::copy(lo[a].begin(), lo[a].end(), h.begin() + o);
+        o += p->n[a];
+        off[2 * a + 1] = o;
+        std::copy(hi[a].begin(), hi[a].end(), h.begin() + o);
+        o += p->n[a];
+    }
+    for (int a = 0; a < 3; ++a) {
+        off[6 + a] = o;
+        for (int t = 0; t < nt[a]; ++t) h[o + t] = (int)(t * tile_stride[a] - b0[a][t] * in_stride[a]);
+        o += nt[a];
     }
     NGF_CU(p, dev_alloc((void**)&g.mem, total * sizeof(int), p->stream), "allocate geometry");
     NGF_CU(p, cudaMemcpyAsync(g.mem, h.data(), total * sizeof(int), cudaMemcpyHostToDevice, p->stream), "copy geometry");
     NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
-    g.ox0 = g.mem + off[0];
-    g.ox1 = g.mem + off[1];
-    g.oy0 = g.mem + off[2];
-    g.oy1 = g.mem + off[3];
-    g.oz0 = g.mem + off[4];
-    g.oz1 = g.mem + off[5];
+    g.xlo = g.mem + off[0];
+    g.xhi = g.mem + off[1];
+    g.ylo = g.mem + off[2];
+    g.yhi = g.mem + off[3];
+    g.zlo = g.mem + off[4];
+    g.zhi = g.mem + off[5];
+    g.xtb = g.mem + off[6];
+    g.ytb = g.mem + off[7];
+    g.ztb = g.mem + off[8];
     return NGF_OK;
 }
 
@@ -281,6 +286,30 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     std::vector<int> f[3];
     std::vector<float> w[3];
     for (int a = 0; a < 3; ++a) pw_table(p->m[a], p->n[a], f[a], w[a]);
+    // diagonal variant: a three-node span per axis needs two or more voxels per
+    // cell; the per-row windows then hold at most PXW x-nodes
+    {
+        bool span3 = true;
+        for (int a = 0; a < 3; ++a) span3 = span3 && 2 * (p->n[a] - 1) <= p->m[a];
+        // runs of equal keys as the kernel's lanes see them: lane l of a tile
+        // starting at xs holds the floor of voxel xs - 1 + l (clamped)
+        int longest[2] = {1, 1}, widest = 0;  // first x tile (clamped lane 0), the others
+        for (int xs = 0; xs < p->m[0]; xs += TX) {
+            const int txe = std::min(TX, p->m[0] - xs);
+            int run = 1;
+            for (int l = 1; l < txe; ++l) {
+                const int k0 = f[0][std::max(xs - 2 + l, 0)], k1 = f[0][std::max(xs - 1 + l, 0)];
+                run = (k1 == k0) ? run + 1 : 1;
+                longest[xs > 0] = std::max(longest[xs > 0], run);
+            }
+            widest = std::max(widest, f[0][std::min(xs + TX, p->m[0] - 1)] + 2 - f[0][std::max(xs - 1, 0)]);
+        }
+        for (int k = 0; k < 2; ++k) {
+            p->dsteps[k] = 0;
+            while ((1 << p->dsteps[k]) < std::min(longest[k], TX)) ++p->dsteps[k];
+        }
+        p->diag_private = span3 && widest <= PXW;
+    }
     const size_t tl = (size_t)p->m[0] + p->m[1] + p->m[2];
     std::vector<int> fh;
     std::vector<float> wh;
@@ -376,6 +405,8 @@ ImgParams img_params(const Plan* p, const float* R, const float* T, const float*
     P.wy = p->wtab + p->m[0];
     P.wz = p->wtab + p->m[0] + p->m[1];
     P.zc = p->zc;
+    P.dsteps0 = p->dsteps[0];
+    P.dsteps = p->dsteps[1];
     P.pbx = g.pbx;
     P.pby = g.pby;
     P.pbz = g.pbz;
@@ -392,12 +423,17 @@ CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const
     C.G = node_geom(p);
     C.partial = p->partial;
     C.box = g.pbx * g.pby * g.pbz;
-    C.ox0 = g.ox0;
-    C.ox1 = g.ox1;
-    C.oy0 = g.oy0;
-    C.oy1 = g.oy1;
-    C.oz0 = g.oz0;
-    C.oz1 = g.oz1;
+    C.pbx = g.pbx;
+    C.pbxy = g.pbx * g.pby;
+    C.xlo = g.xlo;
+    C.xhi = g.xhi;
+    C.ylo = g.ylo;
+    C.yhi = g.yhi;
+    C.zlo = g.zlo;
+    C.zhi = g.zhi;
+    C.xtb = g.xtb;
+    C.ytb = g.ytb;
+    C.ztb = g.ztb;
     C.L = L;
     C.ctab = ctab;
     C.cscale = (float)(p->desc.alpha * 2.0 * p->hbary);
@@ -453,8 +489,8 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
 ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g1, nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
-    const bool span3 = 2 * (p->n[0] - 1) <= p->m[0] && 2 * (p->n[1] - 1) <= p->m[1] && 2 * (p->n[2] - 1) <= p->m[2];
-    NGF_CU(p, launch(span3 ? k_diag : k_diag4, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P), "k_diag");
+    NGF_CU(p, launch(p->diag_private ? k_diag : k_diag4, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P),
+           "k_diag");
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g1, diag, nullptr, p->ctab, nullptr, nullptr);
     NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");

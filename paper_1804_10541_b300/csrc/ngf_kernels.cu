@@ -501,9 +501,19 @@ __global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) { image
 // entry's voxel, using the separable structure of P:
 //   J(a,b,g) = ez ey ax + ez by ex + cz ey ex
 // with e* the weights of voxel i itself and ax/by/cz the coefficient-weighted
-// weights of its x/y/z stencil entries.  Rows of the owned columns scatter
-// their squared entries into shared node-plane accumulators (4 live planes),
-// which are stored as tile partials of the halo-1 geometry.
+// weights of its x/y/z stencil entries.  The squared entries of the owned
+// rows are summed onto node planes (four live planes), which are stored as
+// tile partials of the halo-1 geometry.
+//
+// SPAN 3 (two or more voxels per cell on every axis): each warp is one row of
+// the tile and owns a private accumulator window (4 planes x 3 components x
+// 3 y-nodes x PXW x-nodes).  Lanes whose voxels share an x-node floor form
+// runs; a segmented shuffle sum gives each run's total to its first lane,
+// which alone adds it (plain read-modify-write, distinct addresses).  The
+// windows of the rows are merged in a fixed order when a node plane is
+// complete, so the diagonal is deterministic.
+// SPAN 4 (some axis with fewer than two voxels per cell): shared-memory
+// atomics into one window for the whole tile.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float pw_weight(int f, float w1, int node) {
     return (node == f) ? 1.f - w1 : ((node == f + 1) ? w1 : 0.f);
@@ -513,6 +523,7 @@ template <int SPAN>
 __device__ __forceinline__ void diag_pass(const ImgParams& P) {
     NGF_DYNAMIC_SMEM(smraw);
     DiagSmem& S = *reinterpret_cast<DiagSmem*>(smraw);
+    constexpr bool PRIV = (SPAN == 3);
     const int tid = threadIdx.x;
     const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
     const int z0 = blockIdx.z * P.zc, z1 = min(P.m2, z0 + P.zc);
@@ -535,8 +546,29 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
         S.fy1[i] = P.fy[gy] - UY0;
         S.wy1[i] = P.wy[gy];
     }
-    for (int i = tid; i < 4 * 3 * DBY * DBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
+    for (int i = tid; i < (PRIV ? DIAG_PRIVATE : DIAG_SHARED); i += NT) S.Acc[i] = 0.f;
     __syncthreads();
+
+    // lane layout of the owned columns: warp = row ly, lane = lx
+    const int lx = tid % TX, ly = tid / TX;
+    const bool act = lx < txe;
+    const int lxc = min(lx, txe - 1);  // inactive lanes mirror the last column, contribute zero
+    // runs of lanes sharing the x-node floor of the stencil's lowest voxel
+    const int dsteps = (xs == 0) ? P.dsteps0 : P.dsteps;
+    unsigned int same = 0u;
+    bool head = true;
+    if (PRIV) {
+        const int key = S.fx1[lxc];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int o = __shfl_down_sync(0xffffffffu, key, 1 << k);
+            if (k < dsteps && lx + (1 << k) < TX && o == key) same |= 1u << k;
+        }
+        const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+        head = (lx == 0) || (prev != key);
+    }
+    constexpr int WPLANE = 3 * 3 * PXW;  // one plane of a row's private window
+    float* const priv = S.Acc + ly * (4 * WPLANE);
 
     const int items = 3 * nby * nbx;
     int next = BZ0;  // next node plane to store
@@ -564,14 +596,14 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
         if (fe) {
             const int slot = zf % 3;
             for (int k = tid; k < NT + ring_size(1); k += NT) {
-                int lx, ly;
-                if (k < NT) { lx = k % TX; ly = k / TX; }
-                else ring_coord(k - NT, 1, lx, ly);
-                const int gx = xs + lx, gy = ys + ly;
+                int cx, cy;
+                if (k < NT) { cx = k % TX; cy = k / TX; }
+                else ring_coord(k - NT, 1, cx, cy);
+                const int gx = xs + cx, gy = ys + cy;
                 if (gx < 0 || gx >= P.m0 || gy < 0 || gy >= P.m1) continue;
-                const int li = (ly + 1) * SX1 + (lx + 1);
-                const int ax = S.fx1[lx + 1], ay = S.fy1[ly + 1];
-                const float wxv = S.wx1[lx + 1], wyv = S.wy1[ly + 1];
+                const int li = (cy + 1) * SX1 + (cx + 1);
+                const int ax = S.fx1[cx + 1], ay = S.fy1[cy + 1];
+                const float wxv = S.wx1[cx + 1], wyv = S.wy1[cy + 1];
                 float uh[3];
                 for (int c = 0; c < 3; ++c) {
                     const float v00 = S.Uz[c][ay][ax], v10 = S.Uz[c][ay][ax + 1];
@@ -592,102 +624,107 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
         }
         __syncthreads();
         const int zq = zf - 1;
-        if (zq >= z0 && zq < z1) {
-            const int lx = tid % TX, ly = tid / TX;
-            if (lx < txe && ly < tye) {
-                const int gx = xs + lx, gy = ys + ly;
-                const int sc = zq % 3;
-                const int szm = (zq > 0 ? zq - 1 : zq) % 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) % 3;
-                const int li = (ly + 1) * SX1 + (lx + 1);
-                const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
-                const int ym = (gy > 0) ? li - SX1 : li, yp = (gy < P.m1 - 1) ? li + SX1 : li;
-                const float r0 = S.R[sc][li], t0 = S.Tw[sc][li];
-                const float dR[6] = {S.R[szm][li] - r0, S.R[sc][ym] - r0, S.R[sc][xm] - r0,
-                                     S.R[sc][xp] - r0, S.R[sc][yp] - r0, S.R[szp][li] - r0};
-                const float dTv[6] = {S.Tw[szm][li] - t0, S.Tw[sc][ym] - t0, S.Tw[sc][xm] - t0,
-                                      S.Tw[sc][xp] - t0, S.Tw[sc][yp] - t0, S.Tw[szp][li] - t0};
-                const float ihs[6] = {P.ihs[2], P.ihs[1], P.ihs[0], P.ihs[0], P.ihs[1], P.ihs[2]};
-                float nn = 0.f, a2 = 0.f, b2 = 0.f;
+        if (zq >= z0 && zq < z1 && ly < tye) {  // whole warps (rows) only
+            const int gx = xs + lxc, gy = ys + ly;
+            const int sc = zq % 3;
+            const int szm = (zq > 0 ? zq - 1 : zq) % 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) % 3;
+            const int li = (ly + 1) * SX1 + (lxc + 1);
+            const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
+            const int ym = (gy > 0) ? li - SX1 : li, yp = (gy < P.m1 - 1) ? li + SX1 : li;
+            const float r0 = S.R[sc][li], t0 = S.Tw[sc][li];
+            const float dR[6] = {S.R[szm][li] - r0, S.R[sc][ym] - r0, S.R[sc][xm] - r0,
+                                 S.R[sc][xp] - r0, S.R[sc][yp] - r0, S.R[szp][li] - r0};
+            const float dTv[6] = {S.Tw[szm][li] - t0, S.Tw[sc][ym] - t0, S.Tw[sc][xm] - t0,
+                                  S.Tw[sc][xp] - t0, S.Tw[sc][yp] - t0, S.Tw[szp][li] - t0};
+            const float ihs[6] = {P.ihs[2], P.ihs[1], P.ihs[0], P.ihs[0], P.ihs[1], P.ihs[2]};
+            float nn = 0.f, a2 = 0.f, b2 = 0.f;
 #pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    nn = fmaf(dTv[j] * dR[j], ihs[j], nn);
-                    a2 = fmaf(dTv[j] * dTv[j], ihs[j], a2);
-                    b2 = fmaf(dR[j] * dR[j], ihs[j], b2);
-                }
-                nn = fmaf(0.5f, nn, P.tr);
-                a2 = fmaf(0.5f, a2, P.tau2);
-                b2 = fmaf(0.5f, b2, P.rho2);
-                const float c1 = rsqrtf(a2 * b2);
-                const float c2 = nn * c1 / a2;
-                const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
-                float rh[6], rs = 0.f;
+            for (int j = 0; j < 6; ++j) {
+                nn = fmaf(dTv[j] * dR[j], ihs[j], nn);
+                a2 = fmaf(dTv[j] * dTv[j], ihs[j], a2);
+                b2 = fmaf(dR[j] * dR[j], ihs[j], b2);
+            }
+            nn = fmaf(0.5f, nn, P.tr);
+            a2 = fmaf(0.5f, a2, P.tau2);
+            b2 = fmaf(0.5f, b2, P.rho2);
+            const float c1 = rsqrtf(a2 * b2);
+            const float c2 = nn * c1 / a2;
+            const float hh[6] = {P.hh[2], P.hh[1], P.hh[0], P.hh[0], P.hh[1], P.hh[2]};
+            float rh[6], rs = 0.f;
 #pragma unroll
-                for (int j = 0; j < 6; ++j) {
-                    rh[j] = hh[j] * fmaf(dR[j], c1, -dTv[j] * c2);
-                    rs += rh[j];
-                }
-                const float rh0 = -rs;
-                // node floors and weights of the stencil entries' voxels (clamped)
-                const int vzm = max(zq - 1, 0), vzp = min(zq + 1, P.m2 - 1);
-                const int fxm = S.fx1[lx], fxc = S.fx1[lx + 1], fxp = S.fx1[lx + 2];
-                const float wxm = S.wx1[lx], wxc = S.wx1[lx + 1], wxp = S.wx1[lx + 2];
-                const int fym = S.fy1[ly], fyc = S.fy1[ly + 1], fyp = S.fy1[ly + 2];
-                const float wym = S.wy1[ly], wyc = S.wy1[ly + 1], wyp = S.wy1[ly + 2];
-                const int fzm = P.fz[vzm] - BZ0, fzc = P.fz[zq] - BZ0, fzp = P.fz[vzp] - BZ0;
-                const float wzm = P.wz[vzm], wzc = P.wz[zq], wzp = P.wz[vzp];
-                const int bxm = fxm, bym = fym, bzm = fzm;  // lowest node touched per axis
-                // trilinear weights of the stencil voxels (offset -1, 0, +1 per
-                // axis) on the SPAN nodes from the lowest floor; independent of
-                // the component
-                float WX[3][SPAN], WY[3][SPAN], WZ[3][SPAN];
+            for (int j = 0; j < 6; ++j) {
+                rh[j] = hh[j] * fmaf(dR[j], c1, -dTv[j] * c2);
+                rs += rh[j];
+            }
+            const float rh0 = -rs;
+            // node floors and weights of the stencil entries' voxels (clamped)
+            const int vzm = max(zq - 1, 0), vzp = min(zq + 1, P.m2 - 1);
+            const int fxm = S.fx1[lxc], fxc = S.fx1[lxc + 1], fxp = S.fx1[lxc + 2];
+            const float wxm = S.wx1[lxc], wxc = S.wx1[lxc + 1], wxp = S.wx1[lxc + 2];
+            const int fym = S.fy1[ly], fyc = S.fy1[ly + 1], fyp = S.fy1[ly + 2];
+            const float wym = S.wy1[ly], wyc = S.wy1[ly + 1], wyp = S.wy1[ly + 2];
+            const int fzm = P.fz[vzm] - BZ0, fzc = P.fz[zq] - BZ0, fzp = P.fz[vzp] - BZ0;
+            const float wzm = P.wz[vzm], wzc = P.wz[zq], wzp = P.wz[vzp];
+            const int bxm = fxm, bym = fym, bzm = fzm;  // lowest node touched per axis
+            // trilinear weights of the stencil voxels (offset -1, 0, +1 per
+            // axis) on the SPAN nodes from the lowest floor; independent of
+            // the component
+            float WX[3][SPAN], WY[3][SPAN], WZ[3][SPAN];
+#pragma unroll
+            for (int a = 0; a < SPAN; ++a) {
+                WX[0][a] = pw_weight(fxm, wxm, bxm + a);
+                WX[1][a] = pw_weight(fxc, wxc, bxm + a);
+                WX[2][a] = pw_weight(fxp, wxp, bxm + a);
+                WY[0][a] = pw_weight(fym, wym, bym + a);
+                WY[1][a] = pw_weight(fyc, wyc, bym + a);
+                WY[2][a] = pw_weight(fyp, wyp, bym + a);
+                WZ[0][a] = pw_weight(fzm, wzm, bzm + a);
+                WZ[1][a] = pw_weight(fzc, wzc, bzm + a);
+                WZ[2][a] = pw_weight(fzp, wzp, bzm + a);
+            }
+            int po[SPAN];
+#pragma unroll
+            for (int g = 0; g < SPAN; ++g)
+                po[g] = PRIV ? ((bzm + g + BZ0) & 3) * WPLANE + bxm
+                             : ((bzm + g + BZ0) & 3) * (3 * DBY * DBX) + bym * DBX + bxm;
+#pragma unroll 1
+            for (int d = 0; d < 3; ++d) {
+                const float* dTd[3] = {S.dT[szm][d], S.dT[sc][d], S.dT[szp][d]};
+                const float cc = rh0 * dTd[1][li];
+                const float cxm = rh[2] * dTd[1][xm], cxp = rh[3] * dTd[1][xp];
+                const float cym = rh[1] * dTd[1][ym], cyp = rh[4] * dTd[1][yp];
+                const float czm = rh[0] * dTd[0][li], czp = rh[5] * dTd[2][li];
+                float ax[SPAN], byv[SPAN], cz[SPAN];
 #pragma unroll
                 for (int a = 0; a < SPAN; ++a) {
-                    WX[0][a] = pw_weight(fxm, wxm, bxm + a);
-                    WX[1][a] = pw_weight(fxc, wxc, bxm + a);
-                    WX[2][a] = pw_weight(fxp, wxp, bxm + a);
-                    WY[0][a] = pw_weight(fym, wym, bym + a);
-                    WY[1][a] = pw_weight(fyc, wyc, bym + a);
-                    WY[2][a] = pw_weight(fyp, wyp, bym + a);
-                    WZ[0][a] = pw_weight(fzm, wzm, bzm + a);
-                    WZ[1][a] = pw_weight(fzc, wzc, bzm + a);
-                    WZ[2][a] = pw_weight(fzp, wzp, bzm + a);
+                    ax[a] = fmaf(cc, WX[1][a], fmaf(cxm, WX[0][a], cxp * WX[2][a]));
+                    byv[a] = fmaf(cym, WY[0][a], cyp * WY[2][a]);
+                    cz[a] = fmaf(czm, WZ[0][a], czp * WZ[2][a]);
                 }
-                constexpr int PLANE = 3 * DBY * DBX;
-                int po[SPAN];
+                // entries outside the support are exactly zero, so only the box
+                // bounds are checked; the 2 hbar factor is applied at the store
 #pragma unroll
-                for (int g = 0; g < SPAN; ++g) po[g] = ((bzm + g + BZ0) & 3) * PLANE + bym * DBX + bxm;
-                float* acc = &S.Acc[0][0][0][0];
-#pragma unroll 1
-                for (int d = 0; d < 3; ++d) {
-                    const float* dTd[3] = {S.dT[szm][d], S.dT[sc][d], S.dT[szp][d]};
-                    const float cc = rh0 * dTd[1][li];
-                    const float cxm = rh[2] * dTd[1][xm], cxp = rh[3] * dTd[1][xp];
-                    const float cym = rh[1] * dTd[1][ym], cyp = rh[4] * dTd[1][yp];
-                    const float czm = rh[0] * dTd[0][li], czp = rh[5] * dTd[2][li];
-                    // row entries J(a,b,g) = ez (ey ax + by ex) + cz ey ex with e*
-                    // the voxel's own weights and a*/b*/c* the coefficient-weighted
-                    // weights of its x / y / z stencil entries
-                    float ax[SPAN], byv[SPAN], cz[SPAN];
+                for (int b = 0; b < SPAN; ++b) {
+                    if (bym + b >= nby) continue;  // uniform over the warp
 #pragma unroll
                     for (int a = 0; a < SPAN; ++a) {
-                        ax[a] = fmaf(cc, WX[1][a], fmaf(cxm, WX[0][a], cxp * WX[2][a]));
-                        byv[a] = fmaf(cym, WY[0][a], cyp * WY[2][a]);
-                        cz[a] = fmaf(czm, WZ[0][a], czp * WZ[2][a]);
-                    }
-                    float* accd = acc + d * DBY * DBX;
-                    // entries outside the support are exactly zero, so only the
-                    // box bounds are checked; the 2 hbar factor is applied at the store
+                        const bool inb = bxm + a < nbx;
+                        const float xy1 = fmaf(WY[1][b], ax[a], byv[b] * WX[1][a]);
+                        const float xy2 = WY[1][b] * WX[1][a];
 #pragma unroll
-                    for (int b = 0; b < SPAN; ++b) {
+                        for (int g = 0; g < SPAN; ++g) {
+                            const float J = fmaf(WZ[1][g], xy1, cz[g] * xy2);
+                            float v = act ? J * J : 0.f;
+                            if (PRIV) {
 #pragma unroll
-                        for (int a = 0; a < SPAN; ++a) {
-                            if (bxm + a >= nbx || bym + b >= nby) continue;
-                            const float xy1 = fmaf(WY[1][b], ax[a], byv[b] * WX[1][a]);
-                            const float xy2 = WY[1][b] * WX[1][a];
-#pragma unroll
-                            for (int g = 0; g < SPAN; ++g) {
-                                const float J = fmaf(WZ[1][g], xy1, cz[g] * xy2);
-                                atomicAdd(accd + po[g] + b * DBX + a, J * J);
+                                for (int k = 0; k < 5; ++k) {
+                                    if (k >= dsteps) break;
+                                    const float t = __shfl_down_sync(0xffffffffu, v, 1 << k);
+                                    if (same & (1u << k)) v += t;
+                                }
+                                if (head && inb) priv[po[g] + (d * 3 + b) * PXW + a] += v;
+                            } else if (act && inb) {
+                                atomicAdd(S.Acc + po[g] + d * DBY * DBX + b * DBX + a, v);
                             }
                         }
                     }
@@ -699,12 +736,25 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
         if (zq >= z0 && zq < z1) {
             const int limit = (zq == z1 - 1) ? BZ1 + 1 : P.fz[zq];
             while (next < limit) {
+                const int sl = next & 3;
                 for (int i = tid; i < items; i += NT) {
                     const int c = i / (nby * nbx), rem = i % (nby * nbx), byy = rem / nbx, bxx = rem % nbx;
-                    float& a = S.Acc[next & 3][c][byy][bxx];
+                    float sum = 0.f;
+                    if (PRIV) {  // rows in a fixed order
+                        for (int w = 0; w < tye; ++w) {
+                            const int b = byy - S.fy1[w];
+                            if (b < 0 || b > 2) continue;
+                            float& e = S.Acc[w * (4 * WPLANE) + sl * WPLANE + (c * 3 + b) * PXW + bxx];
+                            sum += e;
+                            e = 0.f;
+                        }
+                    } else {
+                        float& e = S.Acc[sl * (3 * DBY * DBX) + (c * DBY + byy) * DBX + bxx];
+                        sum = e;
+                        e = 0.f;
+                    }
                     P.partial[((tile * 3 + c) * P.pbz + (next - BZ0)) * (long long)(P.pby * P.pbx) + byy * P.pbx + bxx] =
-                        twoh * a;
-                    a = 0.f;
+                        twoh * sum;
                 }
                 ++next;
             }
@@ -782,21 +832,16 @@ __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
         const int iy = (int)fdiv((unsigned int)rem, G.fn0);
         const int ix = rem - iy * G.n0;
         float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        // tile partials in a fixed order: lower tile before upper tile, z outermost
-        const int oz[2] = {__ldg(P.oz0 + iz), __ldg(P.oz1 + iz)};
-        const int oy[2] = {__ldg(P.oy0 + iy), __ldg(P.oy1 + iy)};
-        const int ox[2] = {__ldg(P.ox0 + ix), __ldg(P.ox1 + ix)};
+        // tile partials in a fixed order: ascending tiles, z outermost
         const int box = P.box;
-#pragma unroll
-        for (int kz = 0; kz < 2; ++kz) {
-            if (oz[kz] < 0) continue;
-#pragma unroll
-            for (int ky = 0; ky < 2; ++ky) {
-                if (oy[ky] < 0) continue;
-#pragma unroll
-                for (int kx = 0; kx < 2; ++kx) {
-                    if (ox[kx] < 0) continue;
-                    const float* pp = P.partial + (oz[kz] + oy[ky] + ox[kx]);
+        const int tz1 = __ldg(P.zhi + iz), ty0 = __ldg(P.ylo + iy), ty1 = __ldg(P.yhi + iy);
+        const int tx0 = __ldg(P.xlo + ix), tx1 = __ldg(P.xhi + ix);
+        for (int tz = __ldg(P.zlo + iz); tz <= tz1; ++tz) {
+            const int oz = __ldg(P.ztb + tz) + iz * P.pbxy;
+            for (int ty = ty0; ty <= ty1; ++ty) {
+                const int oy = oz + __ldg(P.ytb + ty) + iy * P.pbx;
+                for (int tx = tx0; tx <= tx1; ++tx) {
+                    const float* pp = P.partial + (oy + __ldg(P.xtb + tx) + ix);
                     s0 += __ldg(pp);
                     s1 += __ldg(pp + box);
                     s2 += __ldg(pp + 2 * box);

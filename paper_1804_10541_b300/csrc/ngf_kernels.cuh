@@ -30,6 +30,9 @@ constexpr int R0N = TX * TY;
 constexpr int UBX = TX + 5, UBY = TY + 5;       // node box of the halo-2 region (ratio >= 1)
 constexpr int NBX = TX + 1, NBY = TY + 1;       // node box of the owned columns
 constexpr int DBX = TX + 3, DBY = TY + 3;       // node box of the halo-1 region (diagonal)
+constexpr int PXW = 20;                          // x-node window of one warp row (two or more voxels per cell)
+constexpr int DIAG_SHARED = 4 * 3 * DBY * DBX, DIAG_PRIVATE = TY * 4 * 3 * 3 * PXW;
+constexpr int DIAG_ACC = DIAG_SHARED > DIAG_PRIVATE ? DIAG_SHARED : DIAG_PRIVATE;
 
 enum Mode { MODE_OBJ = 0, MODE_GRAD = 1, MODE_HESS = 2 };
 
@@ -53,6 +56,8 @@ struct ImgParams {
     const float* wy;
     const float* wz;
     int zc;                     // planes per z-chunk
+    int dsteps0, dsteps;        // diagonal: shuffle steps that sum a run of voxels sharing an x-node
+                                // floor, in the first x tile (clamped lane 0) and in the others
     int pbx, pby, pbz;          // partial box strides of this geometry
     float* partial;             // [tile][3][pbz][pby][pbx]
     double* dpart;              // per-CTA float64 partial sums (D)
@@ -81,7 +86,9 @@ struct DiagSmem {
     float Tw[3][R1N];
     float dT[3][3][R1N];        // [plane slot][component][column]
     float Uz[3][UBY][UBX];
-    float Acc[4][3][DBY][DBX];
+    // node-plane accumulators: shared by all rows (four live planes) with
+    // atomics, or one private window per warp row (see diag_pass)
+    float Acc[DIAG_ACC];
     float wx1[SX1], wy1[SY1];
     int fx1[SX1], fy1[SY1];     // node floor relative to the Uz (= partial) box
 };
@@ -137,12 +144,16 @@ struct CombineParams {
     NodeGeom G;
     const float* partial;
     int box;             // floats per component of one tile partial
-    const int* ox0;      // per-axis partial offsets of each node (lower tile;
-    const int* ox1;      // upper tile or -1), summed over the axes
-    const int* oy0;
-    const int* oy1;
-    const int* oz0;
-    const int* oz1;
+    int pbx, pbxy;       // in-box strides in y and z
+    const int* xlo;      // tiles [lo, hi] covering each node, per axis
+    const int* xhi;
+    const int* ylo;
+    const int* yhi;
+    const int* zlo;
+    const int* zhi;
+    const int* xtb;      // per-tile base offsets, summed over the axes
+    const int* ytb;
+    const int* ztb;
     const float* L;      // Lap(input) for the curvature term (nullable)
     const float* ctab;   // curvature diagonal per axis, d1 | dg (nullable)
     float cscale;        // alpha 2 hbar^y

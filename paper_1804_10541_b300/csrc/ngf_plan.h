@@ -16,15 +16,18 @@ namespace ngf {
 struct Geometry {
     int ntx = 0, nty = 0, ntz = 0;
     int pbx = 0, pby = 0, pbz = 0;
-    // per axis and node: offsets (into the partial array, summed over the
-    // three axes) of the node in the lower and the upper tile that cover it;
-    // the upper one is -1 when a single tile covers the node
-    int* ox0 = nullptr;
-    int* ox1 = nullptr;
-    int* oy0 = nullptr;
-    int* oy1 = nullptr;
-    int* oz0 = nullptr;
-    int* oz1 = nullptr;
+    // per axis: tiles [lo, hi] that cover each node, and per tile the base
+    // offset tb (into the partial array, summed over the three axes) such
+    // that the node's entry in tile t is at tb[t] + node * (in-box stride)
+    int* xlo = nullptr;
+    int* xhi = nullptr;
+    int* ylo = nullptr;
+    int* yhi = nullptr;
+    int* zlo = nullptr;
+    int* zhi = nullptr;
+    int* xtb = nullptr;
+    int* ytb = nullptr;
+    int* ztb = nullptr;
     int* mem = nullptr;
     long long tiles() const { return (long long)ntx * nty * ntz; }
     long long partial_floats() const { return tiles() * 3 * pbz * pby * pbx; }
@@ -37,6 +40,9 @@ struct Plan {
     long long M = 0, N = 0;
     double hbar = 0, hbary = 0, hy[3]{};
     int zc = 0;
+    bool diag_private = false;  // diagonal: per-row private windows (three-node span)
+    int dsteps[2] = {0, 0};     // diagonal: shuffle steps covering the longest run of equal x
+                                // floors in the first x tile and in the others
     int img_blocks = 0, diag_blocks = 0, node_blocks = 0, node1_blocks = 0;
     // device workspace
     int* ftab = nullptr;    // fx | fy | fz

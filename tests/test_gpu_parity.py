@@ -23,6 +23,7 @@ CASES = [
     ((70, 35, 21), (1.0, 1.0, 2.5), (36, 18, 11)), # 3 x 3 tiles, ragged, z-chunks
     ((40, 20, 10), (1.0, 1.0, 1.0), (41, 21, 11)), # ratio 1 on every axis
     ((65, 33, 40), (0.8, 0.8, 1.0), (17, 9, 11)),  # ratio 4, non-integer in z
+    ((30, 20, 60), (1.0, 1.0, 1.0), (4, 3, 2)),    # coarse grid: every z-chunk covers both node planes
 ]
 
 
@@ -110,8 +111,13 @@ def test_hessvec_is_deterministic(ngf):
         g1, g2 = c.empty(), c.empty()
         ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g1)
         ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g2)
+        # two or more voxels per cell on every axis: the diagonal sums its rows
+        # in a fixed order too
+        d1, d2 = c.empty(), c.empty()
+        ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, d1)
+        ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, d2)
         torch.cuda.synchronize()
-    assert torch.equal(q1, q2) and torch.equal(g1, g2)
+    assert torch.equal(q1, q2) and torch.equal(g1, g2) and torch.equal(d1, d2)
 
 
 def test_identity_and_identical_images(ngf):
