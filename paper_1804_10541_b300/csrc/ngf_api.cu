@@ -405,6 +405,9 @@ ImgParams img_params(const Plan* p, const float* R, const float* T, const float*
     P.wy = p->wtab + p->m[0];
     P.wz = p->wtab + p->m[0] + p->m[1];
     P.zc = p->zc;
+    P.ntx = g.ntx;
+    P.nty = g.nty;
+    P.ntz = g.ntz;
     P.dsteps0 = p->dsteps[0];
     P.dsteps = p->dsteps[1];
     P.pbx = g.pbx;

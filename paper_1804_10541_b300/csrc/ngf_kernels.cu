@@ -149,15 +149,15 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
 // just computed, so it shares S2's interval.
 // ---------------------------------------------------------------------------
 template <int MODE>
-__device__ __forceinline__ void image_pass(const ImgParams& P) {
+__device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, int bz) {
     NGF_DYNAMIC_SMEM(smraw);
     ImgSmem& S = *reinterpret_cast<ImgSmem*>(smraw);
     constexpr bool OBJ = (MODE == MODE_OBJ), HESS = (MODE == MODE_HESS);
     constexpr int FH = OBJ ? 1 : 2;  // front-end halo
     constexpr int NVEC = HESS ? 6 : 3;
     const int tid = threadIdx.x;
-    const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
-    const int z0 = blockIdx.z * P.zc, z1 = min(P.m2, z0 + P.zc);
+    const int xs = bx * TX, ys = by * TY;
+    const int z0 = bz * P.zc, z1 = min(P.m2, z0 + P.zc);
     const int txe = min(TX, P.m0 - xs), tye = min(TY, P.m1 - ys);
 
     // node box of the front-end region (z-interpolated node planes)
@@ -168,7 +168,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
     const int BX0 = P.fx[xs], BY0 = P.fy[ys], BZ0 = P.fz[z0];
     const int nbx = P.fx[xs + txe - 1] + 1 - BX0 + 1;
     const int nby = P.fy[ys + tye - 1] + 1 - BY0 + 1;
-    const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const long long tile = ((long long)bz * P.nty + by) * P.ntx + bx;
 
     for (int i = tid; i < SX2; i += NT) {
         const int gx = min(max(xs - 2 + i, 0), P.m0 - 1);
@@ -485,14 +485,20 @@ __device__ __forceinline__ void image_pass(const ImgParams& P) {
     }
     if (!HESS) {
         const double bs = block_sum(dacc, S.red);
-        const int nblocks = gridDim.x * gridDim.y * gridDim.z;
+        const int nblocks = P.ntx * P.nty * P.ntz;
         grid_sum_finish(bs, P.dpart, P.dcount, P.dout, P.hbar, S.red, nblocks, (int)tile);
     }
 }
 
-__global__ void __launch_bounds__(NT, 2) k_image_obj(const ImgParams P) { image_pass<MODE_OBJ>(P); }
-__global__ void __launch_bounds__(NT, 2) k_image_grad(const ImgParams P) { image_pass<MODE_GRAD>(P); }
-__global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) { image_pass<MODE_HESS>(P); }
+__global__ void __launch_bounds__(NT, 2) k_image_obj(const ImgParams P) {
+    image_pass<MODE_OBJ>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_image_grad(const ImgParams P) {
+    image_pass<MODE_GRAD>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) {
+    image_pass<MODE_HESS>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
 
 // ---------------------------------------------------------------------------
 // Exact Jacobi diagonal of the Gauss-Newton matrix (without the curvature
@@ -520,13 +526,13 @@ __device__ __forceinline__ float pw_weight(int f, float w1, int node) {
 }
 
 template <int SPAN>
-__device__ __forceinline__ void diag_pass(const ImgParams& P) {
+__device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, int bz) {
     NGF_DYNAMIC_SMEM(smraw);
     DiagSmem& S = *reinterpret_cast<DiagSmem*>(smraw);
     constexpr bool PRIV = (SPAN == 3);
     const int tid = threadIdx.x;
-    const int xs = blockIdx.x * TX, ys = blockIdx.y * TY;
-    const int z0 = blockIdx.z * P.zc, z1 = min(P.m2, z0 + P.zc);
+    const int xs = bx * TX, ys = by * TY;
+    const int z0 = bz * P.zc, z1 = min(P.m2, z0 + P.zc);
     const int txe = min(TX, P.m0 - xs), tye = min(TY, P.m1 - ys);
     const int UX0 = P.fx[max(xs - 1, 0)], UY0 = P.fy[max(ys - 1, 0)];
     const int UXn = P.fx[min(xs + TX, P.m0 - 1)] + 1 - UX0 + 1;
@@ -534,7 +540,7 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
     // the partial box of the halo-1 geometry equals the Uz box in x and y
     const int BZ0 = P.fz[max(z0 - 1, 0)], BZ1 = P.fz[min(z1, P.m2 - 1)] + 1;
     const int nbx = UXn, nby = UYn;
-    const long long tile = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    const long long tile = ((long long)bz * P.nty + by) * P.ntx + bx;
 
     for (int i = tid; i < SX1; i += NT) {
         const int gx = min(max(xs - 1 + i, 0), P.m0 - 1);
@@ -764,8 +770,10 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P) {
 
 // Three nodes per axis suffice when every axis has at least two voxels per
 // deformation cell (2 (n-1) <= m); four otherwise.
-__global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) { diag_pass<3>(P); }
-__global__ void __launch_bounds__(NT, 1) k_diag4(const ImgParams P) { diag_pass<4>(P); }
+__global__ void __launch_bounds__(NT, 1) k_diag(const ImgParams P) { diag_pass<3>(P, blockIdx.x, blockIdx.y, blockIdx.z); }
+__global__ void __launch_bounds__(NT, 1) k_diag4(const ImgParams P) {
+    diag_pass<4>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
 
 // ---------------------------------------------------------------------------
 // nodal kernels
@@ -794,13 +802,15 @@ __device__ __forceinline__ float lap_at(const float* __restrict__ xc, const Node
 
 // L = Lap x per component (Eq. laplace_discretized, clamped Neumann
 // neighbours); optional S = scale * sum L^2 (deterministic).  One thread per
-// node handles the three components.
-__global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L,
-                                            double* part, unsigned int* count, double* out, double scale) {
+// node handles the three components.  `bid`/`nb`: this CTA's index and the
+// CTA count of the launch (or of its segment in a batched launch).
+__device__ __forceinline__ void lap_body(const NodeGeom& G, const float* __restrict__ x, float* __restrict__ L,
+                                         double* part, unsigned int* count, double* out, double scale,
+                                         unsigned int bid, unsigned int nb) {
     __shared__ double red[NT];
     DFAcc acc;
     const unsigned int N = (unsigned int)G.N;
-    for (unsigned int n = blockIdx.x * NT + threadIdx.x; n < N; n += gridDim.x * NT) {
+    for (unsigned int n = bid * NT + threadIdx.x; n < N; n += nb * NT) {
         const int iz = (int)fdiv(n, G.fplane);
         const int rem = (int)n - iz * G.n0 * G.n1;
         const int iy = (int)fdiv((unsigned int)rem, G.fn0);
@@ -814,19 +824,24 @@ __global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict_
     }
     if (out) {
         const double bs = block_sum(acc.value(), red);
-        grid_sum_finish(bs, part, count, out, scale, red, gridDim.x, blockIdx.x);
+        grid_sum_finish(bs, part, count, out, scale, red, (int)nb, (int)bid);
     }
+}
+
+__global__ void __launch_bounds__(NT) k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L,
+                                            double* part, unsigned int* count, double* out, double scale) {
+    lap_body(G, x, L, part, count, out, scale, blockIdx.x, gridDim.x);
 }
 
 // out_{c,n} = sum of the tile partials containing node n (fixed order)
 //           + alpha 2 hbar^y (Lap L)_{c,n}   or   + alpha 2 hbar^y diag(Lap^T Lap)_n
 // One thread per node handles the three components.
-__global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
+__device__ __forceinline__ void combine_body(const CombineParams& P, unsigned int bid, unsigned int nb) {
     __shared__ double red[NT];
     DFAcc acc;
     const NodeGeom& G = P.G;
     const unsigned int N = (unsigned int)G.N;
-    for (unsigned int n = blockIdx.x * NT + threadIdx.x; n < N; n += gridDim.x * NT) {
+    for (unsigned int n = bid * NT + threadIdx.x; n < N; n += nb * NT) {
         const int iz = (int)fdiv(n, G.fplane);
         const int rem = (int)n - iz * G.n0 * G.n1;
         const int iy = (int)fdiv((unsigned int)rem, G.fn0);
@@ -875,9 +890,11 @@ __global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) {
     }
     if (P.dout) {
         const double bs = block_sum(acc.value(), red);
-        grid_sum_finish(bs, P.dpart, P.dcount, P.dout, 1.0, red, gridDim.x, blockIdx.x);
+        grid_sum_finish(bs, P.dpart, P.dcount, P.dout, 1.0, red, (int)nb, (int)bid);
     }
 }
+
+__global__ void __launch_bounds__(NT) k_node_combine(const CombineParams P) { combine_body(P, blockIdx.x, gridDim.x); }
 
 // q = scale * Lap(L) with L = Lap p, no partials (curvature_apply)
 __global__ void __launch_bounds__(NT) k_lap2(NodeGeom G, const float* __restrict__ L, float* __restrict__ q,
@@ -901,15 +918,14 @@ __device__ __forceinline__ float minv(const float* diag, unsigned int i) {
 // two deterministic float64 sums (e.g. r.z and r.r) finished by the last CTA;
 // returns true in thread 0 of the last CTA, with A and B set there
 __device__ __forceinline__ bool grid_sum2(double a, double b, double* part, unsigned int* count, double* red,
-                                          double& A, double& B) {
+                                          double& A, double& B, int nb, int bid) {
     __shared__ int is_last;
     const double sa = block_sum(a, red);
     __syncthreads();
     const double sb = block_sum(b, red);
-    const int nb = gridDim.x;
     if (threadIdx.x == 0) {
-        part[blockIdx.x] = sa;
-        part[nb + blockIdx.x] = sb;
+        part[bid] = sa;
+        part[nb + bid] = sb;
         __threadfence();
         is_last = (atomicAdd(count, 1u) == (unsigned int)(nb - 1));
     }
@@ -928,11 +944,11 @@ __device__ __forceinline__ bool grid_sum2(double a, double b, double* part, unsi
     return threadIdx.x == 0;
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_init(PcgParams P) {
+__device__ __forceinline__ void pcg_init_body(const PcgParams& P, unsigned int bid, unsigned int nb) {
     __shared__ double red[NT];
     DFAcc a, b;
     const unsigned int n = (unsigned int)P.n;
-    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n; i += gridDim.x * NT) {
+    for (unsigned int i = bid * NT + threadIdx.x; i < n; i += nb * NT) {
         const float rv = P.rhs[i];
         const float zv = rv * minv(P.diag, i);
         P.x[i] = 0.f;
@@ -943,7 +959,7 @@ __global__ void __launch_bounds__(NT) k_pcg_init(PcgParams P) {
         b.add_prod(rv, rv);
     }
     double A, B;
-    if (grid_sum2(a.value(), b.value(), P.part, P.count, red, A, B)) {
+    if (grid_sum2(a.value(), b.value(), P.part, P.count, red, A, B, (int)nb, (int)bid)) {
         P.sc[PS_DELTA] = A;
         P.sc[PS_RR] = B;
         P.sc[PS_BB] = B;
@@ -967,7 +983,7 @@ __device__ __forceinline__ float pcg_elem(float a, float dv, float qv, float& xv
     return rv * (diag > 0.f ? 1.f / diag : 0.f);
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
+__device__ __forceinline__ void pcg_update_body(const PcgParams& P, unsigned int bid, unsigned int nb) {
     __shared__ double red[NT];
     const double st = P.sc[PS_STATUS];
     const double dq = P.sc[PS_DQ];
@@ -978,8 +994,8 @@ __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
     if (active) {
         const unsigned int n = (unsigned int)P.n;
         const unsigned int n4 = P.vec4 ? n / 4 : 0;
-        const unsigned int stride = gridDim.x * NT;
-        for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n4; i += stride) {
+        const unsigned int stride = nb * NT;
+        for (unsigned int i = bid * NT + threadIdx.x; i < n4; i += stride) {
             const float4 dv = reinterpret_cast<const float4*>(P.d)[i];
             const float4 qv = reinterpret_cast<const float4*>(P.q)[i];
             const float4 gv = reinterpret_cast<const float4*>(P.diag)[i];
@@ -1002,7 +1018,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
             sb.add_prod(rv.z, rv.z);
             sb.add_prod(rv.w, rv.w);
         }
-        for (unsigned int i = 4 * n4 + blockIdx.x * NT + threadIdx.x; i < n; i += stride) {
+        for (unsigned int i = 4 * n4 + bid * NT + threadIdx.x; i < n; i += stride) {
             float xv = P.x[i], rv = P.r[i];
             const float zv = pcg_elem(a, P.d[i], P.q[i], xv, rv, P.diag[i]);
             P.x[i] = xv;
@@ -1013,7 +1029,7 @@ __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
         }
     }
     double A, B;
-    if (grid_sum2(sa.value(), sb.value(), P.part, P.count, red, A, B)) {
+    if (grid_sum2(sa.value(), sb.value(), P.part, P.count, red, A, B, (int)nb, (int)bid)) {
         if (st != 0.0) return;
         if (!active) {
             P.sc[PS_STATUS] = 2.0;
@@ -1029,13 +1045,13 @@ __global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) {
     }
 }
 
-__global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) {
+__device__ __forceinline__ void pcg_dir_body(const PcgParams& P, unsigned int bid, unsigned int nb) {
     if (P.sc[PS_STATUS] != 0.0) return;
     const float beta = (float)P.sc[PS_BETA];
     const unsigned int n = (unsigned int)P.n;
     const unsigned int n4 = P.vec4 ? n / 4 : 0;
-    const unsigned int stride = gridDim.x * NT;
-    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < n4; i += stride) {
+    const unsigned int stride = nb * NT;
+    for (unsigned int i = bid * NT + threadIdx.x; i < n4; i += stride) {
         const float4 zv = reinterpret_cast<const float4*>(P.z)[i];
         float4 dv = reinterpret_cast<const float4*>(P.d)[i];
         dv.x = fmaf(beta, dv.x, zv.x);
@@ -1044,27 +1060,38 @@ __global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) {
         dv.w = fmaf(beta, dv.w, zv.w);
         reinterpret_cast<float4*>(P.d)[i] = dv;
     }
-    for (unsigned int i = 4 * n4 + blockIdx.x * NT + threadIdx.x; i < n; i += stride) P.d[i] = fmaf(beta, P.d[i], P.z[i]);
+    for (unsigned int i = 4 * n4 + bid * NT + threadIdx.x; i < n; i += stride) P.d[i] = fmaf(beta, P.d[i], P.z[i]);
 }
+
+__global__ void __launch_bounds__(NT) k_pcg_init(PcgParams P) { pcg_init_body(P, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(NT) k_pcg_update(PcgParams P) { pcg_update_body(P, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) { pcg_dir_body(P, blockIdx.x, gridDim.x); }
 
 // ---------------------------------------------------------------------------
 // small vector kernels and multilevel helpers
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_dot(long long n, const float* __restrict__ a, const float* __restrict__ b,
-                                            double* part, unsigned int* count, double* out) {
+__device__ __forceinline__ void dot_body(const DotArgs& A, unsigned int bid, unsigned int nb) {
     __shared__ double red[NT];
     DFAcc acc;
-    for (unsigned int i = blockIdx.x * NT + threadIdx.x; i < (unsigned int)n; i += gridDim.x * NT)
-        acc.add_prod(a[i], b[i]);
+    for (unsigned int i = bid * NT + threadIdx.x; i < (unsigned int)A.n; i += nb * NT) acc.add_prod(A.a[i], A.b[i]);
     const double bs = block_sum(acc.value(), red);
-    grid_sum_finish(bs, part, count, out, 1.0, red, gridDim.x, blockIdx.x);
+    grid_sum_finish(bs, A.part, A.count, A.out, 1.0, red, (int)nb, (int)bid);
 }
 
-// y = x + eta * s (eta as float)
+__global__ void __launch_bounds__(NT) k_dot(long long n, const float* __restrict__ a, const float* __restrict__ b,
+                                            double* part, unsigned int* count, double* out) {
+    dot_body(DotArgs{n, a, b, part, count, out}, blockIdx.x, gridDim.x);
+}
+
+// y = x + eta * s (eta as float); y = x when s is null
+__device__ __forceinline__ void axpy_body(const AxpyArgs& A, unsigned int bid, unsigned int nb) {
+    for (long long i = (long long)bid * NT + threadIdx.x; i < A.n; i += (long long)nb * NT)
+        A.y[i] = A.s ? fmaf(A.eta, A.s[i], A.x[i]) : A.x[i];
+}
+
 __global__ void __launch_bounds__(NT) k_axpy(long long n, float eta, const float* __restrict__ x,
                                              const float* __restrict__ s, float* __restrict__ y) {
-    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
-        y[i] = fmaf(eta, s[i], x[i]);
+    axpy_body(AxpyArgs{n, eta, x, s, y}, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(NT) k_scale(long long n, float a, const float* __restrict__ x, float* __restrict__ y) {

@@ -56,6 +56,7 @@ struct ImgParams {
     const float* wy;
     const float* wz;
     int zc;                     // planes per z-chunk
+    int ntx, nty, ntz;          // tile grid of this geometry
     int dsteps0, dsteps;        // diagonal: shuffle steps that sum a run of voxels sharing an x-node
                                 // floor, in the first x tile (clamped lane 0) and in the others
     int pbx, pby, pbz;          // partial box strides of this geometry
@@ -182,6 +183,33 @@ struct PcgParams {
     unsigned int* count;
     double rtol;
     int vec4;           // every vector 16-byte aligned: float4 body
+};
+
+struct DotArgs {
+    long long n;
+    const float* a;
+    const float* b;
+    double* part;
+    unsigned int* count;
+    double* out;
+};
+
+struct AxpyArgs {
+    long long n;
+    float eta;
+    const float* x;
+    const float* s;  // null: copy
+    float* y;
+};
+
+struct LapArgs {
+    NodeGeom G;
+    const float* x;
+    float* L;
+    double* part;
+    unsigned int* count;
+    double* out;   // optional: scale * sum L^2
+    double scale;
 };
 
 __host__ __device__ constexpr int ring_size(int halo) { return 2 * halo * (TX + 2 * halo) + 2 * halo * TY; }
