@@ -199,6 +199,53 @@ ngf_status register_multilevel(const ngf_level_desc* finest, const ngf_options* 
                                const float* R, const float* T, float* u_out,
                                ngf_report* report, void* cuda_stream);
 
+/* ---- batched form: many independent pairs of uneven size ----------------
+ * A batch holds one plan per pair (own tile geometry, partials and scalars)
+ * and runs each stage of the method for all pairs in one launch: the image
+ * passes as a persistent grid that takes (pair, tile) work items, largest
+ * first, from a device queue; the nodal and PCG kernels with a contiguous
+ * range of thread blocks per pair.  Every pair's result is bitwise the one
+ * its own plan gives with the same z-chunk length.
+ * Pointer arguments R, T, u, p, q, grad, diag are HOST arrays of npairs
+ * DEVICE pointers laid out as for the single-pair calls; D and S are host
+ * arrays of npairs doubles.  Calls enqueue on the batch's stream; the
+ * objective and the autotuner synchronise it.
+ * zc: planes per z-chunk of the image-pass tiles (32 x 16 x zc voxels);
+ * 0 picks about two thread blocks per SM for each pair. */
+typedef struct ngf_batch ngf_batch;
+ngf_status ngf_batch_create(ngf_batch** batch, int32_t npairs, const ngf_level_desc* descs, int32_t zc,
+                            void* cuda_stream);
+ngf_status ngf_batch_destroy(ngf_batch* batch);
+ngf_status ngf_batch_objective(ngf_batch* batch, const float* const* R, const float* const* T,
+                               const float* const* u, double* D, double* S);
+ngf_status ngf_batch_gradient(ngf_batch* batch, const float* const* R, const float* const* T,
+                              const float* const* u, float* const* grad);
+ngf_status ngf_batch_hessvec(ngf_batch* batch, const float* const* R, const float* const* T,
+                             const float* const* u, const float* const* p, float* const* q);
+ngf_status ngf_batch_diagonal(ngf_batch* batch, const float* const* R, const float* const* T,
+                              const float* const* u, float* const* diag);
+/* Tile autotuner: times the batched Hessian-vector product (three calls
+ * after one warm-up, CUDA events) for each candidate z-chunk length in
+ * {8, 16, 24, 32, 48, 64} (capped by the deepest pair), rebuilds the batch
+ * with the fastest and returns it in *zc and the time per call in *ms.
+ * p and q are work vectors of each pair (contents of q are overwritten). */
+ngf_status ngf_batch_autotune(ngf_batch* batch, const float* const* R, const float* const* T,
+                              const float* const* u, const float* const* p, float* const* q,
+                              int32_t* zc, double* ms);
+int32_t ngf_batch_zc(const ngf_batch* batch);
+
+/* Multilevel Gauss-Newton registration of npairs independent pairs, the same
+ * options for all (u_init must be NULL): every Gauss-Newton stage is one
+ * batched launch sequence over the pairs still iterating, each PCG solve one
+ * captured CUDA graph (when opts->use_graph), each Armijo trial one batched
+ * objective over the pairs still searching.  Each pair takes exactly the
+ * decisions of register_multilevel on its own.  R, T, u_out: host arrays of
+ * npairs DEVICE pointers (finest level); reports: host array of npairs.
+ * autotune != 0 runs ngf_batch_autotune once per level.  Synchronises. */
+ngf_status register_batch(int32_t npairs, const ngf_level_desc* finest, const ngf_options* opts,
+                          const float* const* R, const float* const* T, float* const* u_out,
+                          ngf_report* reports, int32_t autotune, void* cuda_stream);
+
 /* ---- objective without any allocation ----------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory: code whose device memory is owned

@@ -258,7 +258,7 @@ static void curvature_tables(const Plan* p, std::vector<float>& t) {
     }
 }
 
-static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t stream) {
+static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t stream, int zc_req) {
     std::string why;
     const ngf_status vs = validate_desc(d, why);
     if (vs != NGF_OK) return set_error(p, vs, why);
@@ -282,6 +282,7 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     long long nchunk = (2LL * sms + txy / 2) / txy;
     nchunk = std::max<long long>(1, std::min<long long>(nchunk, p->m[2]));
     p->zc = (int)std::max<long long>(std::min<long long>(8, p->m[2]), (p->m[2] + nchunk - 1) / nchunk);
+    if (zc_req > 0) p->zc = std::min(zc_req, p->m[2]);
 
     std::vector<int> f[3];
     std::vector<float> w[3];
@@ -520,18 +521,12 @@ static ngf_status sync_read(Plan* p, double* h, int count) {
     return NGF_OK;
 }
 
-}  // namespace ngf
-
-using namespace ngf;
-
-extern "C" {
-
-ngf_status ngf_plan_create(ngf_plan** out, const ngf_level_desc* desc, void* cuda_stream) {
+ngf_status plan_create(ngf_plan** out, const ngf_level_desc* desc, cudaStream_t stream, int zc) {
     if (!out) return set_error(nullptr, NGF_EINVAL, "plan output pointer is NULL");
     *out = nullptr;
     ngf_plan* pl = new (std::nothrow) ngf_plan();
     if (!pl) return set_error(nullptr, NGF_ENOMEM, "host allocation failed");
-    ngf_status s = create_plan(&pl->impl, desc, (cudaStream_t)cuda_stream);
+    ngf_status s = create_plan(&pl->impl, desc, stream, zc);
     if (s != NGF_OK) {
         g_last_error = pl->impl.err;
         free_plan(&pl->impl);
@@ -540,6 +535,16 @@ ngf_status ngf_plan_create(ngf_plan** out, const ngf_level_desc* desc, void* cud
     }
     *out = pl;
     return NGF_OK;
+}
+
+}  // namespace ngf
+
+using namespace ngf;
+
+extern "C" {
+
+ngf_status ngf_plan_create(ngf_plan** out, const ngf_level_desc* desc, void* cuda_stream) {
+    return plan_create(out, desc, (cudaStream_t)cuda_stream, 0);
 }
 
 ngf_status ngf_plan_destroy(ngf_plan* plan) {

@@ -15,7 +15,7 @@ namespace ngf {
 
 // coarse-to-fine level sequence: each coarser level halves image cells and
 // deformation cells (ceil) and keeps the physical extent of the domain
-static ngf_level_desc level_at(const ngf_level_desc& finest, int level) {
+ngf_level_desc level_at(const ngf_level_desc& finest, int level) {
     ngf_level_desc d = finest;
     for (int k = 0; k < level; ++k)
         for (int a = 0; a < 3; ++a) {

@@ -1153,4 +1153,102 @@ __global__ void __launch_bounds__(NT) k_prolong(int f0, int f1, int f2, int c0, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched forms.  The per-pair parameter block is copied into shared memory
+// and the single-problem body runs on it unchanged, so every pair's results
+// equal those of its own plan bit for bit.
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void copy_to_shared(T& dst, const T* src) {
+    static_assert(sizeof(T) % 4 == 0, "parameter blocks are whole words");
+    for (int i = threadIdx.x; i < (int)(sizeof(T) / 4); i += blockDim.x)
+        reinterpret_cast<int*>(&dst)[i] = __ldg(reinterpret_cast<const int*>(src) + i);
+}
+
+__device__ __forceinline__ void queue_release(const BatchQueue& Q) {
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(Q.done, 1u) == gridDim.x - 1) {  // every CTA has left the queue
+            *Q.next = 0u;
+            *Q.done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <int KIND>  // 0..2: image pass mode, 3: diagonal (span 3), 4: diagonal (span 4)
+__device__ __forceinline__ void batch_image_loop(const BatchQueue& Q) {
+    __shared__ ImgParams Ps;
+    __shared__ int4 item;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned int k = atomicAdd(Q.next, 1u);
+            item = (k < (unsigned int)Q.nitems) ? Q.items[k] : make_int4(-1, 0, 0, 0);
+        }
+        __syncthreads();
+        const int4 it = item;
+        if (it.x < 0) break;
+        if (!Q.active || Q.active[it.x]) {
+            copy_to_shared(Ps, Q.params + it.x);
+            __syncthreads();
+            if (KIND == 3) diag_pass<3>(Ps, it.y, it.z, it.w);
+            else if (KIND == 4) diag_pass<4>(Ps, it.y, it.z, it.w);
+            else image_pass<KIND>(Ps, it.y, it.z, it.w);
+        }
+        __syncthreads();
+    }
+    queue_release(Q);
+}
+
+__global__ void __launch_bounds__(NT, 2) k_batch_image_obj(const BatchQueue Q) { batch_image_loop<MODE_OBJ>(Q); }
+__global__ void __launch_bounds__(NT, 2) k_batch_image_grad(const BatchQueue Q) { batch_image_loop<MODE_GRAD>(Q); }
+__global__ void __launch_bounds__(NT, 2) k_batch_image_hess(const BatchQueue Q) { batch_image_loop<MODE_HESS>(Q); }
+__global__ void __launch_bounds__(NT, 1) k_batch_diag(const BatchQueue Q) { batch_image_loop<3>(Q); }
+__global__ void __launch_bounds__(NT, 1) k_batch_diag4(const BatchQueue Q) { batch_image_loop<4>(Q); }
+
+template <class ARGS, class BODY>
+__device__ __forceinline__ void batch_nodal(const ARGS* table, const BatchSegs& S, BODY body) {
+    __shared__ ARGS A;
+    __shared__ int pair;
+    if (threadIdx.x == 0) {  // largest k with first[k] <= blockIdx.x
+        int lo = 0, hi = S.npairs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (S.first[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        pair = lo;
+    }
+    __syncthreads();
+    const int k = pair;
+    if (S.active && !S.active[k]) return;
+    copy_to_shared(A, table + k);
+    __syncthreads();
+    body(A, (unsigned int)(blockIdx.x - S.first[k]), (unsigned int)(S.first[k + 1] - S.first[k]));
+}
+
+__global__ void __launch_bounds__(NT) k_batch_lap(const LapArgs* table, const BatchSegs S) {
+    batch_nodal(table, S, [](const LapArgs& a, unsigned int b, unsigned int n) {
+        lap_body(a.G, a.x, a.L, a.part, a.count, a.out, a.scale, b, n);
+    });
+}
+__global__ void __launch_bounds__(NT) k_batch_combine(const CombineParams* table, const BatchSegs S) {
+    batch_nodal(table, S, [](const CombineParams& a, unsigned int b, unsigned int n) { combine_body(a, b, n); });
+}
+__global__ void __launch_bounds__(NT) k_batch_pcg_init(const PcgParams* table, const BatchSegs S) {
+    batch_nodal(table, S, [](const PcgParams& a, unsigned int b, unsigned int n) { pcg_init_body(a, b, n); });
+}
+__global__ void __launch_bounds__(NT) k_batch_pcg_update(const PcgParams* table, const BatchSegs S) {
+    batch_nodal(table, S, [](const PcgParams& a, unsigned int b, unsigned int n) { pcg_update_body(a, b, n); });
+}
+__global__ void __launch_bounds__(NT) k_batch_pcg_dir(const PcgParams* table, const BatchSegs S) {
+    batch_nodal(table, S, [](const PcgParams& a, unsigned int b, unsigned int n) { pcg_dir_body(a, b, n); });
+}
+__global__ void __launch_bounds__(NT) k_batch_dot(const DotArgs* table, const BatchSegs S) {
+    batch_nodal(table, S, [](const DotArgs& a, unsigned int b, unsigned int n) { dot_body(a, b, n); });
+}
+__global__ void __launch_bounds__(NT) k_batch_axpy(const AxpyArgs* table, const BatchSegs S) {
+    batch_nodal(table, S, [](const AxpyArgs& a, unsigned int b, unsigned int n) { axpy_body(a, b, n); });
+}
+
 }  // namespace ngf

@@ -235,6 +235,36 @@ __global__ void k_scale(long long n, float a, const float* __restrict__ x, float
 __global__ void k_nonfinite(long long n, const float* __restrict__ a, double* part, unsigned int* count,
                             double* out);
 __global__ void k_restrict(int m0, int m1, int m2, const float* __restrict__ img, float* __restrict__ out);
+
+// ---- batched forms (independent problems of uneven size in one launch)
+// Image passes: a persistent grid takes work items (pair, tile x, tile y,
+// tile z) from a queue; the last CTA to finish resets the queue.
+struct BatchQueue {
+    const ImgParams* params;  // one per pair
+    const int4* items;        // (pair, bx, by, bz), largest tiles first
+    int nitems;
+    const int* active;        // per pair: 0 skips its items (nullable)
+    unsigned int* next;       // queue head and finished-CTA count, zero between launches
+    unsigned int* done;
+};
+// Nodal kernels: pair k owns CTAs first[k] .. first[k+1]-1 of the launch.
+struct BatchSegs {
+    const int* first;   // npairs + 1 prefix
+    int npairs;
+    const int* active;  // nullable
+};
+__global__ void k_batch_image_obj(const BatchQueue Q);
+__global__ void k_batch_image_grad(const BatchQueue Q);
+__global__ void k_batch_image_hess(const BatchQueue Q);
+__global__ void k_batch_diag(const BatchQueue Q);
+__global__ void k_batch_diag4(const BatchQueue Q);
+__global__ void k_batch_lap(const LapArgs* table, const BatchSegs S);
+__global__ void k_batch_combine(const CombineParams* table, const BatchSegs S);
+__global__ void k_batch_pcg_init(const PcgParams* table, const BatchSegs S);
+__global__ void k_batch_pcg_update(const PcgParams* table, const BatchSegs S);
+__global__ void k_batch_pcg_dir(const PcgParams* table, const BatchSegs S);
+__global__ void k_batch_dot(const DotArgs* table, const BatchSegs S);
+__global__ void k_batch_axpy(const AxpyArgs* table, const BatchSegs S);
 __global__ void k_prolong(int f0, int f1, int f2, int c0, int c1, long long Nc, const int* __restrict__ tf,
                           const float* __restrict__ tw, const float* __restrict__ uc, float* __restrict__ uf);
 

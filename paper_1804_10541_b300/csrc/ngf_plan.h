@@ -91,6 +91,9 @@ ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u
 cudaError_t prof_mark(Plan* p, int which);
 ngf_status dot_impl(Plan* p, long long n, const float* a, const float* b, double* dout);
 int grid_for(long long n, int max_blocks);
+// plan with a requested z-chunk length (0: about two CTAs per SM)
+ngf_status plan_create(ngf_plan** out, const ngf_level_desc* desc, cudaStream_t stream, int zc);
+ngf_level_desc level_at(const ngf_level_desc& finest, int level);
 
 }  // namespace ngf
 

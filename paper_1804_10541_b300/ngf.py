@@ -22,7 +22,9 @@ NGF_PCG_NSCALARS = 8
 EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_last_error", "ngf_objective",
            "ngf_objective_dev", "ngf_gradient", "ngf_gradient_dev", "gn_hessvec", "curvature_apply",
            "ngf_gn_diagonal", "pcg_init", "pcg_step", "pcg_solve", "pcg_read", "register_multilevel",
-           "ngf_objective_noalloc", "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count"]
+           "ngf_objective_noalloc", "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count",
+           "ngf_batch_create", "ngf_batch_destroy", "ngf_batch_objective", "ngf_batch_gradient",
+           "ngf_batch_hessvec", "ngf_batch_diagonal", "ngf_batch_autotune", "ngf_batch_zc", "register_batch"]
 
 
 class LevelDesc(C.Structure):
@@ -79,6 +81,14 @@ def declare(lib):
         "ngf_objective_noalloc": [C.POINTER(LevelDesc), VP, VP, VP, VP, VP],
         "ngf_profile_enable": [P, I32],
         "ngf_profile_read": [P, I32, D, C.POINTER(C.c_int64)],
+        "ngf_batch_create": [C.POINTER(C.c_void_p), I32, C.POINTER(LevelDesc), I32, VP],
+        "ngf_batch_destroy": [P],
+        "ngf_batch_objective": [P, VP, VP, VP, D, D],
+        "ngf_batch_gradient": [P, VP, VP, VP, VP],
+        "ngf_batch_hessvec": [P, VP, VP, VP, VP, VP],
+        "ngf_batch_diagonal": [P, VP, VP, VP, VP],
+        "ngf_batch_autotune": [P, VP, VP, VP, VP, VP, C.POINTER(I32), D],
+        "register_batch": [I32, C.POINTER(LevelDesc), C.POINTER(Options), VP, VP, VP, C.POINTER(Report), I32, VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -88,6 +98,8 @@ def declare(lib):
     lib.ngf_last_error.restype = C.c_char_p
     lib.ngf_launch_count.argtypes = []
     lib.ngf_launch_count.restype = C.c_int64
+    lib.ngf_batch_zc.argtypes = [P]
+    lib.ngf_batch_zc.restype = C.c_int32
     return lib
 
 
@@ -256,6 +268,89 @@ def ngf_profile_read(plan, which):
 
 def ngf_launch_count():
     return int(lib.ngf_launch_count())
+
+
+# ---- batched form -----------------------------------------------------------
+
+def _ptr_array(xs):
+    """Host array of device pointers (kept alive by the caller's reference)."""
+    arr = (C.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+    return arr
+
+
+def ngf_batch_create(descs, zc=0, stream=None):
+    arr = (LevelDesc * len(descs))(*descs)
+    h = C.c_void_p()
+    _check(lib.ngf_batch_create(C.byref(h), len(descs), arr, int(zc), _stream(stream)))
+    return h
+
+
+def ngf_batch_destroy(batch):
+    _check(lib.ngf_batch_destroy(batch))
+
+
+def ngf_batch_zc(batch):
+    return int(lib.ngf_batch_zc(batch))
+
+
+def ngf_batch_objective(batch, R, T, u):
+    n = len(R)
+    D, S = (C.c_double * n)(), (C.c_double * n)()
+    _check(lib.ngf_batch_objective(batch, _ptr_array(R), _ptr_array(T), _ptr_array(u), D, S))
+    return list(D), list(S)
+
+
+def ngf_batch_gradient(batch, R, T, u, grad):
+    _check(lib.ngf_batch_gradient(batch, _ptr_array(R), _ptr_array(T), _ptr_array(u), _ptr_array(grad)))
+
+
+def ngf_batch_hessvec(batch, R, T, u, p, q):
+    _check(lib.ngf_batch_hessvec(batch, _ptr_array(R), _ptr_array(T), _ptr_array(u), _ptr_array(p),
+                                 _ptr_array(q)))
+
+
+def ngf_batch_diagonal(batch, R, T, u, diag):
+    _check(lib.ngf_batch_diagonal(batch, _ptr_array(R), _ptr_array(T), _ptr_array(u), _ptr_array(diag)))
+
+
+def ngf_batch_autotune(batch, R, T, u, p, q):
+    zc, ms = C.c_int32(), C.c_double()
+    _check(lib.ngf_batch_autotune(batch, _ptr_array(R), _ptr_array(T), _ptr_array(u), _ptr_array(p),
+                                  _ptr_array(q), C.byref(zc), C.byref(ms)))
+    return zc.value, ms.value
+
+
+def register_batch(descs, opts, R, T, u_out, autotune=False, stream=None):
+    n = len(descs)
+    reps = (Report * n)()
+    _check(lib.register_batch(n, (LevelDesc * n)(*descs), C.byref(opts), _ptr_array(R), _ptr_array(T),
+                              _ptr_array(u_out), reps, 1 if autotune else 0, _stream(stream)))
+    return list(reps)
+
+
+class Batch:
+    """Owning wrapper of an ngf_batch."""
+
+    def __init__(self, descs, zc=0, stream=None):
+        self.descs = list(descs)
+        self.handle = ngf_batch_create(self.descs, zc, stream)
+
+    def close(self):
+        if self.handle:
+            ngf_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Plan:

@@ -21,6 +21,9 @@ Workloads (the paper's datasets are not available; these stand in for them):
                organs, lungs, spine), smooth displacement up to 20 mm,
                129x129x225 nodes, 5 levels, alpha = 10, tau = rho = 5
                (Sec. 6.2.2).
+  batch_64     64 blob pairs of uneven cubic size N ~ U{64..192} (seed 30),
+               unit spacing, (N/2+1)^3 nodes, 2 levels; blob centres and
+               widths scale with N (batch_pairs).
 """
 import math
 
@@ -327,6 +330,21 @@ def make(workload, device="cpu"):
     else:
         raise KeyError(workload)
     return R, T, U, w
+
+
+def batch_pairs(count=64, lo=64, hi=192, seed=30, device="cpu"):
+    """`count` blob pairs of cubic size N ~ U{lo..hi} (numpy PCG64, `seed`);
+    pair k uses blob seeds 1000 + 4k ... 1000 + 4k + 3.  Returns a list of
+    (R, T, workload dict) with nodes N//2 + 1 per axis (two voxels per cell)."""
+    sizes = _rng(seed).integers(lo, hi + 1, size=count)
+    out = []
+    for k, N in enumerate(sizes):
+        N = int(N)
+        m = (N, N, N)
+        R, T, _ = blob_pair(m, (1.0, 1.0, 1.0), seed=1000 + 4 * k, device=device)
+        out.append((R, T, dict(m=m, h=(1.0, 1.0, 1.0), n=(N // 2 + 1,) * 3, alpha=1.0, tau=0.1, rho=0.1,
+                               levels=2)))
+    return out
 
 
 def random_fields(n_nodes, seed, amp=0.3, device="cpu"):
