@@ -362,6 +362,94 @@ def run_kernel_case(args):
     return 0
 
 
+def run_batch(args):
+    """Batched form on 64 blob pairs of uneven cubic size (64..192 voxels per
+    side, 2 levels, 10 GN x 20 PCG): one register_batch call per step, against
+    the same 64 pairs registered one after another with register_multilevel
+    (equal decisions per pair, so equal final NGF); plus the per-pair error of
+    the batched gn_hessvec against the FP64 oracle at the finest level."""
+    import numpy as np
+    import torch
+    from paper_1804_10541_b300 import ngf, synth
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    dev = torch.device("cuda", 0)
+    pairs = synth.batch_pairs(device=dev)
+    descs = [ngf.level_desc(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"]) for _, _, w in pairs]
+    R = [p[0] for p in pairs]
+    T = [p[1] for p in pairs]
+    nn = [3 * w["n"][0] * w["n"][1] * w["n"][2] for _, _, w in pairs]
+    U = [torch.zeros(k, device=dev) for k in nn]
+    opts = ngf.options(levels=2, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, device=dev, dtype=torch.float32)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ngf.register_batch(descs, opts, R, T, U, stream=stream)
+    stream.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = ngf.ngf_launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            reps = ngf.register_batch(descs, opts, R, T, U, stream=stream)
+            ev[k][1].record(stream)
+    stream.synchronize()
+    launches = ngf.ngf_launch_count() - launches0
+    clocks = sampler.stop()
+    batch_ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    voxels = sum(r.hessvec_voxels for r in reps)
+    # the same pairs one at a time
+    U1 = [torch.zeros(k, device=dev) for k in nn]
+    with torch.cuda.stream(stream):
+        flush.fill_(0.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        reps1 = [ngf.register_multilevel(d, opts, r, t, u, stream) for d, r, t, u in zip(descs, R, T, U1)]
+        e1.record(stream)
+    stream.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    same_u = all(torch.equal(a, b) for a, b in zip(U, U1))
+    j_rel = max(abs(a.J - b.J) / abs(b.J) for a, b in zip(reps, reps1))
+    # tile autotuner on the finest level, then per-pair parity with the oracle
+    import oracle as O
+    gen = torch.Generator(device="cpu").manual_seed(31)
+    uu = [(0.5 * torch.randn(k, generator=gen)).to(dev) for k in nn]
+    pp = [torch.randn(k, generator=gen).to(dev) for k in nn]
+    qq = [torch.empty(k, device=dev) for k in nn]
+    with torch.cuda.stream(stream), ngf.Batch(descs, 0, stream) as b:
+        e0.record(stream)
+        for _ in range(3):
+            ngf.ngf_batch_hessvec(b.handle, R, T, uu, pp, qq)
+        e1.record(stream)
+        stream.synchronize()
+        ms_default = e0.elapsed_time(e1) / 3
+        zc, ms_tuned = ngf.ngf_batch_autotune(b.handle, R, T, uu, pp, qq)
+        ngf.ngf_batch_hessvec(b.handle, R, T, uu, pp, qq)
+        stream.synchronize()
+    errs = []
+    for k, (d, w) in enumerate(zip(descs, [p[2] for p in pairs])):
+        L = O.level(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"])
+        qo = O.hessvec(L, R[k].double().cpu().numpy(), T[k].double().cpu().numpy(), uu[k].double().cpu().numpy(),
+                       pp[k].double().cpu().numpy())
+        errs.append(float(np.linalg.norm(qq[k].double().cpu().numpy() - qo) / np.linalg.norm(qo)))
+    total_vox = sum(w["m"][0] * w["m"][1] * w["m"][2] for _, _, w in pairs)
+    line = {"workload": "batch_64: 64 blob pairs, cubic N ~ U{64..192} (seed 30), nodes N/2+1, 2 levels, "
+                        f"{GN_ITERS} GN x {PCG_ITERS} PCG", "metric": METRIC,
+            "value": voxels / (batch_ms / 1e3) / 1e9, "unit": "Gvoxel/s", "steps": args.steps,
+            "warmup": args.warmup, "batched_ms": batch_ms, "sequential_ms": seq_ms,
+            "speedup_vs_sequential": seq_ms / batch_ms, "same_u_as_sequential": same_u,
+            "max_rel_J_diff_vs_sequential": j_rel, "total_voxels": total_vox,
+            "batched_hessvec_ms": {"default_zc": ms_default, "autotuned": ms_tuned, "zc": zc},
+            "hessvec_rel_err_vs_oracle": {"max": max(errs), "median": statistics.median(errs)},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "l2": "flushed before every step (256 MB write)", "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,9 +459,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", default=None, help="profile driver: gn_hessvec only on this workload")
     ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_64"],
+                    help="batch_64: the batched form on 64 uneven pairs (its own JSON line)")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
+    if args.workload == "batch_64":
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
