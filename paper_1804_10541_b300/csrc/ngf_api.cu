@@ -709,7 +709,7 @@ ngf_status pcg_solve(ngf_plan* plan, ngf_pcg_state* st, const float* R, const fl
     if (iters < 0) return set_error(p, NGF_EINVAL, "iters must be >= 0");
     if (iters == 0) return NGF_OK;
     // the legacy default stream cannot be captured: launch directly there
-    if (!use_graph || p->stream == nullptr) {
+    if (!use_graph || p->stream == nullptr || p->stream == cudaStreamLegacy) {
         for (int i = 0; i < iters; ++i) NGF_TRY(pcg_step_impl(p, st, R, T, u));
         return NGF_OK;
     }
@@ -723,7 +723,10 @@ ngf_status pcg_solve(ngf_plan* plan, ngf_pcg_state* st, const float* R, const fl
         ngf_status s = NGF_OK;
         for (int i = 0; i < iters && s == NGF_OK; ++i) s = pcg_step_impl(p, st, R, T, u);
         cudaError_t e = cudaStreamEndCapture(p->stream, &g);
-        if (s != NGF_OK) return s;
+        if (s != NGF_OK) {
+            if (e == cudaSuccess && g) cudaGraphDestroy(g);
+            return s;
+        }
         NGF_CU(p, e, "cudaStreamEndCapture");
         p->graph_kernels = launch_counter().load() - before;
         launch_counter().fetch_sub(p->graph_kernels);  // captured, not launched

@@ -673,10 +673,19 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
                 if (*g) cudaGraphExecDestroy(*g);
             }
         } graph_guard{&graph};
-        if (o->use_graph && o->pcg_iters > 0) {
+        // the legacy default stream cannot be captured: direct launches there
+        if (o->use_graph && o->pcg_iters > 0 && stream != nullptr && stream != cudaStreamLegacy) {
             const int64_t before = launch_counter().load();
             cudaGraph_t gr = nullptr;
-            B_CU(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+            const cudaError_t be = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+            if (be != cudaSuccess) {
+                cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+                if (cudaStreamIsCapturing(stream, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                    cudaStreamEndCapture(stream, &gr);
+                    if (gr) cudaGraphDestroy(gr);
+                }
+                return cuda_check(nullptr, be, "cudaStreamBeginCapture");
+            }
             ngf_status cs = NGF_OK;
             for (int it = 0; it < o->pcg_iters && cs == NGF_OK; ++it) cs = pcg_iteration();
             const cudaError_t ce = cudaStreamEndCapture(stream, &gr);

@@ -112,10 +112,14 @@ def test_register_batch_equals_per_pair_registration(ngf, use_graph):
     pairs = _blob_batch([24, 33, 40, 29])
     opts = ngf.options(2, gn_iters=4, pcg_iters=8, use_graph=use_graph)
     ub = [torch.zeros(3 * d.n[0] * d.n[1] * d.n[2], device="cuda") for _, _, d in pairs]
-    reps = ngf.register_batch([d for _, _, d in pairs], opts, [R for R, _, _ in pairs], [T for _, T, _ in pairs], ub)
+    # graphs need a stream other than the legacy default stream
+    stream = torch.cuda.Stream() if use_graph else None
+    torch.cuda.synchronize()
+    reps = ngf.register_batch([d for _, _, d in pairs], opts, [R for R, _, _ in pairs], [T for _, T, _ in pairs], ub,
+                              stream=stream)
     for k, (R, T, d) in enumerate(pairs):
         u1 = torch.zeros_like(ub[k])
-        r1 = ngf.register_multilevel(d, opts, R, T, u1)
+        r1 = ngf.register_multilevel(d, opts, R, T, u1, stream)
         assert torch.equal(u1, ub[k]), k
         assert (r1.J, r1.gn_done, r1.ls_trials, r1.pcg_total, r1.ls_fail) == \
                (reps[k].J, reps[k].gn_done, reps[k].ls_trials, reps[k].pcg_total, reps[k].ls_fail), k
