@@ -202,6 +202,9 @@ extern "C" ngf_status ngf_objective_noalloc(const ngf_level_desc* d, const float
     P.wy = w + P.m0;
     P.wz = w + P.m0 + P.m1;
     P.zc = zc;
+    P.ntx = (int)grid.x;
+    P.nty = (int)grid.y;
+    P.ntz = (int)grid.z;
     P.partial = nullptr;
     P.dpart = part;
     P.dcount = count;
