@@ -288,7 +288,7 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     std::vector<float> w[3];
     for (int a = 0; a < 3; ++a) pw_table(p->m[a], p->n[a], f[a], w[a]);
     // diagonal variant: a three-node span per axis needs two or more voxels per
-    // cell; the per-row windows then hold at most PXW x-nodes
+    // cell, four nodes otherwise; the per-row windows hold diag_pxw(span) x-nodes
     {
         bool span3 = true;
         for (int a = 0; a < 3; ++a) span3 = span3 && 2 * (p->n[a] - 1) <= p->m[a];
@@ -309,7 +309,9 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
             p->dsteps[k] = 0;
             while ((1 << p->dsteps[k]) < std::min(longest[k], TX)) ++p->dsteps[k];
         }
-        p->diag_private = span3 && widest <= PXW;
+        p->diag_span3 = span3;
+        if (widest > diag_pxw(span3 ? 3 : 4))
+            return set_error(p, NGF_EINVAL, "internal: x-node window of the diagonal kernel too small");
     }
     const size_t tl = (size_t)p->m[0] + p->m[1] + p->m[2];
     std::vector<int> fh;
@@ -493,7 +495,7 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
 ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g1, nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
-    NGF_CU(p, launch(p->diag_private ? k_diag : k_diag4, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P),
+    NGF_CU(p, launch(p->diag_span3 ? k_diag : k_diag4, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P),
            "k_diag");
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g1, diag, nullptr, p->ctab, nullptr, nullptr);

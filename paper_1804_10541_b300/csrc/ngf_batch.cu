@@ -93,11 +93,11 @@ static ngf_status fill_segments(DevArray<int>& first, const std::vector<int>& co
 
 // (pair, tile) items of one geometry, by decreasing voxel count (the queue
 // hands them out in this order, so the largest start first)
-static void tile_items(const Batch& b, bool halo1, int want_private, std::vector<int4>& out) {
+static void tile_items(const Batch& b, bool halo1, int want_span3, std::vector<int4>& out) {
     std::vector<std::pair<long long, int4>> it;
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
-        if (want_private >= 0 && (int)p->diag_private != want_private) continue;
+        if (want_span3 >= 0 && (int)p->diag_span3 != want_span3) continue;
         const Geometry& g = halo1 ? p->g1 : p->g0;
         for (int z = 0; z < g.ntz; ++z)
             for (int y = 0; y < g.nty; ++y)

@@ -511,15 +511,15 @@ __global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) {
 // rows are summed onto node planes (four live planes), which are stored as
 // tile partials of the halo-1 geometry.
 //
-// SPAN 3 (two or more voxels per cell on every axis): each warp is one row of
-// the tile and owns a private accumulator window (4 planes x 3 components x
-// 3 y-nodes x PXW x-nodes).  Lanes whose voxels share an x-node floor form
-// runs; a segmented shuffle sum gives each run's total to its first lane,
-// which alone adds it (plain read-modify-write, distinct addresses).  The
-// windows of the rows are merged in a fixed order when a node plane is
-// complete, so the diagonal is deterministic.
-// SPAN 4 (some axis with fewer than two voxels per cell): shared-memory
-// atomics into one window for the whole tile.
+// Each warp is one row of the tile and owns a private accumulator window
+// (4 node planes x 3 components x SPAN y-nodes x diag_pxw(SPAN) x-nodes).
+// Lanes whose voxels share an x-node floor form runs; a segmented shuffle sum
+// gives each run's total to its first lane, which alone adds it (plain
+// read-modify-write, distinct addresses within a step; a warp barrier orders
+// the steps that reach the same node from neighbouring runs).  The windows of the rows are merged
+// in a fixed order when a node plane is complete, so the diagonal is
+// deterministic.  SPAN 3 when every axis has two or more voxels per cell,
+// SPAN 4 otherwise.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float pw_weight(int f, float w1, int node) {
     return (node == f) ? 1.f - w1 : ((node == f + 1) ? w1 : 0.f);
@@ -529,7 +529,8 @@ template <int SPAN>
 __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, int bz) {
     NGF_DYNAMIC_SMEM(smraw);
     DiagSmem& S = *reinterpret_cast<DiagSmem*>(smraw);
-    constexpr bool PRIV = (SPAN == 3);
+    constexpr int PXWS = diag_pxw(SPAN);
+    constexpr int WPLANE = 3 * SPAN * PXWS;  // one node plane of a row's window
     const int tid = threadIdx.x;
     const int xs = bx * TX, ys = by * TY;
     const int z0 = bz * P.zc, z1 = min(P.m2, z0 + P.zc);
@@ -552,7 +553,7 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
         S.fy1[i] = P.fy[gy] - UY0;
         S.wy1[i] = P.wy[gy];
     }
-    for (int i = tid; i < (PRIV ? DIAG_PRIVATE : DIAG_SHARED); i += NT) S.Acc[i] = 0.f;
+    for (int i = tid; i < TY * diag_window(SPAN); i += NT) S.Acc[i] = 0.f;
     __syncthreads();
 
     // lane layout of the owned columns: warp = row ly, lane = lx
@@ -562,18 +563,14 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
     // runs of lanes sharing the x-node floor of the stencil's lowest voxel
     const int dsteps = (xs == 0) ? P.dsteps0 : P.dsteps;
     unsigned int same = 0u;
-    bool head = true;
-    if (PRIV) {
-        const int key = S.fx1[lxc];
+    const int key = S.fx1[lxc];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            const int o = __shfl_down_sync(0xffffffffu, key, 1 << k);
-            if (k < dsteps && lx + (1 << k) < TX && o == key) same |= 1u << k;
-        }
-        const int prev = __shfl_up_sync(0xffffffffu, key, 1);
-        head = (lx == 0) || (prev != key);
+    for (int k = 0; k < 5; ++k) {
+        const int o = __shfl_down_sync(0xffffffffu, key, 1 << k);
+        if (k < dsteps && lx + (1 << k) < TX && o == key) same |= 1u << k;
     }
-    constexpr int WPLANE = 3 * 3 * PXW;  // one plane of a row's private window
+    const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const bool head = (lx == 0) || (prev != key);
     float* const priv = S.Acc + ly * (4 * WPLANE);
 
     const int items = 3 * nby * nbx;
@@ -690,9 +687,7 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
             }
             int po[SPAN];
 #pragma unroll
-            for (int g = 0; g < SPAN; ++g)
-                po[g] = PRIV ? ((bzm + g + BZ0) & 3) * WPLANE + bxm
-                             : ((bzm + g + BZ0) & 3) * (3 * DBY * DBX) + bym * DBX + bxm;
+            for (int g = 0; g < SPAN; ++g) po[g] = ((bzm + g + BZ0) & 3) * WPLANE + bxm;
 #pragma unroll 1
             for (int d = 0; d < 3; ++d) {
                 const float* dTd[3] = {S.dT[szm][d], S.dT[sc][d], S.dT[szp][d]};
@@ -721,18 +716,16 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
                         for (int g = 0; g < SPAN; ++g) {
                             const float J = fmaf(WZ[1][g], xy1, cz[g] * xy2);
                             float v = act ? J * J : 0.f;
-                            if (PRIV) {
 #pragma unroll
-                                for (int k = 0; k < 5; ++k) {
-                                    if (k >= dsteps) break;
-                                    const float t = __shfl_down_sync(0xffffffffu, v, 1 << k);
-                                    if (same & (1u << k)) v += t;
-                                }
-                                if (head && inb) priv[po[g] + (d * 3 + b) * PXW + a] += v;
-                            } else if (act && inb) {
-                                atomicAdd(S.Acc + po[g] + d * DBY * DBX + b * DBX + a, v);
+                            for (int k = 0; k < 5; ++k) {
+                                if (k >= dsteps) break;
+                                const float t = __shfl_down_sync(0xffffffffu, v, 1 << k);
+                                if (same & (1u << k)) v += t;
                             }
+                            if (head && inb) priv[po[g] + (d * SPAN + b) * PXWS + a] += v;
                         }
+                        // the next a reaches the x-nodes of this one from the neighbouring run
+                        __syncwarp();
                     }
                 }
             }
@@ -746,17 +739,11 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
                 for (int i = tid; i < items; i += NT) {
                     const int c = i / (nby * nbx), rem = i % (nby * nbx), byy = rem / nbx, bxx = rem % nbx;
                     float sum = 0.f;
-                    if (PRIV) {  // rows in a fixed order
-                        for (int w = 0; w < tye; ++w) {
-                            const int b = byy - S.fy1[w];
-                            if (b < 0 || b > 2) continue;
-                            float& e = S.Acc[w * (4 * WPLANE) + sl * WPLANE + (c * 3 + b) * PXW + bxx];
-                            sum += e;
-                            e = 0.f;
-                        }
-                    } else {
-                        float& e = S.Acc[sl * (3 * DBY * DBX) + (c * DBY + byy) * DBX + bxx];
-                        sum = e;
+                    for (int w = 0; w < tye; ++w) {  // rows in a fixed order
+                        const int b = byy - S.fy1[w];
+                        if (b < 0 || b >= SPAN) continue;
+                        float& e = S.Acc[w * (4 * WPLANE) + sl * WPLANE + (c * SPAN + b) * PXWS + bxx];
+                        sum += e;
                         e = 0.f;
                     }
                     P.partial[((tile * 3 + c) * P.pbz + (next - BZ0)) * (long long)(P.pby * P.pbx) + byy * P.pbx + bxx] =

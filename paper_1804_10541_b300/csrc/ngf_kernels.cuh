@@ -30,9 +30,13 @@ constexpr int R0N = TX * TY;
 constexpr int UBX = TX + 5, UBY = TY + 5;       // node box of the halo-2 region (ratio >= 1)
 constexpr int NBX = TX + 1, NBY = TY + 1;       // node box of the owned columns
 constexpr int DBX = TX + 3, DBY = TY + 3;       // node box of the halo-1 region (diagonal)
-constexpr int PXW = 20;                          // x-node window of one warp row (two or more voxels per cell)
-constexpr int DIAG_SHARED = 4 * 3 * DBY * DBX, DIAG_PRIVATE = TY * 4 * 3 * 3 * PXW;
-constexpr int DIAG_ACC = DIAG_SHARED > DIAG_PRIVATE ? DIAG_SHARED : DIAG_PRIVATE;
+// x-node window of one warp row in the diagonal kernel: 32 voxels plus the
+// stencil's neighbours cover at most 20 nodes with two or more voxels per
+// cell (three-node span), at most 35 otherwise (four-node span)
+__host__ __device__ constexpr int diag_pxw(int span) { return span == 3 ? 20 : 36; }
+// four live node planes x 3 components x span y-nodes x window, per row
+__host__ __device__ constexpr int diag_window(int span) { return 4 * 3 * span * diag_pxw(span); }
+constexpr int DIAG_ACC = TY * diag_window(4);
 
 enum Mode { MODE_OBJ = 0, MODE_GRAD = 1, MODE_HESS = 2 };
 
@@ -87,9 +91,7 @@ struct DiagSmem {
     float Tw[3][R1N];
     float dT[3][3][R1N];        // [plane slot][component][column]
     float Uz[3][UBY][UBX];
-    // node-plane accumulators: shared by all rows (four live planes) with
-    // atomics, or one private window per warp row (see diag_pass)
-    float Acc[DIAG_ACC];
+    float Acc[DIAG_ACC];        // one private node window per warp row (see diag_pass)
     float wx1[SX1], wy1[SY1];
     int fx1[SX1], fy1[SY1];     // node floor relative to the Uz (= partial) box
 };

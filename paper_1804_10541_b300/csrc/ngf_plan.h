@@ -40,7 +40,7 @@ struct Plan {
     long long M = 0, N = 0;
     double hbar = 0, hbary = 0, hy[3]{};
     int zc = 0;
-    bool diag_private = false;  // diagonal: per-row private windows (three-node span)
+    bool diag_span3 = false;    // diagonal: three-node span (>= 2 voxels per cell on every axis)
     int dsteps[2] = {0, 0};     // diagonal: shuffle steps covering the longest run of equal x
                                 // floors in the first x tile and in the others
     int img_blocks = 0, diag_blocks = 0, node_blocks = 0, node1_blocks = 0;

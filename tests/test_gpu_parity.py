@@ -111,13 +111,20 @@ def test_hessvec_is_deterministic(ngf):
         g1, g2 = c.empty(), c.empty()
         ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g1)
         ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g2)
-        # two or more voxels per cell on every axis: the diagonal sums its rows
-        # in a fixed order too
+        # the diagonal sums its rows in a fixed order too
         d1, d2 = c.empty(), c.empty()
         ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, d1)
         ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, d2)
         torch.cuda.synchronize()
     assert torch.equal(q1, q2) and torch.equal(g1, g2) and torch.equal(d1, d2)
+    # one voxel per cell (four-node span of the diagonal kernel)
+    c = G.random_case((40, 20, 10), (1.0, 1.0, 1.0), (41, 21, 11), seed=4)
+    with ngf.Plan(c.desc) as pl:
+        d1, d2 = c.empty(), c.empty()
+        ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, d1)
+        ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, d2)
+        torch.cuda.synchronize()
+    assert torch.equal(d1, d2)
 
 
 def test_identity_and_identical_images(ngf):
