@@ -401,6 +401,16 @@ def run_batch(args):
     clocks = sampler.stop()
     batch_ms = statistics.median(a.elapsed_time(b) for a, b in ev)
     voxels = sum(r.hessvec_voxels for r in reps)
+    # with the tile autotuner (z-chunk length chosen per level)
+    Ua = [torch.zeros(k, device=dev) for k in nn]
+    with torch.cuda.stream(stream):
+        flush.fill_(0.5)
+        ea0, ea1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea0.record(stream)
+        reps_a = ngf.register_batch(descs, opts, R, T, Ua, autotune=True, stream=stream)
+        ea1.record(stream)
+    stream.synchronize()
+    auto_ms = ea0.elapsed_time(ea1)
     # the same pairs one at a time
     U1 = [torch.zeros(k, device=dev) for k in nn]
     with torch.cuda.stream(stream):
@@ -442,6 +452,8 @@ def run_batch(args):
             "warmup": args.warmup, "batched_ms": batch_ms, "sequential_ms": seq_ms,
             "speedup_vs_sequential": seq_ms / batch_ms, "same_u_as_sequential": same_u,
             "max_rel_J_diff_vs_sequential": j_rel, "total_voxels": total_vox,
+            "autotuned_registration_ms": auto_ms,
+            "autotuned_max_rel_J_diff_vs_sequential": max(abs(a.J - b.J) / abs(b.J) for a, b in zip(reps_a, reps1)),
             "batched_hessvec_ms": {"default_zc": ms_default, "autotuned": ms_tuned, "zc": zc},
             "hessvec_rel_err_vs_oracle": {"max": max(errs), "median": statistics.median(errs)},
             "gpu_launches": int(launches), "clocks": clocks,
