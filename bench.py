@@ -107,6 +107,40 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def image_pass_source_hash():
+    """sha256 of the Hessian image pass's source (kernel body, its helpers and
+    the parameter and shared-memory layouts), to tell whether a stored DRAM
+    traffic figure still describes the kernel that runs."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1804_10541_b300", "csrc")
+    with open(os.path.join(csrc, "ngf_kernels.cu")) as f:
+        cu = f.read()
+    end = cu.index("image_pass<MODE_HESS>(P, blockIdx.x, blockIdx.y, blockIdx.z);")
+    with open(os.path.join(csrc, "ngf_kernels.cuh")) as f:
+        cuh = f.read()
+    a = cuh.index("constexpr int TX")
+    b = cuh.index("};", cuh.index("struct ImgSmem")) + 2
+    return hashlib.sha256((cu[:end] + cuh[a:b]).encode()).hexdigest()
+
+
+def stored_traffic():
+    """DRAM bytes per launch of k_image_hess from the committed ncu summary,
+    or None when the kernel source changed since that capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_image_hess_lung_ct.md")) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in txt.splitlines()
+                  if line.startswith(("traffic_bytes_per_launch: ", "image_pass_source_sha256: ")))
+    if fields.get("image_pass_source_sha256") != image_pass_source_hash():
+        return None
+    try:
+        return float(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -297,7 +331,7 @@ def run_ours(args):
     achieved = HESS_FLOP_PER_VOXEL * M / t_launch / 1e12
     bytes_per_voxel = 8.0 + 36.0 * N / M  # R, T + u, p read and q written, per voxel
     roofline = {"bound": "alu", "kernel": "k_image_hess", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": stored_traffic(),
                 "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 "flop_per_voxel": HESS_FLOP_PER_VOXEL, "launch_us": t_launch * 1e6,
                 "hessvec_call_us": ms_call * 1e3,

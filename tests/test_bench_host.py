@@ -63,3 +63,19 @@ def test_clock_sampler_parses_reasons():
                        "0, 2000, 2032, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
     c = s.stop()
     assert c["sm_mhz"] == 1900 and c["sm_max_mhz"] == 2032 and c["reasons"] == ["sw_power_cap"]
+
+
+def test_stored_traffic_tracks_the_kernel_source(tmp_path, monkeypatch):
+    """The roofline's DRAM traffic comes from the committed capture only while
+    the image pass's source is the one that was captured."""
+    b = bench
+    h = b.image_pass_source_hash()
+    assert len(h) == 64 and h == b.image_pass_source_hash()
+    (tmp_path / "profiles").mkdir()
+    prof = tmp_path / "profiles" / "k_image_hess_lung_ct.md"
+    prof.write_text(f"x\ntraffic_bytes_per_launch: 123\nimage_pass_source_sha256: {h}\n")
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    monkeypatch.setattr(b, "image_pass_source_hash", lambda: h)
+    assert b.stored_traffic() == 123.0
+    prof.write_text("x\ntraffic_bytes_per_launch: 123\nimage_pass_source_sha256: 00\n")
+    assert b.stored_traffic() is None
