@@ -621,6 +621,165 @@ void orc_gn_level(const orc_level* L, const double* R, const double* T, double* 
 }
 
 /* ---------------------------------------------------------------------- */
+/* L-BFGS (Sec. 2.3.2)                                                      */
+/* ---------------------------------------------------------------------- */
+
+static const double PI_ = 3.14159265358979323846;
+
+/* orthonormal DCT-II of the lines of one component along axis `ax`
+ * (inverse = transpose when `inv`) */
+static void dct_axis(const orc_level* L, int ax, int inv, double* a) {
+    const int n = L->n[ax];
+    const long stride = ax == 0 ? 1 : (ax == 1 ? (long)L->n[0] : (long)L->n[0] * L->n[1]);
+    const long lines = nnod(L) / n;
+    double* in = (double*)malloc(sizeof(double) * n);
+    for (long ln = 0; ln < lines; ++ln) {
+        /* first element of line ln: the other two indices in lexicographic order */
+        long base;
+        if (ax == 0) base = ln * n;
+        else if (ax == 1) base = (ln % L->n[0]) + (ln / L->n[0]) * (long)L->n[0] * L->n[1];
+        else base = ln;
+        for (int i = 0; i < n; ++i) in[i] = a[base + i * stride];
+        for (int k = 0; k < n; ++k) {
+            double acc = 0.0;
+            for (int i = 0; i < n; ++i) {
+                /* C[row][col] = s_row cos(pi row (2 col + 1) / 2n) */
+                const int row = inv ? i : k, col = inv ? k : i;
+                const double sr = row == 0 ? sqrt(1.0 / n) : sqrt(2.0 / n);
+                acc += sr * cos(PI_ * row * (2.0 * col + 1.0) / (2.0 * n)) * in[i];
+            }
+            a[base + k * stride] = acc;
+        }
+    }
+    free(in);
+}
+
+void orc_h0_solve(const orc_level* L, double gamma, const double* q, double* r) {
+    const long N = nnod(L);
+    const double c = L->alpha * 2.0 * hbary(L);
+    memcpy(r, q, sizeof(double) * 3 * N);
+    for (int comp = 0; comp < 3; ++comp) {
+        double* a = r + comp * N;
+        for (int ax = 0; ax < 3; ++ax) dct_axis(L, ax, 0, a);
+        for (int z = 0; z < L->n[2]; ++z)
+            for (int y = 0; y < L->n[1]; ++y)
+                for (int x = 0; x < L->n[0]; ++x) {
+                    const int kk[3] = {x, y, z};
+                    double lam = 0.0;
+                    for (int l = 0; l < 3; ++l) {
+                        const double sn = sin(PI_ * kk[l] / (2.0 * L->n[l]));
+                        lam -= 4.0 * sn * sn / (hy(L, l) * hy(L, l));
+                    }
+                    a[x + (long)L->n[0] * (y + (long)L->n[1] * z)] /= c * lam * lam + gamma;
+                }
+        for (int ax = 2; ax >= 0; --ax) dct_axis(L, ax, 1, a);
+    }
+}
+
+void orc_lbfgs_direction(const orc_level* L, double gamma, int32_t count, const double* S, const double* Y,
+                         const double* g, double* d) {
+    const long n = 3 * nnod(L);
+    double* q = (double*)malloc(sizeof(double) * n);
+    double* a = (double*)malloc(sizeof(double) * (count > 0 ? count : 1));
+    memcpy(q, g, sizeof(double) * n);
+    for (int i = count - 1; i >= 0; --i) { /* newest to oldest */
+        const double rho = 1.0 / vdot(n, Y + i * n, S + i * n);
+        a[i] = rho * vdot(n, S + i * n, q);
+        for (long j = 0; j < n; ++j) q[j] -= a[i] * Y[i * n + j];
+    }
+    orc_h0_solve(L, gamma, q, d);
+    for (int i = 0; i < count; ++i) { /* oldest to newest */
+        const double rho = 1.0 / vdot(n, Y + i * n, S + i * n);
+        const double b = rho * vdot(n, Y + i * n, d);
+        for (long j = 0; j < n; ++j) d[j] += (a[i] - b) * S[i * n + j];
+    }
+    for (long j = 0; j < n; ++j) d[j] = -d[j];
+    free(q);
+    free(a);
+}
+
+double orc_lbfgs_level(const orc_level* L, const double* R, const double* T, double* u, const orc_lbfgs_options* o,
+                       orc_gn_report* rep, double* trace) {
+    const long n = 3 * nnod(L);
+    const int m = o->memory > 0 ? o->memory : 1;
+    double* g = (double*)malloc(sizeof(double) * n);
+    double* gp = (double*)malloc(sizeof(double) * n);
+    double* d = (double*)malloc(sizeof(double) * n);
+    double* ut = (double*)malloc(sizeof(double) * n);
+    double* sl = (double*)malloc(sizeof(double) * n); /* last accepted step */
+    double* S = (double*)malloc(sizeof(double) * n * m);
+    double* Y = (double*)malloc(sizeof(double) * n * m);
+    memset(rep, 0, sizeof(*rep));
+    double gamma = o->gamma;
+    if (!(gamma > 0.0)) { /* mean of the Gauss-Newton diagonal at the start */
+        orc_gn_diagonal(L, R, T, u, d);
+        double sum = 0.0;
+        for (long j = 0; j < n; ++j) sum += d[j];
+        gamma = sum / n;
+    }
+    int count = 0, have_step = 0;
+    double D, S_, J0;
+    for (int k = 0; k < o->iters; ++k) {
+        orc_gradient(L, R, T, u, g, &D, &S_);
+        J0 = D + L->alpha * S_;
+        if (trace) trace[2 * k] = J0;
+        if (have_step) { /* pair from the last accepted step */
+            double* yn = (double*)malloc(sizeof(double) * n);
+            for (long j = 0; j < n; ++j) yn[j] = g[j] - gp[j];
+            if (vdot(n, sl, yn) > 0.0) {
+                if (count == m) { /* drop the oldest */
+                    memmove(S, S + n, sizeof(double) * n * (m - 1));
+                    memmove(Y, Y + n, sizeof(double) * n * (m - 1));
+                    --count;
+                }
+                memcpy(S + count * n, sl, sizeof(double) * n);
+                memcpy(Y + count * n, yn, sizeof(double) * n);
+                ++count;
+            }
+            free(yn);
+        }
+        const double gg = vdot(n, g, g);
+        if (gg == 0.0) { rep->status = 8; break; }
+        orc_lbfgs_direction(L, gamma, count, S, Y, g, d);
+        double gs = vdot(n, g, d);
+        if (!(gs < 0.0)) {
+            for (long j = 0; j < n; ++j) d[j] = -g[j];
+            gs = -gg;
+        }
+        double eta = 1.0;
+        int accepted = 0;
+        for (int t = 0; t < o->ls_max; ++t) {
+            for (long j = 0; j < n; ++j) ut[j] = u[j] + eta * d[j];
+            double Dt, St;
+            orc_objective(L, R, T, ut, &Dt, &St);
+            rep->ls_trials++;
+            if (Dt + L->alpha * St <= J0 + o->armijo_c1 * eta * gs) { accepted = 1; break; }
+            eta *= 0.5;
+        }
+        if (trace) trace[2 * k + 1] = accepted ? eta : 0.0;
+        if (!accepted) { rep->status = 6; break; }
+        for (long j = 0; j < n; ++j) sl[j] = ut[j] - u[j];
+        memcpy(gp, g, sizeof(double) * n);
+        memcpy(u, ut, sizeof(double) * n);
+        have_step = 1;
+        rep->gn_done++;
+    }
+    orc_objective(L, R, T, u, &D, &S_);
+    rep->D = D;
+    rep->S = S_;
+    rep->J = D + L->alpha * S_;
+    if (trace) trace[2 * o->iters] = rep->J;
+    free(g);
+    free(gp);
+    free(d);
+    free(ut);
+    free(sl);
+    free(S);
+    free(Y);
+    return gamma;
+}
+
+/* ---------------------------------------------------------------------- */
 /* multilevel (Sec. 2.3, coarse to fine)                                    */
 /* ---------------------------------------------------------------------- */
 

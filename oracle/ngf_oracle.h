@@ -122,6 +122,39 @@ void orc_gn_level(const orc_level* L, const double* R, const double* T,
                   double* u, const orc_gn_options* o, orc_gn_report* rep,
                   double* trace);
 
+/* ---- L-BFGS (Sec. 2.3.2) ----------------------------------------------- */
+/* r = H0^{-1} q with the initial Hessian H0 = alpha grad^2 S + gamma I
+ * (Sec. 2.3.2).  grad^2 S = 2 hbar^y Lap^T Lap, Lap the clamped (Neumann)
+ * Laplacian of Eq. (laplace_discretized); the 1-D clamped second difference
+ * of n nodes is diagonalised by the orthonormal DCT-II (basis
+ * cos(pi k (2i+1) / 2n), eigenvalue -4 sin^2(pi k / 2n) / hy^2), so H0 is
+ * diagonal in the 3-D DCT-II basis with eigenvalue alpha 2 hbar^y lambda^2
+ * + gamma, lambda the sum of the three 1-D eigenvalues.  Evaluated by
+ * explicit cosine sums.  q, r: 3*N. */
+void orc_h0_solve(const orc_level* L, double gamma, const double* q, double* r);
+typedef struct {
+    int32_t iters;       /* L-BFGS steps per level                        */
+    int32_t memory;      /* stored (s, y) pairs                           */
+    int32_t ls_max;      /* Armijo halvings allowed                       */
+    double  armijo_c1;   /* sufficient-decrease constant                  */
+    double  gamma;       /* H0 = alpha grad^2 S + gamma I; <= 0: the mean
+                            of the Gauss-Newton diagonal at the level's start */
+} orc_lbfgs_options;
+/* L-BFGS on one level with the two-loop recursion (Nocedal and Wright,
+ * Alg. 7.4) and H0 as above; the Armijo rule of the Gauss-Newton level; a
+ * pair (s, y) = (u_{k+1} - u_k, g_{k+1} - g_k) is kept only when s^T y > 0
+ * (oldest dropped beyond `memory`); a non-descent direction falls back to
+ * -g.  u is updated in place; report and trace as for orc_gn_level
+ * (pcg_total stays 0).  Returns the gamma used. */
+double orc_lbfgs_level(const orc_level* L, const double* R, const double* T,
+                       double* u, const orc_lbfgs_options* o,
+                       orc_gn_report* rep, double* trace);
+/* One direction of the two-loop recursion: d = -H_k g from `count` stored
+ * pairs (oldest first, each 3*N) and H0 as above. */
+void orc_lbfgs_direction(const orc_level* L, double gamma, int32_t count,
+                         const double* S, const double* Y, const double* g,
+                         double* d);
+
 /* Image pyramid restriction: coarse cell = mean of its (up to 8) children,
  * m' = ceil(m/2), the physical extent is kept (h' = h m / m'). */
 void orc_restrict(const int32_t m[3], const double* img, double* out);

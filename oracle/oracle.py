@@ -38,6 +38,11 @@ class GnReport(C.Structure):
                 ("ls_trials", C.c_int32)]
 
 
+class LbfgsOptions(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("memory", C.c_int32), ("ls_max", C.c_int32),
+                ("armijo_c1", C.c_double), ("gamma", C.c_double)]
+
+
 _lib = None
 
 
@@ -182,6 +187,41 @@ def gn_level(L, R, T, u, opts):
     trace = np.empty(2 * opts.gn_iters + 1)
     lib().orc_gn_level(C.byref(L), _p(_f64(R)), _p(_f64(T)), _p(u), C.byref(opts), C.byref(rep), _p(trace))
     return u, rep, trace
+
+
+def h0_solve(L, gamma, q):
+    """r = (alpha grad^2 S + gamma I)^{-1} q (Sec. 2.3.2, DCT-II eigenbasis)."""
+    r = np.empty(3 * nnod(L))
+    lib().orc_h0_solve(C.byref(L), C.c_double(gamma), _p(_f64(q)), _p(r))
+    return r
+
+
+def lbfgs_direction(L, gamma, S, Y, g):
+    """d = -H_k g by the two-loop recursion; S, Y: lists of stored pairs, oldest first."""
+    n = 3 * nnod(L)
+    Sa = np.ascontiguousarray(np.asarray(S, dtype=np.float64).reshape(-1)) if len(S) else np.zeros(1)
+    Ya = np.ascontiguousarray(np.asarray(Y, dtype=np.float64).reshape(-1)) if len(Y) else np.zeros(1)
+    d = np.empty(n)
+    lib().orc_lbfgs_direction(C.byref(L), C.c_double(gamma), C.c_int32(len(S)), _p(Sa), _p(Ya), _p(_f64(g)),
+                              _p(d))
+    return d
+
+
+def lbfgs_options(iters=20, memory=5, ls_max=10, armijo_c1=1e-4, gamma=0.0):
+    o = LbfgsOptions()
+    o.iters, o.memory, o.ls_max, o.armijo_c1, o.gamma = iters, memory, ls_max, armijo_c1, gamma
+    return o
+
+
+def lbfgs_level(L, R, T, u, opts):
+    """(u, report, trace, gamma) after `opts.iters` L-BFGS steps on one level."""
+    u = _f64(u).copy()
+    rep = GnReport()
+    trace = np.empty(2 * opts.iters + 1)
+    f = lib().orc_lbfgs_level
+    f.restype = C.c_double
+    gamma = f(C.byref(L), _p(_f64(R)), _p(_f64(T)), _p(u), C.byref(opts), C.byref(rep), _p(trace))
+    return u, rep, trace, gamma
 
 
 def level_at(L, lvl):

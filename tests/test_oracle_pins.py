@@ -499,3 +499,82 @@ def test_gn_level_monotone_and_armijo(orc):
     assert rep.status == 0 and rep.gn_done == 4
     assert np.all(np.diff(Js) < 0) and Js[-1] == rep.J
     assert rep.J < 0.9 * trace[0]
+
+
+# ---- L-BFGS (Sec. 2.3.2) ---------------------------------------------------
+
+def _dense_curvature_hessian(orc, L):
+    """grad^2 S as a dense matrix, column by column from the curvature operator."""
+    n = 3 * orc.nnod(L)
+    H = np.empty((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        H[:, j], _ = orc.curvature_apply(L, e)
+    return H
+
+
+@pytest.mark.parametrize("m,h,n,gamma", [((6, 5, 4), (1.0, 1.2, 2.0), (4, 3, 3), 0.37),
+                                         ((9, 4, 3), (0.7, 1.0, 1.3), (6, 3, 2), 5.0)])
+def test_h0_solve_inverts_the_curvature_hessian(orc, m, h, n, gamma):
+    """(alpha grad^2 S + gamma I) r = q, checked with the curvature operator
+    (stencil form, independent of the DCT eigenbasis)."""
+    L = orc.level(m, h, n, alpha=0.7)
+    q = np.random.default_rng(1).standard_normal(3 * orc.nnod(L))
+    r = orc.h0_solve(L, gamma, q)
+    cq, _ = orc.curvature_apply(L, r)
+    np.testing.assert_allclose(0.7 * cq + gamma * r, q, atol=1e-12 * np.abs(q).max())
+    # the translations are the null space of grad^2 S: H0 acts as gamma there
+    c = np.concatenate([np.full(orc.nnod(L), v) for v in (1.0, -2.0, 0.5)])
+    np.testing.assert_allclose(orc.h0_solve(L, gamma, c), c / gamma, rtol=1e-12)
+
+
+def test_two_loop_recursion_equals_dense_bfgs_update(orc):
+    """d = -H_k g from the two-loop recursion equals the explicit inverse-BFGS
+    updates H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T applied to the
+    dense inverse of H0, oldest pair first (Nocedal and Wright, Eq. 6.17)."""
+    L = orc.level((5, 4, 3), (1.0, 1.0, 1.5), (3, 3, 2), alpha=0.6)
+    n = 3 * orc.nnod(L)
+    gamma = 0.8
+    rng = np.random.default_rng(3)
+    H = np.linalg.inv(0.6 * _dense_curvature_hessian(orc, L) + gamma * np.eye(n))
+    S, Y = [], []
+    A = rng.standard_normal((n, n))
+    A = A @ A.T + n * np.eye(n)   # SPD: s^T y > 0
+    for _ in range(4):
+        s = rng.standard_normal(n)
+        S.append(s)
+        Y.append(A @ s)
+    Hk = H.copy()
+    for s, y in zip(S, Y):
+        rho = 1.0 / (y @ s)
+        V = np.eye(n) - rho * np.outer(y, s)
+        Hk = V.T @ Hk @ V + rho * np.outer(s, s)
+    g = rng.standard_normal(n)
+    d = orc.lbfgs_direction(L, gamma, S, Y, g)
+    np.testing.assert_allclose(d, -Hk @ g, rtol=1e-9, atol=1e-12 * np.abs(Hk @ g).max())
+    # secant condition of the newest pair
+    np.testing.assert_allclose(-orc.lbfgs_direction(L, gamma, S, Y, Y[-1]), S[-1], rtol=1e-9)
+    # no pairs: d = -H0^{-1} g
+    np.testing.assert_allclose(orc.lbfgs_direction(L, gamma, [], [], g), -H @ g, rtol=1e-9,
+                               atol=1e-12 * np.abs(H @ g).max())
+
+
+@pytest.mark.slow
+def test_lbfgs_level_monotone_armijo_and_default_gamma(orc):
+    from paper_1804_10541_b300 import synth
+    m, h, n = (16, 16, 16), (1, 1, 1), (9, 9, 9)
+    R, T, _ = synth.blob_pair(m, seed=0)
+    R, T = R.double().numpy(), T.double().numpy()
+    L = orc.level(m, h, n, alpha=1.0, tau=0.1, rho=0.1)
+    opts = orc.lbfgs_options(iters=8, memory=4)
+    u0 = np.zeros(3 * 729)
+    u, rep, trace, gamma = orc.lbfgs_level(L, R, T, u0, opts)
+    assert np.isclose(gamma, orc.gn_diagonal(L, R, T, u0).mean(), rtol=1e-12)
+    Js = trace[0:2 * rep.gn_done + 1:2]
+    assert rep.status == 0 and rep.gn_done == 8 and rep.pcg_total == 0
+    assert np.all(np.diff(Js) < 0) and Js[-1] == rep.J
+    assert rep.J < 0.9 * trace[0]
+    # every accepted step satisfied the Armijo condition: J decreased
+    etas = trace[1:2 * rep.gn_done:2]
+    assert np.all(etas > 0)
