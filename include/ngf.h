@@ -162,6 +162,14 @@ ngf_status pcg_solve(ngf_plan* plan, ngf_pcg_state* st, const float* R, const fl
 /* Read the state (synchronises). */
 ngf_status pcg_read(ngf_plan* plan, const ngf_pcg_state* st, ngf_pcg_info* info);
 
+/* ---- L-BFGS initial Hessian (Sec. 2.3.2) ------------------------------
+ * r = (alpha grad^2 S + gamma I)^{-1} q, gamma > 0: the clamped Laplacian is
+ * diagonal in the 3-D DCT-II basis, so the solve is three forward
+ * transforms, one division per coefficient and three inverse transforms
+ * (FP32, O(N (n_x + n_y + n_z)) work).  q, r: 3*N device arrays (may
+ * alias); enqueued on the plan's stream. */
+ngf_status ngf_h0_solve(ngf_plan* plan, double gamma, const float* q, float* r);
+
 /* ---- full registration (Sec. 2.3, coarse to fine) ---------------------- */
 typedef struct {
     int32_t levels;       /* >= 1; level 0 is `finest`, each coarser level halves
@@ -176,7 +184,14 @@ typedef struct {
                              that level; host or device); NULL = zero field on
                              the coarsest level                                 */
     int32_t use_graph;    /* capture each PCG solve as a CUDA graph             */
+    int32_t method;       /* NGF_METHOD_GN (Sec. 2.3.1) or NGF_METHOD_LBFGS
+                             (Sec. 2.3.2; gn_iters = L-BFGS steps per level,
+                             pcg_iters unused)                                 */
+    int32_t lbfgs_memory; /* stored (s, y) pairs, >= 1                          */
+    double  lbfgs_gamma;  /* H0 = alpha grad^2 S + gamma I; <= 0: the mean of
+                             the Gauss-Newton diagonal at each level's start   */
 } ngf_options;
+enum { NGF_METHOD_GN = 0, NGF_METHOD_LBFGS = 1 };
 
 typedef struct {
     double  J, D, S;      /* objective at the returned u (finest level)         */

@@ -223,7 +223,8 @@ static void clear_prof(Plan* p, int which) {
 static void free_plan(Plan* p) {
     for (int k = 0; k < 4; ++k) clear_prof(p, k);
     for (void* ptr : {(void*)p->ftab, (void*)p->wtab, (void*)p->g0.mem, (void*)p->g1.mem, (void*)p->partial,
-                      (void*)p->L, (void*)p->ctab, (void*)p->dsc, (void*)p->dpart, (void*)p->dcount})
+                      (void*)p->L, (void*)p->ctab, (void*)p->dsc, (void*)p->dpart, (void*)p->dcount,
+                      (void*)p->dct_cos, (void*)p->dct_mu, (void*)p->h0_tmp})
         dev_free(ptr, p->stream);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     p->graph = nullptr;
@@ -500,6 +501,51 @@ ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g1, diag, nullptr, p->ctab, nullptr, nullptr);
     NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+    return NGF_OK;
+}
+
+// r = (alpha grad^2 S + gamma I)^{-1} q through the DCT-II eigenbasis of the
+// clamped Laplacian (tables built on first use)
+ngf_status h0_impl(Plan* p, double gamma, const float* q, float* r) {
+    if (!p->dct_cos) {
+        const int nt = p->n[0] + p->n[1] + p->n[2];
+        std::vector<float> cs(4 * (size_t)nt), mu(nt);
+        int oc = 0, om = 0;
+        for (int a = 0; a < 3; ++a) {
+            const int n = p->n[a];
+            for (int m = 0; m < 4 * n; ++m) cs[oc + m] = (float)std::cos(M_PI * m / (2.0 * n));
+            for (int k = 0; k < n; ++k) {
+                const double sn = std::sin(M_PI * k / (2.0 * n));
+                mu[om + k] = (float)(-4.0 * sn * sn / (p->hy[a] * p->hy[a]));
+            }
+            oc += 4 * n;
+            om += n;
+        }
+        NGF_CU(p, dev_alloc((void**)&p->dct_cos, cs.size() * sizeof(float), p->stream), "allocate DCT tables");
+        NGF_CU(p, dev_alloc((void**)&p->dct_mu, mu.size() * sizeof(float), p->stream), "allocate DCT tables");
+        NGF_CU(p, dev_alloc((void**)&p->h0_tmp, 3 * p->N * sizeof(float), p->stream), "allocate DCT scratch");
+        NGF_CU(p, cudaMemcpyAsync(p->dct_cos, cs.data(), cs.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream),
+               "copy DCT tables");
+        NGF_CU(p, cudaMemcpyAsync(p->dct_mu, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream),
+               "copy DCT tables");
+        NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    }
+    const NodeGeom G = node_geom(p);
+    const dim3 grid(grid_for(3 * p->N, 16 * 148)), blk(NT);
+    const float* cosx = p->dct_cos;
+    const float* cosy = cosx + 4 * p->n[0];
+    const float* cosz = cosy + 4 * p->n[1];
+    float* t = p->h0_tmp;
+    // forward x, y, z (q -> t -> r -> t), scale, inverse z, y, x (t -> r -> t -> r)
+    NGF_CU(p, launch(k_dct_axis, grid, blk, 0, p->stream, G, 0, 0, cosx, q, t), "k_dct_axis");
+    NGF_CU(p, launch(k_dct_axis, grid, blk, 0, p->stream, G, 1, 0, cosy, (const float*)t, r), "k_dct_axis");
+    NGF_CU(p, launch(k_dct_axis, grid, blk, 0, p->stream, G, 2, 0, cosz, (const float*)r, t), "k_dct_axis");
+    NGF_CU(p, launch(k_h0_scale, grid, blk, 0, p->stream, G, (const float*)p->dct_mu,
+                     (float)(p->desc.alpha * 2.0 * p->hbary), (float)gamma, t),
+           "k_h0_scale");
+    NGF_CU(p, launch(k_dct_axis, grid, blk, 0, p->stream, G, 2, 1, cosz, (const float*)t, r), "k_dct_axis");
+    NGF_CU(p, launch(k_dct_axis, grid, blk, 0, p->stream, G, 1, 1, cosy, (const float*)r, t), "k_dct_axis");
+    NGF_CU(p, launch(k_dct_axis, grid, blk, 0, p->stream, G, 0, 1, cosx, (const float*)t, r), "k_dct_axis");
     return NGF_OK;
 }
 
@@ -782,5 +828,13 @@ ngf_status ngf_profile_read(ngf_plan* plan, int32_t which, double* ms, int64_t* 
 }
 
 int64_t ngf_launch_count(void) { return launch_counter().load(); }
+
+ngf_status ngf_h0_solve(ngf_plan* plan, double gamma, const float* q, float* r) {
+    if (!plan) return set_error(nullptr, NGF_EINVAL, "plan is NULL");
+    Plan* p = &plan->impl;
+    if (!(gamma > 0.0)) return set_error(p, NGF_EINVAL, "gamma must be > 0");
+    NGF_TRY(need_dev(p, {{q, "q"}, {r, "r"}}));
+    return h0_impl(p, gamma, q, r);
+}
 
 }  // extern "C"

@@ -58,6 +58,111 @@ using namespace ngf;
         if (_s != NGF_OK) return _s; \
     } while (0)
 
+// L-BFGS on one level (Sec. 2.3.2): two-loop recursion with H0 = alpha
+// grad^2 S + gamma I (ngf_h0_solve), the Armijo rule of the Gauss-Newton
+// level, pairs (s, y) = (u_{k+1} - u_k, g_{k+1} - g_k) kept when s^T y > 0
+// in a ring of `lbfgs_memory`, steepest descent when the direction is not a
+// descent direction.  u/ut are swapped on acceptance like the Gauss-Newton
+// loop's.  lb: float64 scalars, [0, m) s.q, [m, 2m) a, [2m, 3m) y.r, 3m s.y.
+static ngf_status lbfgs_level(Plan* p, const ngf_level_desc& d, const ngf_options* o, const float* R, const float* T,
+                              float*& u, float*& ut, float* g, float* dir, float* gp, float* sl, float* yt,
+                              float* Sr, float* Yr, double* lb, double* dsc, ngf_report& r) {
+    cudaStream_t stream = p->stream;
+    const long long n = 3 * p->N;
+    const int m = o->lbfgs_memory;
+    const dim3 gv(p->node_blocks), blk(NT);
+    double gamma = o->lbfgs_gamma;
+    if (!(gamma > 0.0)) {  // mean of the Gauss-Newton diagonal at the level's start
+        DRV_TRY(diagonal_impl(p, R, T, u, dir));
+        DRV_TRY(dot_impl(p, n, dir, nullptr, dsc + 2));
+        double sum = 0.0;
+        DRV_CU(cudaMemcpyAsync(&sum, dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, stream), "read sum");
+        DRV_CU(cudaStreamSynchronize(stream), "sync");
+        gamma = sum / (double)n;
+        if (!(gamma > 0.0)) gamma = 1.0;
+    }
+    std::vector<double> rho(m);
+    int head = 0, count = 0;
+    bool have_step = false;
+    for (int k = 0; k < o->gn_iters; ++k) {
+        DRV_TRY(gradient_impl(p, R, T, u, g, dsc, dsc + 1));
+        DRV_TRY(dot_impl(p, n, g, g, dsc + 2));
+        if (have_step) {  // y = g - g_prev, s.y
+            DRV_CU(launch(k_axpy, gv, blk, 0, stream, n, -1.0f, (const float*)g, (const float*)gp, yt), "k_axpy");
+            DRV_TRY(dot_impl(p, n, sl, yt, lb + 3 * m));
+        }
+        double h[3], sy = 0.0;
+        DRV_CU(cudaMemcpyAsync(h, dsc, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
+        if (have_step) DRV_CU(cudaMemcpyAsync(&sy, lb + 3 * m, sizeof(double), cudaMemcpyDeviceToHost, stream), "read sy");
+        DRV_CU(cudaStreamSynchronize(stream), "sync");
+        if (have_step && sy > 0.0) {  // keep the pair, dropping the oldest when full
+            const int slot = (count == m) ? head : (head + count) % m;
+            DRV_CU(cudaMemcpyAsync(Sr + (size_t)slot * n, sl, n * sizeof(float), cudaMemcpyDeviceToDevice, stream),
+                   "store s");
+            DRV_CU(cudaMemcpyAsync(Yr + (size_t)slot * n, yt, n * sizeof(float), cudaMemcpyDeviceToDevice, stream),
+                   "store y");
+            rho[slot] = 1.0 / sy;
+            if (count == m) head = (head + 1) % m;
+            else ++count;
+        }
+        const double J0 = h[0] + d.alpha * h[1], gg = h[2];
+        if (gg == 0.0) break;
+        // two-loop recursion: dir = -H_k g
+        DRV_CU(cudaMemcpyAsync(dir, g, n * sizeof(float), cudaMemcpyDeviceToDevice, stream), "copy g");
+        for (int i = count - 1; i >= 0; --i) {
+            const int sl_i = (head + i) % m;
+            DRV_TRY(dot_impl(p, n, Sr + (size_t)sl_i * n, dir, lb + i));
+            DRV_CU(launch(k_lbfgs_q, gv, blk, 0, stream, n, rho[sl_i], (const double*)(lb + i),
+                          (const float*)(Yr + (size_t)sl_i * n), dir, lb + m + i),
+                   "k_lbfgs_q");
+        }
+        DRV_TRY(h0_impl(p, gamma, dir, dir));
+        for (int i = 0; i < count; ++i) {
+            const int sl_i = (head + i) % m;
+            DRV_TRY(dot_impl(p, n, Yr + (size_t)sl_i * n, dir, lb + 2 * m + i));
+            DRV_CU(launch(k_lbfgs_r, gv, blk, 0, stream, n, rho[sl_i], (const double*)(lb + 2 * m + i),
+                          (const double*)(lb + m + i), (const float*)(Sr + (size_t)sl_i * n), dir),
+                   "k_lbfgs_r");
+        }
+        DRV_CU(launch(k_scale, gv, blk, 0, stream, n, -1.0f, (const float*)dir, dir), "k_scale");
+        DRV_TRY(dot_impl(p, n, g, dir, dsc + 2));
+        DRV_CU(cudaMemcpyAsync(h + 2, dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, stream), "read gs");
+        DRV_CU(cudaStreamSynchronize(stream), "sync");
+        double gs = h[2];
+        if (!(gs < 0.0)) {  // not a descent direction: steepest descent
+            DRV_CU(launch(k_scale, gv, blk, 0, stream, n, -1.0f, (const float*)g, dir), "k_scale");
+            gs = -gg;
+        }
+        double eta = 1.0;
+        bool accepted = false;
+        for (int t = 0; t < o->ls_max; ++t) {
+            DRV_CU(launch(k_axpy, gv, blk, 0, stream, n, (float)eta, (const float*)u, (const float*)dir, ut),
+                   "k_axpy");
+            DRV_TRY(objective_impl(p, R, T, ut, dsc, dsc + 1));
+            DRV_CU(cudaMemcpyAsync(h, dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
+            DRV_CU(cudaStreamSynchronize(stream), "sync");
+            r.ls_trials++;
+            if (h[0] + d.alpha * h[1] <= J0 + o->armijo_c1 * eta * gs) {
+                accepted = true;
+                break;
+            }
+            eta *= 0.5;
+        }
+        if (!accepted) {
+            r.ls_fail++;
+            r.status = NGF_ELINESEARCH;
+            break;
+        }
+        // last step s = ut - u, previous gradient, accept
+        DRV_CU(launch(k_axpy, gv, blk, 0, stream, n, -1.0f, (const float*)ut, (const float*)u, sl), "k_axpy");
+        DRV_CU(cudaMemcpyAsync(gp, g, n * sizeof(float), cudaMemcpyDeviceToDevice, stream), "copy g");
+        std::swap(u, ut);
+        have_step = true;
+        r.gn_done++;
+    }
+    return NGF_OK;
+}
+
 extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ngf_options* o, const float* R,
                                           const float* T, float* u_out, ngf_report* rep, void* cuda_stream) {
     const auto t_start = std::chrono::steady_clock::now();
@@ -68,6 +173,11 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
     if (o->levels < 1 || o->levels > 16) return set_error(nullptr, NGF_EINVAL, "levels must be in [1, 16]");
     if (o->gn_iters < 0 || o->pcg_iters < 0 || o->ls_max < 1)
         return set_error(nullptr, NGF_EINVAL, "gn_iters, pcg_iters >= 0 and ls_max >= 1 required");
+    if (o->method != NGF_METHOD_GN && o->method != NGF_METHOD_LBFGS)
+        return set_error(nullptr, NGF_EINVAL, "method must be NGF_METHOD_GN or NGF_METHOD_LBFGS");
+    const bool lbfgs = o->method == NGF_METHOD_LBFGS;
+    if (lbfgs && (o->lbfgs_memory < 1 || o->lbfgs_memory > 64))
+        return set_error(nullptr, NGF_EINVAL, "lbfgs_memory must be in [1, 64]");
     if (o->u_init && (o->start_level < 0 || o->start_level >= o->levels))
         return set_error(nullptr, NGF_EINVAL, "start_level out of range");
     cudaStream_t stream = (cudaStream_t)cuda_stream;
@@ -126,6 +236,18 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
     DRV_CU(alloc(bcnt, 4 * sizeof(unsigned int)), "allocate counter");
     DRV_CU(cudaMemsetAsync(bcnt.ptr, 0, 4 * sizeof(unsigned int), stream), "memset(counter)");
     DRV_CU(alloc(btab, 3 * 4096 * (sizeof(int) + sizeof(float))), "allocate prolongation tables");
+    // L-BFGS: previous gradient, last step, candidate y, the (s, y) ring and
+    // float64 scalars of the two-loop recursion
+    DevBuf bgp, bsl, byt, bS, bY, blb;
+    const int mem = lbfgs ? o->lbfgs_memory : 0;
+    if (lbfgs) {
+        DRV_CU(alloc(bgp, n3 * sizeof(float)), "allocate g_prev");
+        DRV_CU(alloc(bsl, n3 * sizeof(float)), "allocate step");
+        DRV_CU(alloc(byt, n3 * sizeof(float)), "allocate y");
+        DRV_CU(alloc(bS, (size_t)mem * n3 * sizeof(float)), "allocate s ring");
+        DRV_CU(alloc(bY, (size_t)mem * n3 * sizeof(float)), "allocate y ring");
+        DRV_CU(alloc(blb, (size_t)(3 * mem + 8) * sizeof(double)), "allocate two-loop scalars");
+    }
     double* dsc = bsc.as<double>();  // 0 D, 1 S, 2 dot, 3 non-finite count; 8.. PCG state
     double* pcg_sc = dsc + 8;
 
@@ -210,7 +332,11 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
         st.rtol = o->pcg_rtol;
         float* g = bg.as<float>();
         const long long n = 3 * N;
-        for (int k = 0; k < o->gn_iters; ++k) {
+        if (lbfgs) {
+            DRV_TRY(lbfgs_level(p, d, o, Rl[l], Tl[l], u, ut, g, bdiag.as<float>(), bgp.as<float>(), bsl.as<float>(),
+                                byt.as<float>(), bS.as<float>(), bY.as<float>(), blb.as<double>(), dsc, r));
+        }
+        for (int k = 0; k < (lbfgs ? 0 : o->gn_iters); ++k) {
             DRV_TRY(gradient_impl(p, Rl[l], Tl[l], u, g, dsc, dsc + 1));
             DRV_TRY(dot_impl(p, n, g, g, dsc + 2));
             double h[3];

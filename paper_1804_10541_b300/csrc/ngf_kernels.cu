@@ -1060,7 +1060,8 @@ __global__ void __launch_bounds__(NT) k_pcg_dir(PcgParams P) { pcg_dir_body(P, b
 __device__ __forceinline__ void dot_body(const DotArgs& A, unsigned int bid, unsigned int nb) {
     __shared__ double red[NT];
     DFAcc acc;
-    for (unsigned int i = bid * NT + threadIdx.x; i < (unsigned int)A.n; i += nb * NT) acc.add_prod(A.a[i], A.b[i]);
+    for (unsigned int i = bid * NT + threadIdx.x; i < (unsigned int)A.n; i += nb * NT)
+        acc.add_prod(A.a[i], A.b ? A.b[i] : 1.f);
     const double bs = block_sum(acc.value(), red);
     grid_sum_finish(bs, A.part, A.count, A.out, 1.0, red, (int)nb, (int)bid);
 }
@@ -1138,6 +1139,74 @@ __global__ void __launch_bounds__(NT) k_prolong(int f0, int f1, int f2, int c0, 
         const float a0 = fmaf(wy, e10 - e00, e00), a1 = fmaf(wy, e11 - e01, e01);
         uf[i] = fmaf(wz, a1 - a0, a0);
     }
+}
+
+// ---------------------------------------------------------------------------
+// L-BFGS initial Hessian (Sec. 2.3.2).  The clamped second difference of n
+// nodes is diagonalised by the orthonormal DCT-II C[k][i] = s_k cos(pi k
+// (2i+1) / 2n) (s_0 = sqrt(1/n), s_k = sqrt(2/n)); k (2i+1) is reduced mod 4n
+// incrementally, so the cosines come from one table of 4n values.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_dct_axis(NodeGeom G, int axis, int inv, const float* __restrict__ costab,
+                                                 const float* __restrict__ in, float* __restrict__ out) {
+    const unsigned int total = 3u * (unsigned int)G.N;
+    const int n = axis == 0 ? G.n0 : (axis == 1 ? G.n1 : G.n2);
+    const int stride = axis == 0 ? 1 : (axis == 1 ? G.n0 : G.n0 * G.n1);
+    const int n4 = 4 * n;
+    const float s0 = sqrtf(1.f / (float)n), s1 = sqrtf(2.f / (float)n);
+    for (unsigned int e = blockIdx.x * NT + threadIdx.x; e < total; e += gridDim.x * NT) {
+        int c, nd, ix, iy, iz;
+        node_coords(e, G, c, nd, ix, iy, iz);
+        const int k = axis == 0 ? ix : (axis == 1 ? iy : iz);
+        const float* line = in + (e - (unsigned int)(k * stride));
+        float acc = 0.f;
+        if (!inv) {  // out[k] = s_k sum_i cos(pi k (2i+1) / 2n) in[i]
+            const int step = (2 * k) % n4;
+            int m = k % n4;
+            for (int i = 0; i < n; ++i) {
+                acc = fmaf(__ldg(costab + m), __ldg(line + i * stride), acc);
+                m += step;
+                if (m >= n4) m -= n4;
+            }
+            acc *= (k == 0) ? s0 : s1;
+        } else {     // out[i] = sum_j s_j cos(pi j (2i+1) / 2n) in[j], i = k
+            const int step = 2 * k + 1;
+            int m = 0;
+            for (int j = 0; j < n; ++j) {
+                acc = fmaf(((j == 0) ? s0 : s1) * __ldg(costab + m), __ldg(line + j * stride), acc);
+                m += step;
+                if (m >= n4) m -= n4;
+            }
+        }
+        out[e] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_h0_scale(NodeGeom G, const float* __restrict__ mu, float c, float gamma,
+                                                 float* __restrict__ a) {
+    const unsigned int total = 3u * (unsigned int)G.N;
+    for (unsigned int e = blockIdx.x * NT + threadIdx.x; e < total; e += gridDim.x * NT) {
+        int cc, nd, ix, iy, iz;
+        node_coords(e, G, cc, nd, ix, iy, iz);
+        const float lam = mu[ix] + mu[G.n0 + iy] + mu[G.n0 + G.n1 + iz];
+        a[e] = a[e] / fmaf(c * lam, lam, gamma);
+    }
+}
+
+__global__ void __launch_bounds__(NT) k_lbfgs_q(long long n, double rho, const double* dot,
+                                                const float* __restrict__ y, float* __restrict__ q, double* a_out) {
+    const double a = rho * dot[0];
+    const float af = (float)a;
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
+        q[i] = fmaf(-af, y[i], q[i]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a_out = a;
+}
+
+__global__ void __launch_bounds__(NT) k_lbfgs_r(long long n, double rho, const double* dot, const double* a,
+                                                const float* __restrict__ s, float* __restrict__ r) {
+    const float coef = (float)(a[0] - rho * dot[0]);
+    for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < n; i += (long long)gridDim.x * NT)
+        r[i] = fmaf(coef, s[i], r[i]);
 }
 
 // ---------------------------------------------------------------------------

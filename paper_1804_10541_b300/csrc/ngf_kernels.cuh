@@ -190,7 +190,7 @@ struct PcgParams {
 struct DotArgs {
     long long n;
     const float* a;
-    const float* b;
+    const float* b;  // null: sum of a
     double* part;
     unsigned int* count;
     double* out;
@@ -237,6 +237,22 @@ __global__ void k_scale(long long n, float a, const float* __restrict__ x, float
 __global__ void k_nonfinite(long long n, const float* __restrict__ a, double* part, unsigned int* count,
                             double* out);
 __global__ void k_restrict(int m0, int m1, int m2, const float* __restrict__ img, float* __restrict__ out);
+
+// ---- L-BFGS (Sec. 2.3.2): H0 = alpha grad^2 S + gamma I in the DCT-II basis
+// One orthonormal DCT-II (inv = 0) or its transpose (inv = 1) along `axis`
+// of a 3 x N nodal field; costab: cos(pi m / 2n) for m in [0, 4n), n the
+// axis length.
+__global__ void k_dct_axis(NodeGeom G, int axis, int inv, const float* __restrict__ costab,
+                           const float* __restrict__ in, float* __restrict__ out);
+// a /= c lambda^2 + gamma per DCT coefficient; mu: 1-D eigenvalues of the
+// clamped second difference, x | y | z
+__global__ void k_h0_scale(NodeGeom G, const float* __restrict__ mu, float c, float gamma, float* __restrict__ a);
+// two-loop recursion steps with float64 scalars on the device:
+// a = rho (s.q), q -= a y   |   r += (a - rho (y.r)) s
+__global__ void k_lbfgs_q(long long n, double rho, const double* dot, const float* __restrict__ y,
+                          float* __restrict__ q, double* a_out);
+__global__ void k_lbfgs_r(long long n, double rho, const double* dot, const double* a,
+                          const float* __restrict__ s, float* __restrict__ r);
 
 // ---- batched forms (independent problems of uneven size in one launch)
 // Image passes: a persistent grid takes work items (pair, tile x, tile y,

@@ -51,6 +51,9 @@ struct Plan {
     float* partial = nullptr;
     float* L = nullptr;      // Laplacian scratch, 3N
     float* ctab = nullptr;   // curvature diagonal per axis: d1 | dg (2 x (n0+n1+n2))
+    float* dct_cos = nullptr;  // L-BFGS: cos(pi m / 2n) tables, 4 n per axis (x | y | z)
+    float* dct_mu = nullptr;   // L-BFGS: 1-D eigenvalues of the clamped second difference
+    float* h0_tmp = nullptr;   // L-BFGS: 3N scratch of the DCT passes
     double* dsc = nullptr;   // scalars: 0 D, 1 S, 2 dot, 3 nonfinite count
     double* dpart = nullptr;
     unsigned int* dcount = nullptr;
@@ -90,6 +93,7 @@ ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u
 ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag);
 cudaError_t prof_mark(Plan* p, int which);
 ngf_status dot_impl(Plan* p, long long n, const float* a, const float* b, double* dout);
+ngf_status h0_impl(Plan* p, double gamma, const float* q, float* r);
 int grid_for(long long n, int max_blocks);
 // plan with a requested z-chunk length (0: about two CTAs per SM)
 ngf_status plan_create(ngf_plan** out, const ngf_level_desc* desc, cudaStream_t stream, int zc);

@@ -24,7 +24,9 @@ EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_la
            "ngf_gn_diagonal", "pcg_init", "pcg_step", "pcg_solve", "pcg_read", "register_multilevel",
            "ngf_objective_noalloc", "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count",
            "ngf_batch_create", "ngf_batch_destroy", "ngf_batch_objective", "ngf_batch_gradient",
-           "ngf_batch_hessvec", "ngf_batch_diagonal", "ngf_batch_autotune", "ngf_batch_zc", "register_batch"]
+           "ngf_batch_hessvec", "ngf_batch_diagonal", "ngf_batch_autotune", "ngf_batch_zc", "register_batch",
+           "ngf_h0_solve"]
+NGF_METHOD_GN, NGF_METHOD_LBFGS = 0, 1
 
 
 class LevelDesc(C.Structure):
@@ -44,7 +46,8 @@ class PcgInfo(C.Structure):
 class Options(C.Structure):
     _fields_ = [("levels", C.c_int32), ("gn_iters", C.c_int32), ("pcg_iters", C.c_int32), ("ls_max", C.c_int32),
                 ("armijo_c1", C.c_double), ("pcg_rtol", C.c_double), ("start_level", C.c_int32),
-                ("u_init", C.c_void_p), ("use_graph", C.c_int32)]
+                ("u_init", C.c_void_p), ("use_graph", C.c_int32), ("method", C.c_int32),
+                ("lbfgs_memory", C.c_int32), ("lbfgs_gamma", C.c_double)]
 
 
 class Report(C.Structure):
@@ -89,6 +92,7 @@ def declare(lib):
         "ngf_batch_diagonal": [P, VP, VP, VP, VP],
         "ngf_batch_autotune": [P, VP, VP, VP, VP, VP, C.POINTER(I32), D],
         "register_batch": [I32, C.POINTER(LevelDesc), C.POINTER(Options), VP, VP, VP, C.POINTER(Report), I32, VP],
+        "ngf_h0_solve": [P, C.c_double, VP, VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -237,13 +241,19 @@ def pcg_read(plan, st):
 
 
 def options(levels, gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rtol=0.0, u_init=None,
-            start_level=0, use_graph=True):
+            start_level=0, use_graph=True, method=NGF_METHOD_GN, lbfgs_memory=5, lbfgs_gamma=0.0):
     o = Options()
     o.levels, o.gn_iters, o.pcg_iters, o.ls_max = levels, gn_iters, pcg_iters, ls_max
     o.armijo_c1, o.pcg_rtol, o.start_level = armijo_c1, pcg_rtol, start_level
     o.u_init = _ptr(u_init)
     o.use_graph = 1 if use_graph else 0
+    o.method, o.lbfgs_memory, o.lbfgs_gamma = int(method), int(lbfgs_memory), float(lbfgs_gamma)
     return o
+
+
+def ngf_h0_solve(plan, gamma, q, r):
+    """r = (alpha grad^2 S + gamma I)^{-1} q (the L-BFGS initial Hessian)."""
+    _check(lib.ngf_h0_solve(plan, float(gamma), _ptr(q), _ptr(r)), plan)
 
 
 def register_multilevel(desc, opts, R, T, u_out, stream=None):
