@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "lung_ct"
 GN_ITERS, PCG_ITERS = 10, 20
+LBFGS_ITERS = 50  # L-BFGS steps per level of the comparison run
 # algorithmic cost of one gn_hessvec image-grid pass per voxel (see design notes):
 # P u and P p (separable) 30, warp + dT 50, 12 differences + N, A, B 40, rho_hat 25,
 # v = dr s and t = dr^T v 28, q_hat 3, P^T 25  ->  200 FP32 flop (FMA = 2 flop)
@@ -285,6 +286,21 @@ def run_ours(args):
     stream.synchronize()
     fixed_ms = e0.elapsed_time(e1)
 
+    # ---- L-BFGS registration of the same pair (Sec. 2.3.2), for comparison
+    opts_l = ngf.options(levels=levels, gn_iters=LBFGS_ITERS, method=ngf.NGF_METHOD_LBFGS, lbfgs_memory=5)
+    ul = torch.empty(3 * N, device=dev)
+    with torch.cuda.stream(stream):
+        ngf.register_multilevel(desc, opts_l, R, T, ul, stream)
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep_l = ngf.register_multilevel(desc, opts_l, R, T, ul, stream)
+        e1.record(stream)
+    stream.synchronize()
+    lbfgs = {"registration_ms": e0.elapsed_time(e1), "steps_per_level": LBFGS_ITERS, "memory": 5,
+             "final_J": rep_l.J, "steps": rep_l.gn_done, "ls_trials": rep_l.ls_trials,
+             "J_rel_to_gauss_newton": (rep_l.J - reps[-1].J) / abs(reps[-1].J)}
+
     # ---- end to end through the public API with host buffers (pinned)
     Rp = torch.empty(M, dtype=torch.float32, pin_memory=True)
     Tp = torch.empty(M, dtype=torch.float32, pin_memory=True)
@@ -354,7 +370,7 @@ def run_ours(args):
                            "registration_ms": 1e3 * t_max / args.steps, "final_J": r0.J,
                            "gn_done": r0.gn_done, "pcg_total": r0.pcg_total, "ls_trials": r0.ls_trials,
                            "fixed_ms_per_registration": fixed_ms},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "lbfgs": lbfgs,
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
     if ws > 1:
