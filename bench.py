@@ -512,6 +512,46 @@ def run_batch(args):
     return 0
 
 
+def run_thorax(args):
+    """Full multilevel registration of the 512x512x900 thorax-abdomen workload
+    (0.8x0.8x1.0 mm, 129x129x225 nodes, 5 levels, 10 GN x 20 PCG per level),
+    timed with CUDA events after warm-up; its own JSON line."""
+    import torch
+    from paper_1804_10541_b300 import ngf, synth
+    dev = torch.device("cuda", 0)
+    R, T, _, w = synth.make("thorax_abd", device=dev)
+    m, h, n, levels = w["m"], w["h"], w["n"], w["levels"]
+    N = n[0] * n[1] * n[2]
+    desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"])
+    opts = ngf.options(levels=levels, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True)
+    stream = torch.cuda.Stream(device=dev)
+    u = torch.empty(3 * N, device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            ngf.register_multilevel(desc, opts, R, T, u, stream)
+    stream.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            rep = ngf.register_multilevel(desc, opts, R, T, u, stream)
+            ev[k][1].record(stream)
+    stream.synchronize()
+    clocks = sampler.stop()
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    line = {"workload": f"thorax_abd {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes {n[0]}x{n[1]}x{n[2]}, "
+                        f"{levels} levels, {GN_ITERS} GN x {PCG_ITERS} PCG", "metric": METRIC,
+            "value": rep.hessvec_voxels / (ms / 1e3) / 1e9, "unit": "Gvoxel/s", "registration_ms": ms,
+            "steps": args.steps, "warmup": args.warmup, "final_J": rep.J, "gn_done": rep.gn_done,
+            "pcg_total": rep.pcg_total, "ls_trials": rep.ls_trials, "status": rep.status,
+            "device_memory_peak_gb": torch.cuda.max_memory_allocated(dev) / 1e9, "clocks": clocks,
+            "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -521,13 +561,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", default=None, help="profile driver: gn_hessvec only on this workload")
     ap.add_argument("--calls", type=int, default=3)
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_64"],
-                    help="batch_64: the batched form on 64 uneven pairs (its own JSON line)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_64", "thorax_abd"],
+                    help="batch_64: the batched form on 64 uneven pairs; thorax_abd: the 512x512x900 "
+                         "registration (each its own JSON line)")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
     if args.workload == "batch_64":
         return run_batch(args)
+    if args.workload == "thorax_abd":
+        return run_thorax(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
