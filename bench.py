@@ -546,7 +546,7 @@ def run_thorax(args):
             "value": rep.hessvec_voxels / (ms / 1e3) / 1e9, "unit": "Gvoxel/s", "registration_ms": ms,
             "steps": args.steps, "warmup": args.warmup, "final_J": rep.J, "gn_done": rep.gn_done,
             "pcg_total": rep.pcg_total, "ls_trials": rep.ls_trials, "status": rep.status,
-            "device_memory_peak_gb": torch.cuda.max_memory_allocated(dev) / 1e9, "clocks": clocks,
+            "torch_allocated_peak_gb": torch.cuda.max_memory_allocated(dev) / 1e9, "clocks": clocks,
             "dtype": "f32", "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
