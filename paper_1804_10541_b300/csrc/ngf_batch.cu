@@ -53,6 +53,7 @@ struct Batch {
     DevArray<int4> items0, items3, items4;  // image tiles (halo 0); diagonal tiles (halo 1) by span
     DevArray<unsigned int> qctr;             // queue head, finished CTAs
     DevArray<int> first1, firstv, firstd;    // block ranges: per node, per vector element, dot
+    DevArray<int> pair1, pairv, paird;       // pair of every block of those launches
     // parameter tables of the operator calls
     DevArray<ImgParams> t_img;
     DevArray<LapArgs> t_lap;
@@ -80,7 +81,8 @@ struct Batch {
         if (_s != NGF_OK) return _s; \
     } while (0)
 
-static ngf_status fill_segments(DevArray<int>& first, const std::vector<int>& counts, cudaStream_t s) {
+static ngf_status fill_segments(DevArray<int>& first, DevArray<int>& pair_of, const std::vector<int>& counts,
+                                cudaStream_t s) {
     B_CU(first.alloc(counts.size() + 1, s), "allocate batch segments");
     first.h[0] = 0;
     for (size_t k = 0; k < counts.size(); ++k) {
@@ -88,6 +90,10 @@ static ngf_status fill_segments(DevArray<int>& first, const std::vector<int>& co
         first.h[k + 1] = first.h[k] + counts[k];
     }
     B_CU(first.upload(), "upload batch segments");
+    B_CU(pair_of.alloc(first.h.back(), s), "allocate batch segments");
+    for (size_t k = 0; k < counts.size(); ++k)
+        for (int b = first.h[k]; b < first.h[k + 1]; ++b) pair_of.h[b] = (int)k;
+    B_CU(pair_of.upload(), "upload batch segments");
     return NGF_OK;
 }
 
@@ -149,9 +155,9 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
         cv[k] = p->node_blocks;
         cd[k] = grid_for(3 * p->N, (int)(p->dpart_len / 2));
     }
-    B_TRY(fill_segments(b->first1, c1, stream));
-    B_TRY(fill_segments(b->firstv, cv, stream));
-    B_TRY(fill_segments(b->firstd, cd, stream));
+    B_TRY(fill_segments(b->first1, b->pair1, c1, stream));
+    B_TRY(fill_segments(b->firstv, b->pairv, cv, stream));
+    B_TRY(fill_segments(b->firstd, b->paird, cd, stream));
     B_CU(b->t_img.alloc(np, stream), "allocate batch tables");
     B_CU(b->t_lap.alloc(np, stream), "allocate batch tables");
     B_CU(b->t_comb.alloc(np, stream), "allocate batch tables");
@@ -177,7 +183,8 @@ static BatchQueue queue(const Batch& b, const DevArray<int4>& items, const ImgPa
 }
 
 static BatchSegs segs(const Batch& b, const DevArray<int>& first, const int* active) {
-    return BatchSegs{first.d, b.np, active};
+    const int* pair_of = (&first == &b.first1) ? b.pair1.d : ((&first == &b.firstv) ? b.pairv.d : b.paird.d);
+    return BatchSegs{first.d, pair_of, b.np, active};
 }
 
 // ---- launch sequences shared by the operator calls and the registration

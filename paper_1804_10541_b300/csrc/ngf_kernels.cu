@@ -1265,18 +1265,7 @@ __global__ void __launch_bounds__(NT, 1) k_batch_diag4(const BatchQueue Q) { bat
 template <class ARGS, class BODY>
 __device__ __forceinline__ void batch_nodal(const ARGS* table, const BatchSegs& S, BODY body) {
     __shared__ ARGS A;
-    __shared__ int pair;
-    if (threadIdx.x == 0) {  // largest k with first[k] <= blockIdx.x
-        int lo = 0, hi = S.npairs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) / 2;
-            if (S.first[mid] <= (int)blockIdx.x) lo = mid;
-            else hi = mid - 1;
-        }
-        pair = lo;
-    }
-    __syncthreads();
-    const int k = pair;
+    const int k = __ldg(S.pair_of + blockIdx.x);
     if (S.active && !S.active[k]) return;
     copy_to_shared(A, table + k);
     __syncthreads();

@@ -267,9 +267,10 @@ struct BatchQueue {
 };
 // Nodal kernels: pair k owns CTAs first[k] .. first[k+1]-1 of the launch.
 struct BatchSegs {
-    const int* first;   // npairs + 1 prefix
+    const int* first;    // npairs + 1 prefix
+    const int* pair_of;  // pair of each CTA of the launch
     int npairs;
-    const int* active;  // nullable
+    const int* active;   // nullable
 };
 __global__ void k_batch_image_obj(const BatchQueue Q);
 __global__ void k_batch_image_grad(const BatchQueue Q);
