@@ -328,10 +328,15 @@ void orc_objective(const orc_level* L, const double* R, const double* T, const d
     double* r = (double*)malloc(sizeof(double) * M);
     orc_P(L, u, uh);
     orc_warp(L, T, uh, Tw, dT);
-    orc_residual(L, R, Tw, r);
     double s = 0.0;
-    for (long i = 0; i < M; ++i) s += 1.0 - r[i] * r[i];
-    *D = hbar(L) * s; /* Eq. (NGF_discretized_ri), midpoint rule */
+    if (L->distance == ORC_DIST_SSD) { /* D = hbar/2 sum (T(x + Pu) - R)^2 */
+        for (long i = 0; i < M; ++i) s += (Tw[i] - R[i]) * (Tw[i] - R[i]);
+        *D = 0.5 * hbar(L) * s;
+    } else {
+        orc_residual(L, R, Tw, r);
+        for (long i = 0; i < M; ++i) s += 1.0 - r[i] * r[i];
+        *D = hbar(L) * s; /* Eq. (NGF_discretized_ri), midpoint rule */
+    }
     orc_curvature_apply(L, u, NULL, S);
     free(uh);
     free(Tw);
@@ -353,15 +358,22 @@ void orc_gradient(const orc_level* L, const double* R, const double* T, const do
     double* cg = (double*)malloc(sizeof(double) * 3 * N);
     orc_P(L, u, uh);
     orc_warp(L, T, uh, Tw, dT);
-    orc_residual(L, R, Tw, r);
-    orc_rho_hat(L, R, Tw, rh);
     double s = 0.0;
-    for (long i = 0; i < M; ++i) s += 1.0 - r[i] * r[i];
-    *D = hbar(L) * s;
-    /* (d psi / d r)^T = -2 hbar r, Eq. (dPsi) */
-    for (long i = 0; i < M; ++i) dpsi[i] = -2.0 * hbar(L) * r[i];
-    /* dr^T (d psi / d r)^T */
-    orc_drT(L, rh, dpsi, g);
+    if (L->distance == ORC_DIST_SSD) {
+        /* r = T(x + Pu) - R, d psi / d r = hbar r, dr = I */
+        for (long i = 0; i < M; ++i) s += (Tw[i] - R[i]) * (Tw[i] - R[i]);
+        *D = 0.5 * hbar(L) * s;
+        for (long i = 0; i < M; ++i) g[i] = hbar(L) * (Tw[i] - R[i]);
+    } else {
+        orc_residual(L, R, Tw, r);
+        orc_rho_hat(L, R, Tw, rh);
+        for (long i = 0; i < M; ++i) s += 1.0 - r[i] * r[i];
+        *D = hbar(L) * s;
+        /* (d psi / d r)^T = -2 hbar r, Eq. (dPsi) */
+        for (long i = 0; i < M; ++i) dpsi[i] = -2.0 * hbar(L) * r[i];
+        /* dr^T (d psi / d r)^T */
+        orc_drT(L, rh, dpsi, g);
+    }
     /* dT^T: the three diagonal blocks of Eq. (dT) */
     for (int d = 0; d < 3; ++d)
         for (long i = 0; i < M; ++i) gh[d * M + i] = dT[d * M + i] * g[i];
@@ -396,15 +408,21 @@ void orc_hessvec(const orc_level* L, const double* R, const double* T, const dou
     double* cq = (double*)malloc(sizeof(double) * 3 * N);
     orc_P(L, u, uh);
     orc_warp(L, T, uh, Tw, dT);
-    orc_rho_hat(L, R, Tw, rh);
     /* H p = 2 hbar P^T dT^T dr^T dr dT P p, Eq. (NGF_discretized_hessian);
-     * the sign is that of the PSD Gauss-Newton matrix (Sec. 3.2) */
+     * the sign is that of the PSD Gauss-Newton matrix (Sec. 3.2).
+     * SSD: H p = hbar P^T dT^T dT P p (dr = I, psi'' = hbar) */
     orc_P(L, p, ph);
     for (long i = 0; i < M; ++i) sv[i] = dT[i] * ph[i] + dT[M + i] * ph[M + i] + dT[2 * M + i] * ph[2 * M + i];
-    orc_dr(L, rh, sv, v);
-    orc_drT(L, rh, v, t);
-    for (int d = 0; d < 3; ++d)
-        for (long i = 0; i < M; ++i) qh[d * M + i] = 2.0 * hbar(L) * dT[d * M + i] * t[i];
+    if (L->distance == ORC_DIST_SSD) {
+        for (int d = 0; d < 3; ++d)
+            for (long i = 0; i < M; ++i) qh[d * M + i] = hbar(L) * dT[d * M + i] * sv[i];
+    } else {
+        orc_rho_hat(L, R, Tw, rh);
+        orc_dr(L, rh, sv, v);
+        orc_drT(L, rh, v, t);
+        for (int d = 0; d < 3; ++d)
+            for (long i = 0; i < M; ++i) qh[d * M + i] = 2.0 * hbar(L) * dT[d * M + i] * t[i];
+    }
     orc_PT(L, qh, q);
     /* + alpha grad^2 S p, Eq. (curv_hessMult) */
     orc_curvature_apply(L, p, cq, NULL);
@@ -437,10 +455,11 @@ void orc_gn_diagonal(const orc_level* L, const double* R, const double* T, const
     double* rh = (double*)malloc(sizeof(double) * 7 * M);
     orc_P(L, u, uh);
     orc_warp(L, T, uh, Tw, dT);
-    orc_rho_hat(L, R, Tw, rh);
     memset(diag, 0, sizeof(double) * 3 * N);
     long ent_n[56];
     double ent_v[56];
+    const int ssd = L->distance == ORC_DIST_SSD;
+    if (!ssd) orc_rho_hat(L, R, Tw, rh);
     for (int z = 0; z < m2; ++z)
         for (int y = 0; y < m1; ++y)
             for (int x = 0; x < m0; ++x) {
@@ -448,9 +467,11 @@ void orc_gn_diagonal(const orc_level* L, const double* R, const double* T, const
                 for (int d = 0; d < 3; ++d) {
                     int cnt = 0;
                     for (int k = 0; k < 7; ++k) {
+                        /* SSD: the row of dr is the unit row (only k = 0, coefficient 1) */
+                        if (ssd && k != 3) continue;
                         long j = nb(L, x, y, z, k);
                         long jx = j % m0, jy = (j / m0) % m1, jz = j / ((long)m0 * m1);
-                        double c = rh[7 * i + k] * dT[d * M + j];
+                        double c = (ssd ? 1.0 : rh[7 * i + k]) * dT[d * M + j];
                         long fx, fy, fz;
                         double wx, wy, wz;
                         pw((int)jx, m0, L->n[0], &fx, &wx);
@@ -467,7 +488,8 @@ void orc_gn_diagonal(const orc_level* L, const double* R, const double* T, const
                                     ent_v[e] += c * w;
                                 }
                     }
-                    for (int e = 0; e < cnt; ++e) diag[d * N + ent_n[e]] += 2.0 * hbar(L) * ent_v[e] * ent_v[e];
+                    for (int e = 0; e < cnt; ++e)
+                        diag[d * N + ent_n[e]] += (ssd ? 1.0 : 2.0) * hbar(L) * ent_v[e] * ent_v[e];
                 }
             }
     /* curvature: squared entries of each Laplacian row, summed by column */

@@ -32,7 +32,11 @@ typedef struct {
     double  alpha;  /* curvature weight                             */
     double  tau;    /* NGF edge parameter of the template           */
     double  rho;    /* NGF edge parameter of the reference          */
+    int32_t distance; /* ORC_DIST_NGF, or ORC_DIST_SSD: the sum of
+                         squared differences, whose residual Jacobian
+                         is the identity (Sec. 7); tau, rho unused    */
 } orc_level;
+enum { ORC_DIST_NGF = 0, ORC_DIST_SSD = 1 };
 
 /* ---- building blocks (each cites the passage it evaluates) ------------ */
 

@@ -17,9 +17,12 @@ if HERE not in sys.path:
 import build as _build  # noqa: E402
 
 
+DIST_NGF, DIST_SSD = 0, 1
+
+
 class Level(C.Structure):
     _fields_ = [("m", C.c_int32 * 3), ("h", C.c_double * 3), ("n", C.c_int32 * 3),
-                ("alpha", C.c_double), ("tau", C.c_double), ("rho", C.c_double)]
+                ("alpha", C.c_double), ("tau", C.c_double), ("rho", C.c_double), ("distance", C.c_int32)]
 
 
 class PcgInfo(C.Structure):
@@ -53,8 +56,9 @@ def lib():
     return _lib
 
 
-def level(m, h, n, alpha=1.0, tau=0.1, rho=0.1):
+def level(m, h, n, alpha=1.0, tau=0.1, rho=0.1, distance=DIST_NGF):
     L = Level()
+    L.distance = int(distance)
     for a in range(3):
         L.m[a] = int(m[a])
         L.h[a] = float(h[a])

@@ -578,3 +578,52 @@ def test_lbfgs_level_monotone_armijo_and_default_gamma(orc):
     # every accepted step satisfied the Armijo condition: J decreased
     etas = trace[1:2 * rep.gn_done:2]
     assert np.all(etas > 0)
+
+
+# ---- SSD distance (Sec. 7: dr = I) ------------------------------------------
+
+def _ssd_assembled(m, h, n, alpha, R, T, u):
+    """SSD objective, gradient and Gauss-Newton matrix from the independent
+    dense factors: D = hbar/2 ||Tw - R||^2, grad = hbar (dT P)^T (Tw - R),
+    H = hbar (dT P)^T (dT P) (+ alpha grad^2 S)."""
+    As = A.Assembled(m, h, n, alpha, 0.1, 0.1, R, T, u)
+    r = As.Tw - np.asarray(R, float)
+    Jc = As.dT @ As.P
+    D = 0.5 * As.hbar * np.sum(r ** 2)
+    g = As.hbar * (r @ Jc) + alpha * 2.0 * As.hbary * (As.Lap.T @ (As.Lap @ As.u))
+    H = As.hbar * Jc.T @ Jc + alpha * 2.0 * As.hbary * As.Lap.T @ As.Lap
+    return D, g, H
+
+
+@pytest.mark.parametrize("m,h,n", TINY)
+def test_ssd_operators_match_assembled(orc, m, h, n):
+    L = orc.level(m, h, n, alpha=0.7, distance=orc.DIST_SSD)
+    R, T, u, p = _inputs(m, n, 21)
+    D_ref, g_ref, H = _ssd_assembled(m, h, n, 0.7, R, T, u)
+    g, D, S = orc.gradient(L, R, T, u)
+    D2, _ = orc.objective(L, R, T, u)
+    assert abs(D - D_ref) < 1e-12 * abs(D_ref) and D2 == D
+    np.testing.assert_allclose(g, g_ref, rtol=0, atol=1e-9 * np.max(np.abs(g_ref)))
+    q = orc.hessvec(L, R, T, u, p)
+    np.testing.assert_allclose(q, H @ p, rtol=0, atol=1e-9 * np.max(np.abs(H @ p)))
+    np.testing.assert_allclose(orc.gn_diagonal(L, R, T, u), np.diag(H), rtol=1e-9,
+                               atol=1e-12 * np.max(np.diag(H)))
+
+
+def test_ssd_gradient_finite_differences_and_identity(orc):
+    m, h, n = (7, 6, 5), (1.0, 0.9, 1.3), (4, 4, 3)
+    L = orc.level(m, h, n, alpha=0.3, distance=orc.DIST_SSD)
+    R, T, u, _ = _inputs(m, n, 22)
+    g, _, _ = orc.gradient(L, R, T, u)
+    rng = np.random.default_rng(23)
+    J = lambda v: (lambda DS: DS[0] + 0.3 * DS[1])(orc.objective(L, R, T, v))
+    for _ in range(10):
+        dvec = rng.standard_normal(u.size)
+        eps = 1e-6
+        fd = (J(u + eps * dvec) - J(u - eps * dvec)) / (2 * eps)
+        assert abs(fd - g @ dvec) < 1e-6 * (abs(fd) + np.abs(g).max())
+    # identical images, identity warp: D = 0 and grad D = 0
+    L0 = orc.level(m, h, n, alpha=0.0, distance=orc.DIST_SSD)
+    z = np.zeros_like(u)
+    g0, D0, _ = orc.gradient(L0, R, R, z)
+    assert D0 == 0.0 and np.abs(g0).max() == 0.0
