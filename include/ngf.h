@@ -70,7 +70,11 @@ typedef struct {
     double  alpha;  /* curvature weight, >= 0 (Eq. discreteenergy)               */
     double  tau;    /* NGF edge parameter of the template, > 0 (Eq. ngf)         */
     double  rho;    /* NGF edge parameter of the reference, > 0 (Eq. ngf)        */
+    int32_t distance; /* NGF_DIST_NGF (0, the paper's distance) or NGF_DIST_SSD:
+                         D = hbar/2 sum (T(x + Pu) - R)^2, whose residual
+                         Jacobian is the identity (Sec. 7); tau, rho unused  */
 } ngf_level_desc;
+enum { NGF_DIST_NGF = 0, NGF_DIST_SSD = 1 };
 
 typedef struct ngf_plan ngf_plan;
 

@@ -80,7 +80,12 @@ ngf_status validate_desc(const ngf_level_desc* d, std::string& why) {
             return NGF_EINVAL;
         }
     }
-    if (!(d->tau > 0.0) || !(d->rho > 0.0) || !std::isfinite(d->tau) || !std::isfinite(d->rho)) {
+    if (d->distance != NGF_DIST_NGF && d->distance != NGF_DIST_SSD) {
+        why = "distance must be NGF_DIST_NGF or NGF_DIST_SSD";
+        return NGF_EINVAL;
+    }
+    if (d->distance == NGF_DIST_NGF &&
+        (!(d->tau > 0.0) || !(d->rho > 0.0) || !std::isfinite(d->tau) || !std::isfinite(d->rho))) {
         why = "NGF parameters tau and rho must be finite and > 0";
         return NGF_EINVAL;
     }
@@ -356,6 +361,9 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     NGF_CU(p, cudaFuncSetAttribute(k_image_obj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_image_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_image_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
+    for (auto kern : {k_ssd_obj, k_ssd_grad, k_ssd_hess, k_ssd_diag})
+        NGF_CU(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)),
+               "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
     return NGF_OK;
@@ -454,10 +462,13 @@ CombineParams combine_params(const Plan* p, const Geometry& g, float* out, const
 
 static dim3 img_grid(const Geometry& g) { return dim3(g.ntx, g.nty, g.ntz); }
 
+static bool ssd(const Plan* p) { return p->desc.distance == NGF_DIST_SSD; }
+
 ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* u, double* dD, double* dS) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_OBJ, p->g0, dD);
     NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
-    NGF_CU(p, launch(k_image_obj, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_obj");
+    NGF_CU(p, launch(ssd(p) ? k_ssd_obj : k_image_obj, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P),
+           "k_image_obj");
     NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
     NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
                      p->dcount, dS, p->hbary),
@@ -469,7 +480,8 @@ ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u
                          double* dS) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_GRAD, p->g0, dD);
     NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
-    NGF_CU(p, launch(k_image_grad, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_grad");
+    NGF_CU(p, launch(ssd(p) ? k_ssd_grad : k_image_grad, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P),
+           "k_image_grad");
     NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
     NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
                      p->dcount, dS, p->hbary),
@@ -486,7 +498,8 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
            "k_lap");
     ImgParams P = img_params(p, R, T, u, pv, MODE_HESS, p->g0, nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
-    NGF_CU(p, launch(k_image_hess, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_image_hess");
+    NGF_CU(p, launch(ssd(p) ? k_ssd_hess : k_image_hess, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P),
+           "k_image_hess");
     NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g0, q, p->L, nullptr, dotw, dout);
     NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
@@ -494,6 +507,15 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
 }
 
 ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u, float* diag) {
+    if (ssd(p)) {  // no neighbour coupling: the halo-0 geometry
+        ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g0, nullptr);
+        NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
+        NGF_CU(p, launch(k_ssd_diag, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_ssd_diag");
+        NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
+        CombineParams C = combine_params(p, p->g0, diag, nullptr, p->ctab, nullptr, nullptr);
+        NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
+        return NGF_OK;
+    }
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g1, nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     NGF_CU(p, launch(p->diag_span3 ? k_diag : k_diag4, img_grid(p->g1), dim3(NT), sizeof(DiagSmem), p->stream, P),

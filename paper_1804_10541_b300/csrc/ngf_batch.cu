@@ -127,6 +127,9 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int k = 0; k < np; ++k)
+        if (descs[k].distance != NGF_DIST_NGF)
+            return set_error(nullptr, NGF_EINVAL, "the batched form evaluates the NGF distance only");
     for (int k = 0; k < np; ++k) {
         ngf_plan* pl = nullptr;
         const ngf_status s = plan_create(&pl, &descs[k], stream, zc);

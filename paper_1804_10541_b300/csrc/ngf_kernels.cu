@@ -501,6 +501,225 @@ __global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) {
 }
 
 // ---------------------------------------------------------------------------
+// SSD distance (Sec. 7): r = T(x + P u) - R with the identity as residual
+// Jacobian, D = hbar/2 sum r^2, grad D = hbar P^T dT^T r, H = hbar P^T dT^T dT P.
+// No neighbour of a voxel is needed, so the march has no halo: per plane,
+// interval 1 warps the own columns (q_hat to shared memory) and adds the
+// previous plane's x-reduced q_hat into the node planes (B), interval 2
+// x-reduces this plane's q_hat (A) and z-interpolates the next node plane.
+// MODE_SSD_DIAG forms hbar dT_d^2 and reduces it with squared weights, the
+// diagonal of hbar (dT P)^T (dT P).
+// ---------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, int bz_) {
+    NGF_DYNAMIC_SMEM(smraw);
+    ImgSmem& S = *reinterpret_cast<ImgSmem*>(smraw);
+    constexpr bool OBJ = (MODE == MODE_OBJ), HESS = (MODE == MODE_HESS), DIAG = (MODE == MODE_SSD_DIAG);
+    constexpr int NVEC = HESS ? 6 : 3;
+    const int tid = threadIdx.x;
+    const int xs = bx_ * TX, ys = by_ * TY;
+    const int z0 = bz_ * P.zc, z1 = min(P.m2, z0 + P.zc);
+    const int txe = min(TX, P.m0 - xs), tye = min(TY, P.m1 - ys);
+    // node box of the owned columns: z-interpolated planes and tile partials
+    const int BX0 = P.fx[xs], BY0 = P.fy[ys], BZ0 = P.fz[z0];
+    const int nbx = P.fx[xs + txe - 1] + 1 - BX0 + 1;
+    const int nby = P.fy[ys + tye - 1] + 1 - BY0 + 1;
+    const long long tile = ((long long)bz_ * P.nty + by_) * P.ntx + bx_;
+
+    for (int i = tid; i < TX; i += NT) {
+        const int gx = min(xs + i, P.m0 - 1);
+        S.fxb[i] = P.fx[gx] - BX0;
+        S.wx2[i] = P.wx[gx];
+    }
+    for (int i = tid; i < TY; i += NT) {
+        const int gy = min(ys + i, P.m1 - 1);
+        S.fyb[i] = P.fy[gy] - BY0;
+        S.wy2[i] = P.wy[gy];
+    }
+    if (!OBJ) {
+        for (int b = tid; b < nbx; b += NT) {
+            int lo = TX, hi = -1;
+            for (int lx = 0; lx < txe; ++lx) {
+                const int f = P.fx[xs + lx] - BX0;
+                if (f == b || f == b - 1) { lo = min(lo, lx); hi = max(hi, lx); }
+            }
+            S.xr_lo[b] = lo;
+            S.xr_hi[b] = hi;
+        }
+        for (int b = tid; b < nby; b += NT) {
+            int lo = TY, hi = -1;
+            for (int ly = 0; ly < tye; ++ly) {
+                const int f = P.fy[ys + ly] - BY0;
+                if (f == b || f == b - 1) { lo = min(lo, ly); hi = max(hi, ly); }
+            }
+            S.yr_lo[b] = lo;
+            S.yr_hi[b] = hi;
+        }
+        for (int i = tid; i < 2 * 3 * NBY * NBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
+    }
+    const int lx0 = tid % TX, ly0 = tid / TX;
+    const int gx0 = xs + lx0, gy0 = ys + ly0;
+    const bool own_ok = (lx0 < txe) && (ly0 < tye);
+    const int box = nbx * nby;
+    int s0_g[2], s0_s[2], a_it[2], b_it[2];
+    for (int k = 0; k < 2; ++k) {
+        const int i = tid + k * NT;
+        if (i < box) {
+            const int by = i / nbx, bx = i - by * nbx;
+            s0_g[k] = (BX0 + bx) + P.n0 * (BY0 + by);
+            s0_s[k] = by * UBX + bx;
+        } else {
+            s0_g[k] = 0;
+            s0_s[k] = -1;
+        }
+        a_it[k] = (!OBJ && i < TY * nbx) ? ((i / nbx) << 6) + (i % nbx) : -1;
+        b_it[k] = (!OBJ && i < nby * nbx) ? ((i / nbx) << 6) + (i % nbx) : -1;
+    }
+    const int plane_n = P.n0 * P.n1;
+    const float hb = (float)P.hbar;
+    double dacc = 0.0;
+    int cur = BZ0;
+
+    auto stage0 = [&](int zf) {
+        const int fzz = P.fz[zf];
+        const float wzz = P.wz[zf];
+        const int pl0 = fzz * plane_n;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (s0_s[k] < 0) continue;
+            const int o = pl0 + s0_g[k];
+#pragma unroll
+            for (int c = 0; c < NVEC; ++c) {
+                const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
+                const float a = __ldg(src + o), b = __ldg(src + o + plane_n);
+                (&S.Uz[c][0][0])[s0_s[k]] = fmaf(wzz, b - a, a);
+            }
+        }
+    };
+    auto store_plane = [&](int pl) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (b_it[k] < 0) continue;
+            const int by = b_it[k] >> 6, bx = b_it[k] & 63;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float& a = S.Acc[pl & 1][c][by][bx];
+                P.partial[((tile * 3 + c) * P.pbz + (pl - BZ0)) * (long long)(P.pby * P.pbx) + by * P.pbx + bx] = a;
+                a = 0.f;
+            }
+        }
+    };
+    auto wsel = [](float w, bool upper) {  // trilinear weight, squared for the diagonal
+        const float v = upper ? w : 1.f - w;
+        return DIAG ? v * v : v;
+    };
+
+    stage0(z0);
+    __syncthreads();
+    for (int zf = z0; zf <= z1; ++zf) {
+        // ============ interval 1: warp the own columns of plane zf; B(zf - 1)
+        if (zf < z1) {
+            float4 qv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (own_ok) {
+                const int ax = S.fxb[lx0], ay = S.fyb[ly0];
+                const float wxv = S.wx2[lx0], wyv = S.wy2[ly0];
+                float uh[NVEC];
+#pragma unroll
+                for (int c = 0; c < NVEC; ++c) {
+                    const float v00 = S.Uz[c][ay][ax], v10 = S.Uz[c][ay][ax + 1];
+                    const float v01 = S.Uz[c][ay + 1][ax], v11 = S.Uz[c][ay + 1][ax + 1];
+                    const float a0 = fmaf(wxv, v10 - v00, v00), a1 = fmaf(wxv, v11 - v01, v01);
+                    uh[c] = fmaf(wyv, a1 - a0, a0);
+                }
+                float g0, g1, g2;
+                const float tw = warp_sample(P, gx0, gy0, zf, uh[0] * P.ih[0], uh[1] * P.ih[1], uh[2] * P.ih[2], g0,
+                                             g1, g2);
+                const float r = tw - __ldg(P.R + (gx0 + P.m0 * (gy0 + P.m1 * zf)));
+                if (OBJ) {
+                    dacc += (double)(r * r);
+                } else if (DIAG) {
+                    qv = make_float4(hb * g0 * g0, hb * g1 * g1, hb * g2 * g2, 0.f);
+                } else {
+                    const float w = HESS ? hb * fmaf(g0, uh[3], fmaf(g1, uh[4], g2 * uh[5])) : hb * r;
+                    qv = make_float4(g0 * w, g1 * w, g2 * w, 0.f);
+                }
+            }
+            if (!OBJ) *reinterpret_cast<float4*>(S.Q4[tid]) = qv;
+        }
+        const int za = zf - 1;
+        if (!OBJ && za >= z0) {  // B: y-reduction and z accumulation of plane za
+            const int fzo = P.fz[za];
+            const float wzo = P.wz[za];
+            if (fzo > cur) {
+                store_plane(cur);
+                cur = fzo;
+            }
+            const float wlo = wsel(wzo, false), whi = wsel(wzo, true);
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (b_it[k] < 0) continue;
+                const int by = b_it[k] >> 6, bx = b_it[k] & 63;
+                float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+                for (int ly = S.yr_lo[by]; ly <= S.yr_hi[by]; ++ly) {
+                    const float wy = wsel(S.wy2[ly], S.fyb[ly] != by);
+                    const float4 q = *reinterpret_cast<const float4*>(S.Qx4[ly][bx]);
+                    q0 = fmaf(wy, q.x, q0);
+                    q1 = fmaf(wy, q.y, q1);
+                    q2 = fmaf(wy, q.z, q2);
+                }
+                const int lo = cur & 1, hi = (cur + 1) & 1;
+                S.Acc[lo][0][by][bx] = fmaf(wlo, q0, S.Acc[lo][0][by][bx]);
+                S.Acc[lo][1][by][bx] = fmaf(wlo, q1, S.Acc[lo][1][by][bx]);
+                S.Acc[lo][2][by][bx] = fmaf(wlo, q2, S.Acc[lo][2][by][bx]);
+                S.Acc[hi][0][by][bx] = fmaf(whi, q0, S.Acc[hi][0][by][bx]);
+                S.Acc[hi][1][by][bx] = fmaf(whi, q1, S.Acc[hi][1][by][bx]);
+                S.Acc[hi][2][by][bx] = fmaf(whi, q2, S.Acc[hi][2][by][bx]);
+            }
+        }
+        __syncthreads();
+        // ============ interval 2: A(zf), next node plane
+        if (!OBJ && zf < z1) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                if (a_it[k] < 0) continue;
+                const int ly = a_it[k] >> 6, bx = a_it[k] & 63;
+                float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int lx = S.xr_lo[bx]; lx <= S.xr_hi[bx]; ++lx) {
+                    const float wx = wsel(S.wx2[lx], S.fxb[lx] != bx);
+                    const float4 q = *reinterpret_cast<const float4*>(S.Q4[ly * TX + lx]);
+                    r4.x = fmaf(wx, q.x, r4.x);
+                    r4.y = fmaf(wx, q.y, r4.y);
+                    r4.z = fmaf(wx, q.z, r4.z);
+                }
+                *reinterpret_cast<float4*>(S.Qx4[ly][bx]) = r4;
+            }
+        }
+        if (zf + 1 < z1) stage0(zf + 1);
+        __syncthreads();
+    }
+    if (!OBJ) {
+        store_plane(cur);
+        store_plane(cur + 1);
+    } else {
+        const double bs = block_sum(dacc, S.red);
+        grid_sum_finish(bs, P.dpart, P.dcount, P.dout, 0.5 * P.hbar, S.red, P.ntx * P.nty * P.ntz, (int)tile);
+    }
+}
+
+__global__ void __launch_bounds__(NT, 2) k_ssd_obj(const ImgParams P) {
+    ssd_pass<MODE_OBJ>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_ssd_grad(const ImgParams P) {
+    ssd_pass<MODE_GRAD>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_ssd_hess(const ImgParams P) {
+    ssd_pass<MODE_HESS>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_ssd_diag(const ImgParams P) {
+    ssd_pass<MODE_SSD_DIAG>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// ---------------------------------------------------------------------------
 // Exact Jacobi diagonal of the Gauss-Newton matrix (without the curvature
 // part): diag_{d,n} = 2 hbar sum_i J_{i,(d,n)}^2, J = dr dT P, row i formed
 // from the 7 entries of row i of dr (Eq. dr) and the trilinear weights of each

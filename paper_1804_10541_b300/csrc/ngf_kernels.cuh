@@ -222,6 +222,13 @@ __global__ void k_image_grad(const ImgParams P);  // D and gradient tile partial
 __global__ void k_image_hess(const ImgParams P);  // Hessian-vector tile partials
 __global__ void k_diag(const ImgParams P);        // Jacobi-diagonal tile partials (>= 2 voxels per cell)
 __global__ void k_diag4(const ImgParams P);       // same, any voxels-per-cell ratio
+// SSD distance (identity residual Jacobian): D, gradient, Hessian-vector and
+// diagonal tile partials on the halo-0 geometry
+constexpr int MODE_SSD_DIAG = 3;
+__global__ void k_ssd_obj(const ImgParams P);
+__global__ void k_ssd_grad(const ImgParams P);
+__global__ void k_ssd_hess(const ImgParams P);
+__global__ void k_ssd_diag(const ImgParams P);
 __global__ void k_lap(NodeGeom G, const float* __restrict__ x, float* __restrict__ L, double* part,
                       unsigned int* count, double* out, double scale);
 __global__ void k_node_combine(const CombineParams P);

@@ -147,6 +147,8 @@ extern "C" ngf_status ngf_objective_noalloc(const ngf_level_desc* d, const float
     long long nchunk = (2LL * sms + txy / 2) / txy;
     nchunk = std::max<long long>(1, std::min<long long>(nchunk, d->m[2]));
     const int zc = (int)std::max<long long>(std::min<long long>(8, d->m[2]), (d->m[2] + nchunk - 1) / nchunk);
+    if (d->distance != NGF_DIST_NGF)
+        return set_error(nullptr, NGF_EINVAL, "ngf_objective_noalloc evaluates the NGF distance only");
     const dim3 grid((d->m[0] + TX - 1) / TX, (d->m[1] + TY - 1) / TY, (d->m[2] + zc - 1) / zc);
     const long long img_blocks = (long long)grid.x * grid.y * grid.z;
     const long long N = (long long)d->n[0] * d->n[1] * d->n[2];

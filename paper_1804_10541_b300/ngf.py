@@ -29,9 +29,12 @@ EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_la
 NGF_METHOD_GN, NGF_METHOD_LBFGS = 0, 1
 
 
+NGF_DIST_NGF, NGF_DIST_SSD = 0, 1
+
+
 class LevelDesc(C.Structure):
     _fields_ = [("m", C.c_int32 * 3), ("h", C.c_double * 3), ("n", C.c_int32 * 3),
-                ("alpha", C.c_double), ("tau", C.c_double), ("rho", C.c_double)]
+                ("alpha", C.c_double), ("tau", C.c_double), ("rho", C.c_double), ("distance", C.c_int32)]
 
 
 class PcgState(C.Structure):
@@ -144,8 +147,9 @@ def _stream(s):
     return s.cuda_stream
 
 
-def level_desc(m, h, n, alpha=1.0, tau=0.1, rho=0.1):
+def level_desc(m, h, n, alpha=1.0, tau=0.1, rho=0.1, distance=NGF_DIST_NGF):
     d = LevelDesc()
+    d.distance = int(distance)
     for a in range(3):
         d.m[a], d.h[a], d.n[a] = int(m[a]), float(h[a]), int(n[a])
     d.alpha, d.tau, d.rho = float(alpha), float(tau), float(rho)
