@@ -32,11 +32,27 @@ def test_every_declared_symbol_is_exported(ngf):
     assert sorted(ngf.EXPORTS) == decl
 
 
-def test_struct_layouts_match_header(ngf):
-    # sizes implied by the header's field order on x86-64
-    assert C.sizeof(ngf.LevelDesc) == 12 + 4 + 24 + 12 + 4 + 24
-    assert C.sizeof(ngf.PcgState) == 8 * 8
-    assert C.sizeof(ngf.Report) == 24 + 20 + 4 + 8 + 8
+def test_struct_layouts_match_header(ngf, tmp_path):
+    """The ctypes mirrors have the size and field offsets the C compiler gives
+    the header's structs."""
+    import subprocess
+    structs = {"ngf_level_desc": ngf.LevelDesc, "ngf_pcg_state": ngf.PcgState, "ngf_options": ngf.Options,
+               "ngf_report": ngf.Report, "ngf_pcg_info": ngf.PcgInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ngf.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, py in structs.items():
+        assert int(out[cname]) == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert int(out[f"{cname}.{fname}"]) == getattr(py, fname).offset, (cname, fname)
 
 
 @pytest.mark.parametrize("m,n,tau,rho,alpha,what", [
