@@ -515,6 +515,7 @@ __device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, i
     NGF_DYNAMIC_SMEM(smraw);
     ImgSmem& S = *reinterpret_cast<ImgSmem*>(smraw);
     constexpr bool OBJ = (MODE == MODE_OBJ), HESS = (MODE == MODE_HESS), DIAG = (MODE == MODE_SSD_DIAG);
+    constexpr bool WANT_D = (MODE == MODE_OBJ || MODE == MODE_GRAD);  // the gradient pass also returns D
     constexpr int NVEC = HESS ? 6 : 3;
     const int tid = threadIdx.x;
     const int xs = bx_ * TX, ys = by_ * TY;
@@ -635,8 +636,8 @@ __device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, i
                 const float tw = warp_sample(P, gx0, gy0, zf, uh[0] * P.ih[0], uh[1] * P.ih[1], uh[2] * P.ih[2], g0,
                                              g1, g2);
                 const float r = tw - __ldg(P.R + (gx0 + P.m0 * (gy0 + P.m1 * zf)));
+                if (WANT_D) dacc += (double)(r * r);
                 if (OBJ) {
-                    dacc += (double)(r * r);
                 } else if (DIAG) {
                     qv = make_float4(hb * g0 * g0, hb * g1 * g1, hb * g2 * g2, 0.f);
                 } else {
@@ -700,7 +701,8 @@ __device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, i
     if (!OBJ) {
         store_plane(cur);
         store_plane(cur + 1);
-    } else {
+    }
+    if (WANT_D) {
         const double bs = block_sum(dacc, S.red);
         grid_sum_finish(bs, P.dpart, P.dcount, P.dout, 0.5 * P.hbar, S.red, P.ntx * P.nty * P.ntz, (int)tile);
     }

@@ -44,12 +44,13 @@ def test_ssd_operators_match_oracle(ngf, m, h, n):
     with ngf.Plan(c.desc) as pl:
         D, S = ngf.ngf_objective(pl.handle, c.R, c.T, c.u)
         g, q, dg = c.empty(), c.empty(), c.empty()
-        ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g, want_scalars=False)
+        Dg, Sg = ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g)
         ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q)
         ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, dg)
         torch.cuda.synchronize()
     Do, So = O.objective(c.L, c.Rh, c.Th, c.uh)
     assert abs(D - Do) <= G.TOL_OBJ * abs(Do) and abs(S - So) <= G.TOL_OBJ * max(abs(So), 1e-300)
+    assert abs(Dg - Do) <= G.TOL_OBJ * abs(Do) and Sg == S  # the gradient call returns D and S too
     go, _, _ = O.gradient(c.L, c.Rh, c.Th, c.uh)
     assert G.rel(G.f64(g), go) < G.TOL_GRAD
     assert G.rel(G.f64(q), O.hessvec(c.L, c.Rh, c.Th, c.uh, c.ph)) < G.TOL_HESS
