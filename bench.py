@@ -386,7 +386,8 @@ def run_kernel_case(args):
     R, T, _, w = synth.make(args.kernel_case, device="cuda")
     m, h, n = w["m"], w["h"], w["n"]
     N = n[0] * n[1] * n[2]
-    desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"])
+    dist = ngf.NGF_DIST_SSD if args.distance == "ssd" else ngf.NGF_DIST_NGF
+    desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"], distance=dist)
     u, p = synth.random_fields(N, 5, amp=0.5 * min(h), device="cuda")
     q = torch.empty(3 * N, device="cuda")
     g = torch.empty(3 * N, device="cuda")
@@ -407,7 +408,7 @@ def run_kernel_case(args):
             torch.cuda.synchronize()
             times[name] = e0.elapsed_time(e1) / args.calls
     M = m[0] * m[1] * m[2]
-    print(json.dumps({"kernel_case": args.kernel_case, "calls": args.calls,
+    print(json.dumps({"kernel_case": args.kernel_case, "distance": args.distance, "calls": args.calls,
                       "ms": times, "hessvec_gvoxel_s": M / times["hessvec"] / 1e6}), flush=True)
     return 0
 
@@ -561,6 +562,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", default=None, help="profile driver: gn_hessvec only on this workload")
     ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--distance", default="ngf", choices=["ngf", "ssd"], help="distance of --kernel-case")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_64", "thorax_abd"],
                     help="batch_64: the batched form on 64 uneven pairs; thorax_abd: the 512x512x900 "
                          "registration (each its own JSON line)")
