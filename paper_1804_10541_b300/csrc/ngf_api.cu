@@ -280,14 +280,25 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     p->hbar = d->h[0] * d->h[1] * d->h[2];
     p->hbary = p->hy[0] * p->hy[1] * p->hy[2];
 
-    // z-chunking: about two CTAs per SM, at least 8 planes per chunk
+    // z-chunking: k chunks per column of tiles, chosen to minimise
+    // (rounds of 2 CTAs per SM) x (planes marched per chunk, 5 of them fill
+    // and drain), with at least 8 planes per chunk
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long txy = (long long)((p->m[0] + TX - 1) / TX) * ((p->m[1] + TY - 1) / TY);
-    long long nchunk = (2LL * sms + txy / 2) / txy;
-    nchunk = std::max<long long>(1, std::min<long long>(nchunk, p->m[2]));
-    p->zc = (int)std::max<long long>(std::min<long long>(8, p->m[2]), (p->m[2] + nchunk - 1) / nchunk);
+    const long long slots = 2LL * sms;
+    long long best_k = 1, best_cost = LLONG_MAX;
+    for (long long k = 1; k <= std::max<long long>(1, std::min<long long>(p->m[2] / 8, 256)); ++k) {
+        const long long zc = (p->m[2] + k - 1) / k;
+        const long long chunks = (p->m[2] + zc - 1) / zc;
+        const long long cost = ((txy * chunks + slots - 1) / slots) * (zc + 5);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best_k = k;
+        }
+    }
+    p->zc = (int)std::max<long long>(std::min<long long>(8, p->m[2]), (p->m[2] + best_k - 1) / best_k);
     if (zc_req > 0) p->zc = std::min(zc_req, p->m[2]);
 
     std::vector<int> f[3];
