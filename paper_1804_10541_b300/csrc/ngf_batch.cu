@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <memory>
 #include <cmath>
 #include <new>
 #include <string>
@@ -43,6 +44,13 @@ struct DevArray {
     }
 };
 
+// pairs [p0, p1) of one batched image-pass launch (at most BATCH_TAB) and
+// their work items
+struct PairRange {
+    int p0 = 0, p1 = 0;
+    DevArray<int4> items0, items3, items4;  // image tiles (halo 0); diagonal tiles (halo 1) by span
+};
+
 struct Batch {
     int np = 0;
     int zc = 0;
@@ -50,7 +58,7 @@ struct Batch {
     cudaStream_t stream = nullptr;
     std::vector<ngf_level_desc> descs;
     std::vector<ngf_plan*> plans;
-    DevArray<int4> items0, items3, items4;  // image tiles (halo 0); diagonal tiles (halo 1) by span
+    std::vector<std::unique_ptr<PairRange>> ranges;
     DevArray<unsigned int> qctr;             // queue head, finished CTAs
     DevArray<int> first1, firstv, firstd;    // block ranges: per node, per vector element, dot
     DevArray<int> pair1, pairv, paird;       // pair of every block of those launches
@@ -67,7 +75,6 @@ struct Batch {
         plans.clear();
     }
     Plan* plan(int k) const { return &plans[k]->impl; }
-    int img_grid() const { return std::max(1, std::min((int)items0.h.size(), 2 * sms)); }
 };
 
 #define B_CU(expr, what)                                             \
@@ -99,9 +106,9 @@ static ngf_status fill_segments(DevArray<int>& first, DevArray<int>& pair_of, co
 
 // (pair, tile) items of one geometry, by decreasing voxel count (the queue
 // hands them out in this order, so the largest start first)
-static void tile_items(const Batch& b, bool halo1, int want_span3, std::vector<int4>& out) {
+static void tile_items(const Batch& b, int p0, int p1, bool halo1, int want_span3, std::vector<int4>& out) {
     std::vector<std::pair<long long, int4>> it;
-    for (int k = 0; k < b.np; ++k) {
+    for (int k = p0; k < p1; ++k) {
         const Plan* p = b.plan(k);
         if (want_span3 >= 0 && (int)p->diag_span3 != want_span3) continue;
         const Geometry& g = halo1 ? p->g1 : p->g0;
@@ -136,19 +143,22 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
         if (s != NGF_OK) return set_error(nullptr, s, "pair " + std::to_string(k) + ": " + ngf_last_error(nullptr));
         b->plans.push_back(pl);
     }
-    std::vector<int4> v;
-    tile_items(*b, false, -1, v);
-    B_CU(b->items0.alloc(v.size(), stream), "allocate batch items");
-    b->items0.h = v;
-    B_CU(b->items0.upload(), "upload batch items");
-    tile_items(*b, true, 1, v);
-    B_CU(b->items3.alloc(v.size(), stream), "allocate batch items");
-    b->items3.h = v;
-    B_CU(b->items3.upload(), "upload batch items");
-    tile_items(*b, true, 0, v);
-    B_CU(b->items4.alloc(v.size(), stream), "allocate batch items");
-    b->items4.h = v;
-    B_CU(b->items4.upload(), "upload batch items");
+    b->ranges.clear();
+    for (int p0 = 0; p0 < np; p0 += BATCH_TAB) {
+        std::unique_ptr<PairRange> r(new (std::nothrow) PairRange());
+        if (!r) return set_error(nullptr, NGF_ENOMEM, "host allocation failed");
+        r->p0 = p0;
+        r->p1 = std::min(np, p0 + BATCH_TAB);
+        std::vector<int4> v;
+        DevArray<int4>* lists[3] = {&r->items0, &r->items3, &r->items4};
+        for (int li = 0; li < 3; ++li) {
+            tile_items(*b, r->p0, r->p1, li > 0, li == 0 ? -1 : (li == 1 ? 1 : 0), v);
+            B_CU(lists[li]->alloc(v.size(), stream), "allocate batch items");
+            lists[li]->h = v;
+            B_CU(lists[li]->upload(), "upload batch items");
+        }
+        b->ranges.push_back(std::move(r));
+    }
     B_CU(b->qctr.alloc(2, stream), "allocate batch queue");
     B_CU(b->qctr.upload(), "clear batch queue");
     std::vector<int> c1(np), cv(np), cd(np);
@@ -174,11 +184,11 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     return NGF_OK;
 }
 
-static BatchQueue queue(const Batch& b, const DevArray<int4>& items, const ImgParams* params, const int* active) {
+static BatchQueue queue(const Batch& b, const PairRange& r, const DevArray<int4>& items, const int* active) {
     BatchQueue Q;
-    Q.params = params;
     Q.items = items.d;
     Q.nitems = (int)items.h.size();
+    Q.pair0 = r.p0;
     Q.active = active;
     Q.next = b.qctr.d;
     Q.done = b.qctr.d + 1;
@@ -190,29 +200,46 @@ static BatchSegs segs(const Batch& b, const DevArray<int>& first, const int* act
     return BatchSegs{first.d, pair_of, b.np, active};
 }
 
-// ---- launch sequences shared by the operator calls and the registration
-// (tables already uploaded)
+// the parameter blocks of one range, passed by value with the launch
+static void fill_table(const PairRange& r, const std::vector<ImgParams>& tab, BatchImgTable& T) {
+    for (int k = r.p0; k < r.p1; ++k) T.p[k - r.p0] = tab[k];
+}
 
-static ngf_status launch_image(const Batch& b, int mode, const ImgParams* tab, const int* active) {
-    const BatchQueue Q = queue(b, b.items0, tab, active);
-    const dim3 grid(b.img_grid());
-    if (mode == MODE_OBJ) B_CU(launch(k_batch_image_obj, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q), "k_batch_image_obj");
-    else if (mode == MODE_GRAD)
-        B_CU(launch(k_batch_image_grad, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q), "k_batch_image_grad");
-    else B_CU(launch(k_batch_image_hess, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q), "k_batch_image_hess");
+// ---- launch sequences shared by the operator calls and the registration
+// (nodal tables already uploaded)
+
+static ngf_status launch_image(const Batch& b, int mode, const std::vector<ImgParams>& tab, const int* active) {
+    std::unique_ptr<BatchImgTable> T(new BatchImgTable());
+    for (const auto& rp : b.ranges) {
+        const PairRange& r = *rp;
+        if (r.items0.h.empty()) continue;
+        fill_table(r, tab, *T);
+        const BatchQueue Q = queue(b, r, r.items0, active);
+        const dim3 grid(std::min((int)r.items0.h.size(), 2 * b.sms));
+        if (mode == MODE_OBJ)
+            B_CU(launch(k_batch_image_obj, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_image_obj");
+        else if (mode == MODE_GRAD)
+            B_CU(launch(k_batch_image_grad, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_image_grad");
+        else B_CU(launch(k_batch_image_hess, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_image_hess");
+    }
     return NGF_OK;
 }
 
-static ngf_status launch_diag(const Batch& b, const ImgParams* tab, const int* active) {
-    if (!b.items3.h.empty()) {
-        const BatchQueue Q = queue(b, b.items3, tab, active);
-        const dim3 grid(std::min((int)b.items3.h.size(), b.sms));
-        B_CU(launch(k_batch_diag, grid, dim3(NT), sizeof(DiagSmem), b.stream, Q), "k_batch_diag");
-    }
-    if (!b.items4.h.empty()) {
-        const BatchQueue Q = queue(b, b.items4, tab, active);
-        const dim3 grid(std::min((int)b.items4.h.size(), b.sms));
-        B_CU(launch(k_batch_diag4, grid, dim3(NT), sizeof(DiagSmem), b.stream, Q), "k_batch_diag4");
+static ngf_status launch_diag(const Batch& b, const std::vector<ImgParams>& tab, const int* active) {
+    std::unique_ptr<BatchImgTable> T(new BatchImgTable());
+    for (const auto& rp : b.ranges) {
+        const PairRange& r = *rp;
+        fill_table(r, tab, *T);
+        if (!r.items3.h.empty()) {
+            const BatchQueue Q = queue(b, r, r.items3, active);
+            const dim3 grid(std::min((int)r.items3.h.size(), b.sms));
+            B_CU(launch(k_batch_diag, grid, dim3(NT), sizeof(DiagSmem), b.stream, Q, *T), "k_batch_diag");
+        }
+        if (!r.items4.h.empty()) {
+            const BatchQueue Q = queue(b, r, r.items4, active);
+            const dim3 grid(std::min((int)r.items4.h.size(), b.sms));
+            B_CU(launch(k_batch_diag4, grid, dim3(NT), sizeof(DiagSmem), b.stream, Q, *T), "k_batch_diag4");
+        }
     }
     return NGF_OK;
 }
@@ -258,7 +285,7 @@ static ngf_status batch_hessvec(Batch& b, const float* const* R, const float* co
     B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
     B_TRY(launch_lap(b, b.t_lap.d, nullptr));
-    B_TRY(launch_image(b, MODE_HESS, b.t_img.d, nullptr));
+    B_TRY(launch_image(b, MODE_HESS, b.t_img.h, nullptr));
     return launch_combine(b, b.t_comb.d, nullptr);
 }
 
@@ -362,7 +389,7 @@ ngf_status ngf_batch_objective(ngf_batch* batch, const float* const* R, const fl
     }
     B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_lap.upload(), "upload tables");
-    B_TRY(launch_image(b, MODE_OBJ, b.t_img.d, nullptr));
+    B_TRY(launch_image(b, MODE_OBJ, b.t_img.h, nullptr));
     B_TRY(launch_lap(b, b.t_lap.d, nullptr));
     std::vector<double> h(2);
     for (int k = 0; k < b.np; ++k) {
@@ -392,7 +419,7 @@ ngf_status ngf_batch_gradient(ngf_batch* batch, const float* const* R, const flo
     B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_lap.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
-    B_TRY(launch_image(b, MODE_GRAD, b.t_img.d, nullptr));
+    B_TRY(launch_image(b, MODE_GRAD, b.t_img.h, nullptr));
     B_TRY(launch_lap(b, b.t_lap.d, nullptr));
     return launch_combine(b, b.t_comb.d, nullptr);
 }
@@ -424,7 +451,7 @@ ngf_status ngf_batch_diagonal(ngf_batch* batch, const float* const* R, const flo
     }
     B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
-    B_TRY(launch_diag(b, b.t_img.d, nullptr));
+    B_TRY(launch_diag(b, b.t_img.h, nullptr));
     return launch_combine(b, b.t_comb.d, nullptr);
 }
 
@@ -667,7 +694,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
         int* act = tb.act.d;
         auto pcg_iteration = [&]() -> ngf_status {
             B_TRY(launch_lap(b, tb.lap_d.d, act));
-            B_TRY(launch_image(b, MODE_HESS, tb.hess.d, act));
+            B_TRY(launch_image(b, MODE_HESS, tb.hess.h, act));
             B_TRY(launch_combine(b, tb.comb_hess.d, act));
             B_CU(launch(k_batch_pcg_update, gv, dim3(NT), 0, stream, (const PcgParams*)tb.pcg.d, segs(b, b.firstv, act)),
                  "k_batch_pcg_update");
@@ -726,7 +753,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
         for (int it = 0; it < o->gn_iters; ++it) {
             if (std::none_of(active.begin(), active.end(), [](int a) { return a != 0; })) break;
             B_CU(put(tb.act, active), "upload mask");
-            B_TRY(launch_image(b, MODE_GRAD, tb.grad.d, act));
+            B_TRY(launch_image(b, MODE_GRAD, tb.grad.h, act));
             B_TRY(launch_lap(b, tb.lap_u.d, act));
             B_TRY(launch_combine(b, tb.comb_grad.d, act));
             B_CU(launch(k_batch_dot, gd, dim3(NT), 0, stream, (const DotArgs*)tb.dot_gg.d, segs(b, b.firstd, act)),
@@ -740,7 +767,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             }
             if (std::none_of(active.begin(), active.end(), [](int a) { return a != 0; })) break;
             B_CU(put(tb.act, active), "upload mask");
-            B_TRY(launch_diag(b, tb.diag.d, act));
+            B_TRY(launch_diag(b, tb.diag.h, act));
             B_TRY(launch_combine(b, tb.comb_diag.d, act));
             B_CU(launch(k_scale, dim3(grid_for((long long)off[np], 4 * b.sms)), dim3(NT), 0, stream,
                         (long long)off[np], -1.0f, (const float*)g, r),
@@ -780,7 +807,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
                 B_CU(launch(k_batch_axpy, gv, dim3(NT), 0, stream, (const AxpyArgs*)tb.trial.d,
                             segs(b, b.firstv, tb.srch.d)),
                      "k_batch_axpy");
-                B_TRY(launch_image(b, MODE_OBJ, tb.obj_ut.d, tb.srch.d));
+                B_TRY(launch_image(b, MODE_OBJ, tb.obj_ut.h, tb.srch.d));
                 B_TRY(launch_lap(b, tb.lap_ut.d, tb.srch.d));
                 B_TRY(read_scalars());
                 for (int k = 0; k < np; ++k) {
@@ -813,7 +840,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             }
         }
         // objective at the level's result, every pair
-        B_TRY(launch_image(b, MODE_OBJ, tb.obj_u.d, nullptr));
+        B_TRY(launch_image(b, MODE_OBJ, tb.obj_u.h, nullptr));
         B_TRY(launch_lap(b, tb.lap_u.d, nullptr));
         B_TRY(read_scalars());
         for (int k = 0; k < np; ++k) {

@@ -1454,8 +1454,7 @@ __device__ __forceinline__ void queue_release(const BatchQueue& Q) {
 }
 
 template <int KIND>  // 0..2: image pass mode, 3: diagonal (span 3), 4: diagonal (span 4)
-__device__ __forceinline__ void batch_image_loop(const BatchQueue& Q) {
-    __shared__ ImgParams Ps;
+__device__ __forceinline__ void batch_image_loop(const BatchQueue& Q, const BatchImgTable& T) {
     __shared__ int4 item;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -1466,8 +1465,7 @@ __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q) {
         const int4 it = item;
         if (it.x < 0) break;
         if (!Q.active || Q.active[it.x]) {
-            copy_to_shared(Ps, Q.params + it.x);
-            __syncthreads();
+            const ImgParams& Ps = T.p[it.x - Q.pair0];
             if (KIND == 3) diag_pass<3>(Ps, it.y, it.z, it.w);
             else if (KIND == 4) diag_pass<4>(Ps, it.y, it.z, it.w);
             else image_pass<KIND>(Ps, it.y, it.z, it.w);
@@ -1477,11 +1475,21 @@ __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q) {
     queue_release(Q);
 }
 
-__global__ void __launch_bounds__(NT, 2) k_batch_image_obj(const BatchQueue Q) { batch_image_loop<MODE_OBJ>(Q); }
-__global__ void __launch_bounds__(NT, 2) k_batch_image_grad(const BatchQueue Q) { batch_image_loop<MODE_GRAD>(Q); }
-__global__ void __launch_bounds__(NT, 2) k_batch_image_hess(const BatchQueue Q) { batch_image_loop<MODE_HESS>(Q); }
-__global__ void __launch_bounds__(NT, 1) k_batch_diag(const BatchQueue Q) { batch_image_loop<3>(Q); }
-__global__ void __launch_bounds__(NT, 1) k_batch_diag4(const BatchQueue Q) { batch_image_loop<4>(Q); }
+__global__ void __launch_bounds__(NT, 2) k_batch_image_obj(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<MODE_OBJ>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 2) k_batch_image_grad(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<MODE_GRAD>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 2) k_batch_image_hess(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<MODE_HESS>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 1) k_batch_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<3>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 1) k_batch_diag4(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<4>(Q, T);
+}
 
 template <class ARGS, class BODY>
 __device__ __forceinline__ void batch_nodal(const ARGS* table, const BatchSegs& S, BODY body) {

@@ -264,10 +264,16 @@ __global__ void k_lbfgs_r(long long n, double rho, const double* dot, const doub
 // ---- batched forms (independent problems of uneven size in one launch)
 // Image passes: a persistent grid takes work items (pair, tile x, tile y,
 // tile z) from a queue; the last CTA to finish resets the queue.
+// The pairs' parameter blocks travel as one kernel parameter (constant
+// bank, read-only), so the pass reads them as cheaply as a single launch's.
+constexpr int BATCH_TAB = 112;  // pairs per launch: 112 x 264 B fit the 32 KB parameter limit
+struct BatchImgTable {
+    ImgParams p[BATCH_TAB];
+};
 struct BatchQueue {
-    const ImgParams* params;  // one per pair
     const int4* items;        // (pair, bx, by, bz), largest tiles first
     int nitems;
+    int pair0;                // pair of table entry 0
     const int* active;        // per pair: 0 skips its items (nullable)
     unsigned int* next;       // queue head and finished-CTA count, zero between launches
     unsigned int* done;
@@ -279,11 +285,11 @@ struct BatchSegs {
     int npairs;
     const int* active;   // nullable
 };
-__global__ void k_batch_image_obj(const BatchQueue Q);
-__global__ void k_batch_image_grad(const BatchQueue Q);
-__global__ void k_batch_image_hess(const BatchQueue Q);
-__global__ void k_batch_diag(const BatchQueue Q);
-__global__ void k_batch_diag4(const BatchQueue Q);
+__global__ void k_batch_image_obj(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_image_grad(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_image_hess(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_diag4(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_lap(const LapArgs* table, const BatchSegs S);
 __global__ void k_batch_combine(const CombineParams* table, const BatchSegs S);
 __global__ void k_batch_pcg_init(const PcgParams* table, const BatchSegs S);

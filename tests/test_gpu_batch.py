@@ -137,3 +137,28 @@ def test_register_batch_rejects_bad_arguments(ngf):
     with pytest.raises(ngf.NGFError) as e:
         ngf.register_batch(descs, ngf.options(2), [R[0], bad], T, ub)
     assert e.value.status == -4 and "pair 1" in str(e.value)
+
+
+def test_batch_larger_than_one_parameter_table(ngf):
+    """More pairs than one launch's parameter table holds (two launches per
+    image stage): every pair still equals its own plan."""
+    g = torch.Generator().manual_seed(5)
+    cs = []
+    for k in range(130):
+        m, n = (4 + k % 5, 3 + k % 3, 3 + k % 2), (3, 2, 2)
+        M, N = m[0] * m[1] * m[2], 12
+        c = G.Case(m, (1.0, 1.0, 1.0), n, 0.5, 0.2, 0.2, torch.rand(M, generator=g), torch.rand(M, generator=g),
+                   0.2 * torch.randn(3 * N, generator=g), torch.randn(3 * N, generator=g))
+        cs.append(c)
+    q = [c.empty() for c in cs]
+    with ngf.Batch([c.desc for c in cs]) as b:
+        ngf.ngf_batch_hessvec(b.handle, [c.R for c in cs], [c.T for c in cs], [c.u for c in cs],
+                              [c.p for c in cs], q)
+        torch.cuda.synchronize()
+    for k in (0, 64, 111, 112, 129):
+        c = cs[k]
+        with ngf.Plan(c.desc) as pl:
+            q1 = c.empty()
+            ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
+            torch.cuda.synchronize()
+        assert torch.equal(q[k], q1), k
