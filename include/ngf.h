@@ -230,7 +230,8 @@ ngf_status register_multilevel(const ngf_level_desc* finest, const ngf_options* 
  * arrays of npairs doubles.  Calls enqueue on the batch's stream; the
  * objective and the autotuner synchronise it.
  * zc: planes per z-chunk of the image-pass tiles (32 x 16 x zc voxels);
- * 0 picks about two thread blocks per SM for each pair. */
+ * 0 picks, per pair, the chunk count that minimises rounds of two thread
+ * blocks per SM times planes marched. */
 typedef struct ngf_batch ngf_batch;
 ngf_status ngf_batch_create(ngf_batch** batch, int32_t npairs, const ngf_level_desc* descs, int32_t zc,
                             void* cuda_stream);
