@@ -24,16 +24,24 @@ __device__ __forceinline__ void ring_coord(int k, int halo, int& lx, int& ly) {
     }
 }
 
-// Block-wide float64 sum with a fixed tree order (all threads see the result).
+// Block-wide float64 sum in a fixed order (all threads see the result):
+// shuffle trees within the warps, then over the warp sums in warp 0; two
+// barriers instead of one per tree level.
 __device__ __forceinline__ double block_sum(double v, double* red) {
-    const int tid = threadIdx.x;
-    red[tid] = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();  // red may still be read by a previous call
+    if (lane == 0) red[w] = v;
     __syncthreads();
-    for (int s = NT / 2; s > 0; s >>= 1) {
-        if (tid < s) red[tid] += red[tid + s];
-        __syncthreads();
+    if (w == 0) {
+        double t = (lane < NT / 32) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = NT / 64; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (lane == 0) red[NT / 32] = t;
     }
-    return red[0];
+    __syncthreads();
+    return red[NT / 32];
 }
 
 // Deterministic grid-wide float64 sum: each CTA stores its partial, the last
