@@ -7,9 +7,11 @@
  * J(y) = D(y) + alpha S(y) over a nodal deformation grid y, with D the
  * normalized-gradient-fields distance (Eq. NGF_discretized) and S the
  * curvature regulariser (Eq. CURV_discretized), by Gauss-Newton with a
- * (preconditioned) CG inner solve and Armijo line search, coarse to fine
- * (Sec. 2.3).  Every derivative is evaluated matrix-free (Sec. 4): no
- * Jacobian, sparse matrix or other O(voxels) derivative storage is kept.
+ * (preconditioned) CG inner solve or by L-BFGS, with Armijo line search,
+ * coarse to fine (Sec. 2.3).  Every derivative is evaluated matrix-free
+ * (Sec. 4): no Jacobian, sparse matrix or other O(voxels) derivative storage
+ * is kept.  The sum of squared differences (Sec. 7) can replace NGF per
+ * level; many pairs can be processed together by the batched form.
  *
  * Layout (Sec. 2.2, Table 1), 0-based:
  *  - images R, T: m[0]*m[1]*m[2] float32, x fastest, cell centres at
@@ -47,7 +49,7 @@
 extern "C" {
 #endif
 
-#define NGF_ABI_VERSION 1
+#define NGF_ABI_VERSION 2
 
 typedef enum {
     NGF_OK = 0,

@@ -264,6 +264,8 @@ static void curvature_tables(const Plan* p, std::vector<float>& t) {
     }
 }
 
+static ngf_status build_dct_tables(Plan* p);
+
 static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t stream, int zc_req) {
     std::string why;
     const ngf_status vs = validate_desc(d, why);
@@ -377,7 +379,7 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
                "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
-    return NGF_OK;
+    return build_dct_tables(p);  // L-BFGS initial Hessian (ngf_h0_solve)
 }
 
 NodeGeom node_geom(const Plan* p) {
@@ -537,32 +539,36 @@ ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u
     return NGF_OK;
 }
 
-// r = (alpha grad^2 S + gamma I)^{-1} q through the DCT-II eigenbasis of the
-// clamped Laplacian (tables built on first use)
-ngf_status h0_impl(Plan* p, double gamma, const float* q, float* r) {
-    if (!p->dct_cos) {
-        const int nt = p->n[0] + p->n[1] + p->n[2];
-        std::vector<float> cs(4 * (size_t)nt), mu(nt);
-        int oc = 0, om = 0;
-        for (int a = 0; a < 3; ++a) {
-            const int n = p->n[a];
-            for (int m = 0; m < 4 * n; ++m) cs[oc + m] = (float)std::cos(M_PI * m / (2.0 * n));
-            for (int k = 0; k < n; ++k) {
-                const double sn = std::sin(M_PI * k / (2.0 * n));
-                mu[om + k] = (float)(-4.0 * sn * sn / (p->hy[a] * p->hy[a]));
-            }
-            oc += 4 * n;
-            om += n;
+// DCT-II tables of the L-BFGS initial Hessian: cos(pi m / 2n) for m < 4n
+// and the 1-D eigenvalues -4 sin^2(pi k / 2n) / hy^2, per axis
+static ngf_status build_dct_tables(Plan* p) {
+    const int nt = p->n[0] + p->n[1] + p->n[2];
+    std::vector<float> cs(4 * (size_t)nt), mu(nt);
+    int oc = 0, om = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int n = p->n[a];
+        for (int m = 0; m < 4 * n; ++m) cs[oc + m] = (float)std::cos(M_PI * m / (2.0 * n));
+        for (int k = 0; k < n; ++k) {
+            const double sn = std::sin(M_PI * k / (2.0 * n));
+            mu[om + k] = (float)(-4.0 * sn * sn / (p->hy[a] * p->hy[a]));
         }
-        NGF_CU(p, dev_alloc((void**)&p->dct_cos, cs.size() * sizeof(float), p->stream), "allocate DCT tables");
-        NGF_CU(p, dev_alloc((void**)&p->dct_mu, mu.size() * sizeof(float), p->stream), "allocate DCT tables");
-        NGF_CU(p, dev_alloc((void**)&p->h0_tmp, 3 * p->N * sizeof(float), p->stream), "allocate DCT scratch");
-        NGF_CU(p, cudaMemcpyAsync(p->dct_cos, cs.data(), cs.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream),
-               "copy DCT tables");
-        NGF_CU(p, cudaMemcpyAsync(p->dct_mu, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream),
-               "copy DCT tables");
-        NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+        oc += 4 * n;
+        om += n;
     }
+    NGF_CU(p, dev_alloc((void**)&p->dct_cos, cs.size() * sizeof(float), p->stream), "allocate DCT tables");
+    NGF_CU(p, dev_alloc((void**)&p->dct_mu, mu.size() * sizeof(float), p->stream), "allocate DCT tables");
+    NGF_CU(p, dev_alloc((void**)&p->h0_tmp, 3 * p->N * sizeof(float), p->stream), "allocate DCT scratch");
+    NGF_CU(p, cudaMemcpyAsync(p->dct_cos, cs.data(), cs.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream),
+           "copy DCT tables");
+    NGF_CU(p, cudaMemcpyAsync(p->dct_mu, mu.data(), mu.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream),
+           "copy DCT tables");
+    NGF_CU(p, cudaStreamSynchronize(p->stream), "cudaStreamSynchronize");
+    return NGF_OK;
+}
+
+// r = (alpha grad^2 S + gamma I)^{-1} q through the DCT-II eigenbasis of the
+// clamped Laplacian
+ngf_status h0_impl(Plan* p, double gamma, const float* q, float* r) {
     const NodeGeom G = node_geom(p);
     const dim3 grid(grid_for(3 * p->N, 16 * 148)), blk(NT);
     const float* cosx = p->dct_cos;
