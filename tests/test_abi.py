@@ -84,3 +84,25 @@ def test_register_multilevel_validates_options(ngf):
     buf = (C.c_float * 512)()
     st = ngf.lib.register_multilevel(C.byref(d), C.byref(o), buf, buf, buf, C.byref(rep), None)
     assert st == -1 and "levels" in ngf.ngf_last_error(None)
+
+
+def test_size_limit_and_distance_validation(ngf):
+    """Rejections that come before any CUDA call: grids past the 2^31 index
+    range, an unknown distance, an unknown method, an empty batch."""
+    h = C.c_void_p()
+    big = ngf.level_desc((2048, 2048, 1024), (1, 1, 1), (65, 65, 33))
+    assert ngf.lib.ngf_plan_create(C.byref(h), C.byref(big), None) == -8 and not h.value
+    assert "2^31" in ngf.ngf_last_error(None)
+    bad = ngf.level_desc((8, 8, 8), (1, 1, 1), (5, 5, 5), distance=3)
+    assert ngf.lib.ngf_plan_create(C.byref(h), C.byref(bad), None) == -1
+    assert "distance" in ngf.ngf_last_error(None)
+    ok = ngf.level_desc((8, 8, 8), (1, 1, 1), (5, 5, 5))
+    buf = (C.c_float * 600)()
+    rep = ngf.Report()
+    opts = ngf.options(2, method=5)
+    assert ngf.lib.register_multilevel(C.byref(ok), C.byref(opts), buf, buf, buf, C.byref(rep), None) == -1
+    assert "method" in ngf.ngf_last_error(None)
+    opts = ngf.options(2, method=ngf.NGF_METHOD_LBFGS, lbfgs_memory=0)
+    assert ngf.lib.register_multilevel(C.byref(ok), C.byref(opts), buf, buf, buf, C.byref(rep), None) == -1
+    bh = C.c_void_p()
+    assert ngf.lib.ngf_batch_create(C.byref(bh), 0, C.byref(ok), 0, None) == -1 and not bh.value
