@@ -413,6 +413,65 @@ def run_kernel_case(args):
     return 0
 
 
+def shard_pairs(sizes, ws, rank):
+    """Indices of the pairs rank `rank` of `ws` registers: largest first to
+    the least-loaded rank (ties to the lower rank), by voxel count."""
+    load = [0] * ws
+    mine = []
+    for k in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(ws), key=lambda j: (load[j], j))
+        load[r] += sizes[k]
+        if r == rank:
+            mine.append(k)
+    return sorted(mine)
+
+
+def run_batch_sharded(args, ws, rank):
+    """batch_64 over several GPUs: the pairs are independent, so each rank
+    registers its share (balanced by voxels) with no data-path collective;
+    the job's time is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    from paper_1804_10541_b300 import ngf, synth
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    pairs = synth.batch_pairs(device=dev)
+    mine = shard_pairs([w["m"][0] * w["m"][1] * w["m"][2] for _, _, w in pairs], ws, rank)
+    pairs = [pairs[k] for k in mine]
+    descs = [ngf.level_desc(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"]) for _, _, w in pairs]
+    R, T = [p[0] for p in pairs], [p[1] for p in pairs]
+    U = [torch.zeros(3 * w["n"][0] * w["n"][1] * w["n"][2], device=dev) for _, _, w in pairs]
+    opts = ngf.options(levels=2, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            ngf.register_batch(descs, opts, R, T, U, stream=stream)
+    stream.synchronize()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    voxels = 0
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            reps = ngf.register_batch(descs, opts, R, T, U, stream=stream)
+            voxels += sum(r.hessvec_voxels for r in reps)
+        e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t_max, vox_all = reduce_max_sum(e0.elapsed_time(e1) / 1e3, voxels, ws)
+    if rank == 0:
+        print(json.dumps({"workload": "batch_64 sharded by pairs", "metric": METRIC, "value": vox_all / t_max / 1e9,
+                          "unit": "Gvoxel/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * t_max / args.steps, "scaling": "strong",
+                          "pairs_on_rank0": len(mine), "dtype": "f32", "data": "synthetic"}), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 def run_batch(args):
     """Batched form on 64 blob pairs of uneven cubic size (64..192 voxels per
     side, 2 levels, 10 GN x 20 PCG): one register_batch call per step, against
@@ -570,7 +629,8 @@ def main():
     if args.kernel_case:
         return run_kernel_case(args)
     if args.workload == "batch_64":
-        return run_batch(args)
+        ws, rank = _dist()
+        return run_batch_sharded(args, ws, rank) if ws > 1 else run_batch(args)
     if args.workload == "thorax_abd":
         return run_thorax(args)
     if args.impl == "reference":

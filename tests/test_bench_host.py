@@ -79,3 +79,13 @@ def test_stored_traffic_tracks_the_kernel_source(tmp_path, monkeypatch):
     assert b.stored_traffic() == 123.0
     prof.write_text("x\ntraffic_bytes_per_launch: 123\nimage_pass_source_sha256: 00\n")
     assert b.stored_traffic() is None
+
+
+def test_shard_pairs_partitions_and_balances():
+    sizes = [((k * 37) % 129 + 64) ** 3 for k in range(64)]
+    for ws in (1, 2, 3, 8):
+        shards = [bench.shard_pairs(sizes, ws, r) for r in range(ws)]
+        flat = sorted(i for sh in shards for i in sh)
+        assert flat == list(range(64))  # every pair exactly once
+        loads = [sum(sizes[i] for i in sh) for sh in shards]
+        assert max(loads) - min(loads) <= max(sizes)  # greedy bound
