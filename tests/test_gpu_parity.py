@@ -266,3 +266,22 @@ def test_launch_counter_counts_kernels(ngf):
         before = ngf.ngf_launch_count()
         ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, c.empty())
         assert ngf.ngf_launch_count() - before == 3
+
+
+def _random_shapes(count=12, seed=2024):
+    """Seeded random grids: 1..80 cells per axis, every voxels-per-cell ratio
+    from 1 (nodes = cells + 1) to about 8, anisotropic spacing."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        m = tuple(int(v) for v in rng.integers(1, 81, size=3))
+        n = tuple(max(2, min(mk + 1, mk // int(rng.integers(1, 9)) + 1)) for mk in m)
+        h = tuple(float(v) for v in rng.uniform(0.5, 2.5, size=3))
+        out.append((m, h, n))
+    return out
+
+
+@pytest.mark.parametrize("m,h,n", _random_shapes())
+def test_operators_match_oracle_random_shapes(ngf, m, h, n):
+    c = G.random_case(m, h, n, seed=sum(m) + 7)
+    _assert_ok(_all_ops(ngf, c))
