@@ -63,7 +63,7 @@ struct Batch {
     DevArray<int> first1, firstv, firstd;    // block ranges: per node, per vector element, dot
     DevArray<int> pair1, pairv, paird;       // pair of every block of those launches
     // parameter tables of the operator calls
-    DevArray<ImgParams> t_img;
+    std::vector<ImgParams> t_img;  // image-pass blocks travel with the launch
     DevArray<LapArgs> t_lap;
     DevArray<CombineParams> t_comb;
     Batch() = default;
@@ -171,7 +171,7 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     B_TRY(fill_segments(b->first1, b->pair1, c1, stream));
     B_TRY(fill_segments(b->firstv, b->pairv, cv, stream));
     B_TRY(fill_segments(b->firstd, b->paird, cd, stream));
-    B_CU(b->t_img.alloc(np, stream), "allocate batch tables");
+    b->t_img.assign(np, ImgParams{});
     B_CU(b->t_lap.alloc(np, stream), "allocate batch tables");
     B_CU(b->t_comb.alloc(np, stream), "allocate batch tables");
     const int ismem = (int)sizeof(ImgSmem), dsmem = (int)sizeof(DiagSmem);
@@ -278,14 +278,13 @@ static ngf_status batch_hessvec(Batch& b, const float* const* R, const float* co
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
         b.t_lap.h[k] = lap_args(p, pv[k], nullptr);
-        b.t_img.h[k] = img_params(p, R[k], T[k], u[k], pv[k], MODE_HESS, p->g0, nullptr);
+        b.t_img[k] = img_params(p, R[k], T[k], u[k], pv[k], MODE_HESS, p->g0, nullptr);
         b.t_comb.h[k] = combine_params(p, p->g0, q[k], p->L, nullptr, nullptr, nullptr);
     }
     B_CU(b.t_lap.upload(), "upload tables");
-    B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
     B_TRY(launch_lap(b, b.t_lap.d, nullptr));
-    B_TRY(launch_image(b, MODE_HESS, b.t_img.h, nullptr));
+    B_TRY(launch_image(b, MODE_HESS, b.t_img, nullptr));
     return launch_combine(b, b.t_comb.d, nullptr);
 }
 
@@ -384,12 +383,11 @@ ngf_status ngf_batch_objective(ngf_batch* batch, const float* const* R, const fl
     if (!D || !S) return set_error(nullptr, NGF_EINVAL, "D and S must be non-NULL");
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
-        b.t_img.h[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_OBJ, p->g0, p->dsc);
+        b.t_img[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_OBJ, p->g0, p->dsc);
         b.t_lap.h[k] = lap_args(p, u[k], p->dsc + 1);
     }
-    B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_lap.upload(), "upload tables");
-    B_TRY(launch_image(b, MODE_OBJ, b.t_img.h, nullptr));
+    B_TRY(launch_image(b, MODE_OBJ, b.t_img, nullptr));
     B_TRY(launch_lap(b, b.t_lap.d, nullptr));
     std::vector<double> h(2);
     for (int k = 0; k < b.np; ++k) {
@@ -412,14 +410,13 @@ ngf_status ngf_batch_gradient(ngf_batch* batch, const float* const* R, const flo
                          {(const void* const*)grad, "grad"}}));
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
-        b.t_img.h[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_GRAD, p->g0, p->dsc);
+        b.t_img[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_GRAD, p->g0, p->dsc);
         b.t_lap.h[k] = lap_args(p, u[k], p->dsc + 1);
         b.t_comb.h[k] = combine_params(p, p->g0, grad[k], p->L, nullptr, nullptr, nullptr);
     }
-    B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_lap.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
-    B_TRY(launch_image(b, MODE_GRAD, b.t_img.h, nullptr));
+    B_TRY(launch_image(b, MODE_GRAD, b.t_img, nullptr));
     B_TRY(launch_lap(b, b.t_lap.d, nullptr));
     return launch_combine(b, b.t_comb.d, nullptr);
 }
@@ -446,12 +443,11 @@ ngf_status ngf_batch_diagonal(ngf_batch* batch, const float* const* R, const flo
                          {(const void* const*)diag, "diag"}}));
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
-        b.t_img.h[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_HESS, p->g1, nullptr);
+        b.t_img[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_HESS, p->g1, nullptr);
         b.t_comb.h[k] = combine_params(p, p->g1, diag[k], nullptr, p->ctab, nullptr, nullptr);
     }
-    B_CU(b.t_img.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
-    B_TRY(launch_diag(b, b.t_img.h, nullptr));
+    B_TRY(launch_diag(b, b.t_img, nullptr));
     return launch_combine(b, b.t_comb.d, nullptr);
 }
 
@@ -499,7 +495,7 @@ struct DBuf {  // stream-ordered device buffer
 // per-level tables of the registration, built once per level (the pointers
 // they hold do not change within a level; the PCG graph replays them)
 struct LevelTables {
-    DevArray<ImgParams> obj_u, obj_ut, grad, diag, hess;
+    std::vector<ImgParams> obj_u, obj_ut, grad, diag, hess;  // travel with the launches
     DevArray<LapArgs> lap_u, lap_ut, lap_d;
     DevArray<CombineParams> comb_grad, comb_diag, comb_hess;
     DevArray<PcgParams> pcg;
@@ -641,8 +637,8 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
 
         LevelTables tb;
         auto A = [&](auto& t) { return t.alloc(np, stream); };
-        B_CU(A(tb.obj_u), "tables"); B_CU(A(tb.obj_ut), "tables"); B_CU(A(tb.grad), "tables");
-        B_CU(A(tb.diag), "tables"); B_CU(A(tb.hess), "tables"); B_CU(A(tb.lap_u), "tables");
+        for (auto* t : {&tb.obj_u, &tb.obj_ut, &tb.grad, &tb.diag, &tb.hess}) t->assign(np, ImgParams{});
+        B_CU(A(tb.lap_u), "tables");
         B_CU(A(tb.lap_ut), "tables"); B_CU(A(tb.lap_d), "tables"); B_CU(A(tb.comb_grad), "tables");
         B_CU(A(tb.comb_diag), "tables"); B_CU(A(tb.comb_hess), "tables"); B_CU(A(tb.pcg), "tables");
         B_CU(A(tb.dot_gg), "tables"); B_CU(A(tb.dot_gs), "tables"); B_CU(A(tb.trial), "tables");
@@ -653,11 +649,11 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             double* sk = sc + 32 * k;
             const long long n = 3 * p->N;
             const float *Rk = Rl[l][k], *Tk = Tl[l][k];
-            tb.obj_u.h[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_OBJ, p->g0, sk);
-            tb.obj_ut.h[k] = img_params(p, Rk, Tk, seg(ut, k), nullptr, MODE_OBJ, p->g0, sk);
-            tb.grad.h[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_GRAD, p->g0, sk);
-            tb.diag.h[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_HESS, p->g1, nullptr);
-            tb.hess.h[k] = img_params(p, Rk, Tk, seg(u, k), seg(d, k), MODE_HESS, p->g0, nullptr);
+            tb.obj_u[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_OBJ, p->g0, sk);
+            tb.obj_ut[k] = img_params(p, Rk, Tk, seg(ut, k), nullptr, MODE_OBJ, p->g0, sk);
+            tb.grad[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_GRAD, p->g0, sk);
+            tb.diag[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_HESS, p->g1, nullptr);
+            tb.hess[k] = img_params(p, Rk, Tk, seg(u, k), seg(d, k), MODE_HESS, p->g0, nullptr);
             tb.lap_u.h[k] = lap_args(p, seg(u, k), sk + 1);
             tb.lap_ut.h[k] = lap_args(p, seg(ut, k), sk + 1);
             tb.lap_d.h[k] = lap_args(p, seg(d, k), nullptr);
@@ -683,7 +679,6 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             tb.trial.h[k] = AxpyArgs{n, 1.0f, seg(u, k), seg(x, k), seg(ut, k)};
             tb.accept.h[k] = AxpyArgs{n, 0.0f, seg(ut, k), nullptr, seg(u, k)};
         }
-        for (auto* t : {&tb.obj_u, &tb.obj_ut, &tb.grad, &tb.diag, &tb.hess}) B_CU(t->upload(), "upload tables");
         for (auto* t : {&tb.lap_u, &tb.lap_ut, &tb.lap_d}) B_CU(t->upload(), "upload tables");
         for (auto* t : {&tb.comb_grad, &tb.comb_diag, &tb.comb_hess}) B_CU(t->upload(), "upload tables");
         for (auto* t : {&tb.dot_gg, &tb.dot_gs}) B_CU(t->upload(), "upload tables");
@@ -694,7 +689,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
         int* act = tb.act.d;
         auto pcg_iteration = [&]() -> ngf_status {
             B_TRY(launch_lap(b, tb.lap_d.d, act));
-            B_TRY(launch_image(b, MODE_HESS, tb.hess.h, act));
+            B_TRY(launch_image(b, MODE_HESS, tb.hess, act));
             B_TRY(launch_combine(b, tb.comb_hess.d, act));
             B_CU(launch(k_batch_pcg_update, gv, dim3(NT), 0, stream, (const PcgParams*)tb.pcg.d, segs(b, b.firstv, act)),
                  "k_batch_pcg_update");
@@ -753,7 +748,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
         for (int it = 0; it < o->gn_iters; ++it) {
             if (std::none_of(active.begin(), active.end(), [](int a) { return a != 0; })) break;
             B_CU(put(tb.act, active), "upload mask");
-            B_TRY(launch_image(b, MODE_GRAD, tb.grad.h, act));
+            B_TRY(launch_image(b, MODE_GRAD, tb.grad, act));
             B_TRY(launch_lap(b, tb.lap_u.d, act));
             B_TRY(launch_combine(b, tb.comb_grad.d, act));
             B_CU(launch(k_batch_dot, gd, dim3(NT), 0, stream, (const DotArgs*)tb.dot_gg.d, segs(b, b.firstd, act)),
@@ -767,7 +762,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             }
             if (std::none_of(active.begin(), active.end(), [](int a) { return a != 0; })) break;
             B_CU(put(tb.act, active), "upload mask");
-            B_TRY(launch_diag(b, tb.diag.h, act));
+            B_TRY(launch_diag(b, tb.diag, act));
             B_TRY(launch_combine(b, tb.comb_diag.d, act));
             B_CU(launch(k_scale, dim3(grid_for((long long)off[np], 4 * b.sms)), dim3(NT), 0, stream,
                         (long long)off[np], -1.0f, (const float*)g, r),
@@ -807,7 +802,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
                 B_CU(launch(k_batch_axpy, gv, dim3(NT), 0, stream, (const AxpyArgs*)tb.trial.d,
                             segs(b, b.firstv, tb.srch.d)),
                      "k_batch_axpy");
-                B_TRY(launch_image(b, MODE_OBJ, tb.obj_ut.h, tb.srch.d));
+                B_TRY(launch_image(b, MODE_OBJ, tb.obj_ut, tb.srch.d));
                 B_TRY(launch_lap(b, tb.lap_ut.d, tb.srch.d));
                 B_TRY(read_scalars());
                 for (int k = 0; k < np; ++k) {
@@ -840,7 +835,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             }
         }
         // objective at the level's result, every pair
-        B_TRY(launch_image(b, MODE_OBJ, tb.obj_u.h, nullptr));
+        B_TRY(launch_image(b, MODE_OBJ, tb.obj_u, nullptr));
         B_TRY(launch_lap(b, tb.lap_u.d, nullptr));
         B_TRY(read_scalars());
         for (int k = 0; k < np; ++k) {
