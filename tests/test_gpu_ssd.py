@@ -87,3 +87,21 @@ def test_ssd_rejected_where_only_ngf_is_built(ngf):
     with pytest.raises(ngf.NGFError) as e:
         ngf.Plan(bad)
     assert e.value.status == -1
+
+
+def test_ssd_lbfgs_level_matches_oracle(ngf):
+    """SSD with the L-BFGS method: same steps and trials as the oracle's
+    L-BFGS on the SSD objective, u within 0.01 voxel."""
+    import oracle as O
+    from paper_1804_10541_b300 import synth
+    m, h, n = (24, 24, 24), (1.0, 1.0, 1.0), (13, 13, 13)
+    R, T, _ = synth.blob_pair(m, seed=1, device="cuda")
+    d = ngf.level_desc(m, h, n, 1.0, 0.1, 0.1, distance=ngf.NGF_DIST_SSD)
+    nn = 3 * 13 ** 3
+    u = torch.zeros(nn, device="cuda")
+    rep = ngf.register_multilevel(d, ngf.options(1, gn_iters=6, method=ngf.NGF_METHOD_LBFGS, lbfgs_memory=4), R, T, u)
+    L = O.level(m, h, n, 1.0, distance=O.DIST_SSD)
+    uo, ro, _, _ = O.lbfgs_level(L, G.f64(R), G.f64(T), np.zeros(nn), O.lbfgs_options(iters=6, memory=4))
+    assert rep.gn_done == ro.gn_done == 6 and rep.ls_trials == ro.ls_trials
+    assert float(np.abs(G.f64(u) - uo).max()) < 0.01
+    assert abs(rep.J - ro.J) <= 1e-5 * abs(ro.J)
