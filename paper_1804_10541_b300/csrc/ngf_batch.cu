@@ -48,7 +48,8 @@ struct DevArray {
 // their work items
 struct PairRange {
     int p0 = 0, p1 = 0;
-    DevArray<int4> items0, items3, items4;  // image tiles (halo 0); diagonal tiles (halo 1) by span
+    DevArray<int4> items0, items3, items4;  // image tiles (halo 0); NGF diagonal tiles (halo 1) by span
+    DevArray<int4> itemsS;                  // SSD diagonal tiles (halo 0)
 };
 
 struct Batch {
@@ -106,11 +107,16 @@ static ngf_status fill_segments(DevArray<int>& first, DevArray<int>& pair_of, co
 
 // (pair, tile) items of one geometry, by decreasing voxel count (the queue
 // hands them out in this order, so the largest start first)
+static bool is_ssd(const Plan* p) { return p->desc.distance == NGF_DIST_SSD; }
+
+// want_span3: -1 every pair; 0/1 NGF pairs whose diagonal has span 4/3;
+// 2 SSD pairs
 static void tile_items(const Batch& b, int p0, int p1, bool halo1, int want_span3, std::vector<int4>& out) {
     std::vector<std::pair<long long, int4>> it;
     for (int k = p0; k < p1; ++k) {
         const Plan* p = b.plan(k);
-        if (want_span3 >= 0 && (int)p->diag_span3 != want_span3) continue;
+        if (want_span3 == 2 && !is_ssd(p)) continue;
+        if ((want_span3 == 0 || want_span3 == 1) && (is_ssd(p) || (int)p->diag_span3 != want_span3)) continue;
         const Geometry& g = halo1 ? p->g1 : p->g0;
         for (int z = 0; z < g.ntz; ++z)
             for (int y = 0; y < g.nty; ++y)
@@ -134,9 +140,6 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    for (int k = 0; k < np; ++k)
-        if (descs[k].distance != NGF_DIST_NGF)
-            return set_error(nullptr, NGF_EINVAL, "the batched form evaluates the NGF distance only");
     for (int k = 0; k < np; ++k) {
         ngf_plan* pl = nullptr;
         const ngf_status s = plan_create(&pl, &descs[k], stream, zc);
@@ -150,9 +153,10 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
         r->p0 = p0;
         r->p1 = std::min(np, p0 + BATCH_TAB);
         std::vector<int4> v;
-        DevArray<int4>* lists[3] = {&r->items0, &r->items3, &r->items4};
-        for (int li = 0; li < 3; ++li) {
-            tile_items(*b, r->p0, r->p1, li > 0, li == 0 ? -1 : (li == 1 ? 1 : 0), v);
+        DevArray<int4>* lists[4] = {&r->items0, &r->items3, &r->items4, &r->itemsS};
+        const int want[4] = {-1, 1, 0, 2};
+        for (int li = 0; li < 4; ++li) {
+            tile_items(*b, r->p0, r->p1, li == 1 || li == 2, want[li], v);
             B_CU(lists[li]->alloc(v.size(), stream), "allocate batch items");
             lists[li]->h = v;
             B_CU(lists[li]->upload(), "upload batch items");
@@ -180,6 +184,7 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     B_CU(cudaFuncSetAttribute(k_batch_image_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, ismem), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem), "smem attr");
+    B_CU(cudaFuncSetAttribute(k_batch_ssd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, ismem), "smem attr");
     B_CU(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
     return NGF_OK;
 }
@@ -201,8 +206,11 @@ static BatchSegs segs(const Batch& b, const DevArray<int>& first, const int* act
 }
 
 // the parameter blocks of one range, passed by value with the launch
-static void fill_table(const PairRange& r, const std::vector<ImgParams>& tab, BatchImgTable& T) {
-    for (int k = r.p0; k < r.p1; ++k) T.p[k - r.p0] = tab[k];
+static void fill_table(const Batch& b, const PairRange& r, const std::vector<ImgParams>& tab, BatchImgTable& T) {
+    for (int k = r.p0; k < r.p1; ++k) {
+        T.p[k - r.p0] = tab[k];
+        T.ssd[k - r.p0] = is_ssd(b.plan(k)) ? 1 : 0;
+    }
 }
 
 // ---- launch sequences shared by the operator calls and the registration
@@ -213,7 +221,7 @@ static ngf_status launch_image(const Batch& b, int mode, const std::vector<ImgPa
     for (const auto& rp : b.ranges) {
         const PairRange& r = *rp;
         if (r.items0.h.empty()) continue;
-        fill_table(r, tab, *T);
+        fill_table(b, r, tab, *T);
         const BatchQueue Q = queue(b, r, r.items0, active);
         const dim3 grid(std::min((int)r.items0.h.size(), 2 * b.sms));
         if (mode == MODE_OBJ)
@@ -229,7 +237,7 @@ static ngf_status launch_diag(const Batch& b, const std::vector<ImgParams>& tab,
     std::unique_ptr<BatchImgTable> T(new BatchImgTable());
     for (const auto& rp : b.ranges) {
         const PairRange& r = *rp;
-        fill_table(r, tab, *T);
+        fill_table(b, r, tab, *T);
         if (!r.items3.h.empty()) {
             const BatchQueue Q = queue(b, r, r.items3, active);
             const dim3 grid(std::min((int)r.items3.h.size(), b.sms));
@@ -239,6 +247,11 @@ static ngf_status launch_diag(const Batch& b, const std::vector<ImgParams>& tab,
             const BatchQueue Q = queue(b, r, r.items4, active);
             const dim3 grid(std::min((int)r.items4.h.size(), b.sms));
             B_CU(launch(k_batch_diag4, grid, dim3(NT), sizeof(DiagSmem), b.stream, Q, *T), "k_batch_diag4");
+        }
+        if (!r.itemsS.h.empty()) {
+            const BatchQueue Q = queue(b, r, r.itemsS, active);
+            const dim3 grid(std::min((int)r.itemsS.h.size(), 2 * b.sms));
+            B_CU(launch(k_batch_ssd_diag, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_ssd_diag");
         }
     }
     return NGF_OK;
@@ -443,8 +456,9 @@ ngf_status ngf_batch_diagonal(ngf_batch* batch, const float* const* R, const flo
                          {(const void* const*)diag, "diag"}}));
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
-        b.t_img[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_HESS, p->g1, nullptr);
-        b.t_comb.h[k] = combine_params(p, p->g1, diag[k], nullptr, p->ctab, nullptr, nullptr);
+        const Geometry& gd = is_ssd(p) ? p->g0 : p->g1;  // the SSD diagonal needs no halo
+        b.t_img[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_HESS, gd, nullptr);
+        b.t_comb.h[k] = combine_params(p, gd, diag[k], nullptr, p->ctab, nullptr, nullptr);
     }
     B_CU(b.t_comb.upload(), "upload tables");
     B_TRY(launch_diag(b, b.t_img, nullptr));
@@ -652,13 +666,14 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             tb.obj_u[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_OBJ, p->g0, sk);
             tb.obj_ut[k] = img_params(p, Rk, Tk, seg(ut, k), nullptr, MODE_OBJ, p->g0, sk);
             tb.grad[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_GRAD, p->g0, sk);
-            tb.diag[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_HESS, p->g1, nullptr);
+            const Geometry& gd = is_ssd(p) ? p->g0 : p->g1;
+            tb.diag[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_HESS, gd, nullptr);
             tb.hess[k] = img_params(p, Rk, Tk, seg(u, k), seg(d, k), MODE_HESS, p->g0, nullptr);
             tb.lap_u.h[k] = lap_args(p, seg(u, k), sk + 1);
             tb.lap_ut.h[k] = lap_args(p, seg(ut, k), sk + 1);
             tb.lap_d.h[k] = lap_args(p, seg(d, k), nullptr);
             tb.comb_grad.h[k] = combine_params(p, p->g0, seg(g, k), p->L, nullptr, nullptr, nullptr);
-            tb.comb_diag.h[k] = combine_params(p, p->g1, seg(dg, k), nullptr, p->ctab, nullptr, nullptr);
+            tb.comb_diag.h[k] = combine_params(p, gd, seg(dg, k), nullptr, p->ctab, nullptr, nullptr);
             tb.comb_hess.h[k] = combine_params(p, p->g0, seg(q, k), p->L, nullptr, seg(d, k), sk + 8 + PS_DQ);
             PcgParams& P = tb.pcg.h[k];
             P.n = n;

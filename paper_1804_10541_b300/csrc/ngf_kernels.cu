@@ -1461,7 +1461,7 @@ __device__ __forceinline__ void queue_release(const BatchQueue& Q) {
     }
 }
 
-template <int KIND>  // 0..2: image pass mode, 3: diagonal (span 3), 4: diagonal (span 4)
+template <int KIND>  // 0..2: image pass mode (NGF or SSD per pair), 3/4: NGF diagonal (span 3/4), 5: SSD diagonal
 __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q, const BatchImgTable& T) {
     __shared__ int4 item;
     for (;;) {
@@ -1476,6 +1476,8 @@ __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q, const Batc
             const ImgParams& Ps = T.p[it.x - Q.pair0];
             if (KIND == 3) diag_pass<3>(Ps, it.y, it.z, it.w);
             else if (KIND == 4) diag_pass<4>(Ps, it.y, it.z, it.w);
+            else if (KIND == 5) ssd_pass<MODE_SSD_DIAG>(Ps, it.y, it.z, it.w);
+            else if (T.ssd[it.x - Q.pair0]) ssd_pass<KIND>(Ps, it.y, it.z, it.w);
             else image_pass<KIND>(Ps, it.y, it.z, it.w);
         }
         __syncthreads();
@@ -1497,6 +1499,9 @@ __global__ void __launch_bounds__(NT, 1) k_batch_diag(const BatchQueue Q, const 
 }
 __global__ void __launch_bounds__(NT, 1) k_batch_diag4(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
     batch_image_loop<4>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 2) k_batch_ssd_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<5>(Q, T);
 }
 
 template <class ARGS, class BODY>

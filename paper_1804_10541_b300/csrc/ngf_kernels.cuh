@@ -266,9 +266,10 @@ __global__ void k_lbfgs_r(long long n, double rho, const double* dot, const doub
 // tile z) from a queue; the last CTA to finish resets the queue.
 // The pairs' parameter blocks travel as one kernel parameter (constant
 // bank, read-only), so the pass reads them as cheaply as a single launch's.
-constexpr int BATCH_TAB = 112;  // pairs per launch: 112 x 264 B fit the 32 KB parameter limit
+constexpr int BATCH_TAB = 112;  // pairs per launch: 112 x (264 + 4) B fit the 32 KB parameter limit
 struct BatchImgTable {
     ImgParams p[BATCH_TAB];
+    int ssd[BATCH_TAB];  // 1: the pair's distance is SSD
 };
 struct BatchQueue {
     const int4* items;        // (pair, bx, by, bz), largest tiles first
@@ -290,6 +291,7 @@ __global__ void k_batch_image_grad(const BatchQueue Q, const __grid_constant__ B
 __global__ void k_batch_image_hess(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag4(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_ssd_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_lap(const LapArgs* table, const BatchSegs S);
 __global__ void k_batch_combine(const CombineParams* table, const BatchSegs S);
 __global__ void k_batch_pcg_init(const PcgParams* table, const BatchSegs S);

@@ -162,3 +162,40 @@ def test_batch_larger_than_one_parameter_table(ngf):
             ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
             torch.cuda.synchronize()
         assert torch.equal(q[k], q1), k
+
+
+def test_mixed_ngf_ssd_batch_equals_single_plans(ngf):
+    """Pairs with the SSD distance share the batch's launches with NGF pairs
+    (the SSD diagonal on its halo-free tiles); every pair equals its own plan,
+    and the batched registration each pair's own."""
+    cs = _cases()[:4]
+    for k in (1, 3):
+        cs[k].desc = ngf.level_desc(cs[k].m, cs[k].h, cs[k].n, 0.7, 0.15, 0.25, distance=ngf.NGF_DIST_SSD)
+    R, T, U, P = [c.R for c in cs], [c.T for c in cs], [c.u for c in cs], [c.p for c in cs]
+    q, g, dg = [c.empty() for c in cs], [c.empty() for c in cs], [c.empty() for c in cs]
+    with ngf.Batch([c.desc for c in cs]) as b:
+        ngf.ngf_batch_hessvec(b.handle, R, T, U, P, q)
+        ngf.ngf_batch_gradient(b.handle, R, T, U, g)
+        ngf.ngf_batch_diagonal(b.handle, R, T, U, dg)
+        Db, Sb = ngf.ngf_batch_objective(b.handle, R, T, U)
+        torch.cuda.synchronize()
+    for k, c in enumerate(cs):
+        with ngf.Plan(c.desc) as pl:
+            q1, g1, d1 = c.empty(), c.empty(), c.empty()
+            ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
+            ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g1, want_scalars=False)
+            ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, d1)
+            D, S = ngf.ngf_objective(pl.handle, c.R, c.T, c.u)
+            torch.cuda.synchronize()
+        assert torch.equal(q[k], q1) and torch.equal(g[k], g1) and torch.equal(dg[k], d1), k
+        assert D == Db[k] and S == Sb[k], k
+    pairs = _blob_batch([24, 29])
+    descs = [pairs[0][2], ngf.level_desc((29, 29, 29), (1.0, 1.0, 1.0), (15, 15, 15), 1.0, 0.1, 0.1,
+                                         distance=ngf.NGF_DIST_SSD)]
+    opts = ngf.options(2, gn_iters=3, pcg_iters=6)
+    ub = [torch.zeros(3 * d.n[0] * d.n[1] * d.n[2], device="cuda") for d in descs]
+    reps = ngf.register_batch(descs, opts, [p[0] for p in pairs], [p[1] for p in pairs], ub)
+    for k, d in enumerate(descs):
+        u1 = torch.zeros_like(ub[k])
+        r1 = ngf.register_multilevel(d, opts, pairs[k][0], pairs[k][1], u1)
+        assert torch.equal(u1, ub[k]) and r1.J == reps[k].J, k

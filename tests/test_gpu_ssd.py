@@ -74,14 +74,11 @@ def test_ssd_gauss_newton_level_matches_oracle(ngf):
     assert abs(rep.J - ro.J) <= 1e-5 * abs(ro.J)
 
 
-def test_ssd_rejected_where_only_ngf_is_built(ngf):
+def test_ssd_rejected_by_the_allocation_free_objective(ngf):
     c = _ssd_case(ngf, (20, 18, 16), (1.0, 1.0, 1.0), (11, 10, 9), seed=3)
     out = torch.zeros(2, device="cuda", dtype=torch.float64)
     with pytest.raises(ngf.NGFError) as e:
         ngf.ngf_objective_noalloc(c.desc, c.R, c.T, c.u, out)
-    assert e.value.status == -1
-    with pytest.raises(ngf.NGFError) as e:
-        ngf.Batch([c.desc])
     assert e.value.status == -1
     bad = ngf.level_desc((20, 18, 16), (1.0, 1.0, 1.0), (11, 10, 9), distance=7)
     with pytest.raises(ngf.NGFError) as e:
