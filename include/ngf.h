@@ -257,7 +257,8 @@ ngf_status ngf_batch_autotune(ngf_batch* batch, const float* const* R, const flo
 int32_t ngf_batch_zc(const ngf_batch* batch);
 
 /* Multilevel Gauss-Newton registration of npairs independent pairs, the same
- * options for all (u_init must be NULL): every Gauss-Newton stage is one
+ * options for all (method NGF_METHOD_GN, u_init NULL; each pair's distance,
+ * NGF or SSD, from its descriptor): every Gauss-Newton stage is one
  * batched launch sequence over the pairs still iterating, each PCG solve one
  * captured CUDA graph (when opts->use_graph), each Armijo trial one batched
  * objective over the pairs still searching.  Each pair takes exactly the
