@@ -363,7 +363,7 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     p->img_blocks = (int)p->g0.tiles();
     p->diag_blocks = (int)p->g1.tiles();
     p->node_blocks = grid_for(3 * p->N, sms);   // element-wise vector kernels (float4 bodies)
-    p->node1_blocks = grid_for(p->N, 16 * sms);     // one thread per node
+    p->node1_blocks = grid_for(p->N, 4 * sms);      // one thread per node
     p->dpart_len = 2 * (size_t)std::max({p->img_blocks, p->diag_blocks, p->node_blocks, p->node1_blocks, 8 * sms});
     NGF_CU(p, dev_alloc((void**)&p->dsc, 16 * sizeof(double), p->stream), "allocate scalars");
     NGF_CU(p, cudaMemsetAsync(p->dsc, 0, 16 * sizeof(double), p->stream), "clear scalars");
