@@ -58,6 +58,48 @@ using namespace ngf;
         if (_s != NGF_OK) return _s; \
     } while (0)
 
+// Armijo backtracking (Sec. 2.3): the first eta in 1, 1/2, 1/4, ... (at
+// most ls_max) with J(u + eta s) <= J0 + c1 eta gs.  On levels of up to 2^21
+// voxels a host round trip costs more than an objective pass, so four trial
+// points are evaluated per round trip (each into its own float64 slots,
+// dsc[16..23]); the decision, the accepted point and the trial count are
+// those of evaluating them one by one.  On return ut = u + eta s.
+static ngf_status armijo(Plan* p, const ngf_level_desc& d, const ngf_options* o, const float* R, const float* T,
+                         const float* u, const float* s, float* ut, double J0, double gs, double* dsc,
+                         ngf_report& r, bool& accepted) {
+    cudaStream_t stream = p->stream;
+    const long long n = 3 * p->N;
+    const dim3 gv(p->node_blocks), blk(NT);
+    const int K = (p->M <= (1LL << 21)) ? 4 : 1;
+    accepted = false;
+    double eta = 1.0;
+    int t = 0;
+    while (t < o->ls_max && !accepted) {
+        const int k = std::min(K, o->ls_max - t);
+        double e = eta;
+        for (int j = 0; j < k; ++j, e *= 0.5) {
+            DRV_CU(launch(k_axpy, gv, blk, 0, stream, n, (float)e, u, s, ut), "k_axpy");
+            DRV_TRY(objective_impl(p, R, T, ut, dsc + 16 + 2 * j, dsc + 17 + 2 * j));
+        }
+        double h[8];
+        DRV_CU(cudaMemcpyAsync(h, dsc + 16, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
+        DRV_CU(cudaStreamSynchronize(stream), "sync");
+        int j = 0;
+        for (; j < k; ++j) {
+            r.ls_trials++;
+            if (h[2 * j] + d.alpha * h[2 * j + 1] <= J0 + o->armijo_c1 * eta * gs) {
+                accepted = true;
+                break;
+            }
+            eta *= 0.5;
+        }
+        t += k;
+        if (accepted && j != k - 1)  // ut holds the round's last point
+            DRV_CU(launch(k_axpy, gv, blk, 0, stream, n, (float)eta, u, s, ut), "k_axpy");
+    }
+    return NGF_OK;
+}
+
 // L-BFGS on one level (Sec. 2.3.2): two-loop recursion with H0 = alpha
 // grad^2 S + gamma I (ngf_h0_solve), the Armijo rule of the Gauss-Newton
 // level, pairs (s, y) = (u_{k+1} - u_k, g_{k+1} - g_k) kept when s^T y > 0
@@ -133,21 +175,8 @@ static ngf_status lbfgs_level(Plan* p, const ngf_level_desc& d, const ngf_option
             DRV_CU(launch(k_scale, gv, blk, 0, stream, n, -1.0f, (const float*)g, dir), "k_scale");
             gs = -gg;
         }
-        double eta = 1.0;
         bool accepted = false;
-        for (int t = 0; t < o->ls_max; ++t) {
-            DRV_CU(launch(k_axpy, gv, blk, 0, stream, n, (float)eta, (const float*)u, (const float*)dir, ut),
-                   "k_axpy");
-            DRV_TRY(objective_impl(p, R, T, ut, dsc, dsc + 1));
-            DRV_CU(cudaMemcpyAsync(h, dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
-            DRV_CU(cudaStreamSynchronize(stream), "sync");
-            r.ls_trials++;
-            if (h[0] + d.alpha * h[1] <= J0 + o->armijo_c1 * eta * gs) {
-                accepted = true;
-                break;
-            }
-            eta *= 0.5;
-        }
+        DRV_TRY(armijo(p, d, o, R, T, u, dir, ut, J0, gs, dsc, r, accepted));
         if (!accepted) {
             r.ls_fail++;
             r.status = NGF_ELINESEARCH;
@@ -363,22 +392,8 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
                        "k_scale");
                 gs = -gg;
             }
-            double eta = 1.0;
             bool accepted = false;
-            for (int t = 0; t < o->ls_max; ++t) {
-                DRV_CU(launch(k_axpy, dim3(p->node_blocks), dim3(NT), 0, stream, n, (float)eta, (const float*)u,
-                              (const float*)s, ut),
-                       "k_axpy");
-                DRV_TRY(objective_impl(p, Rl[l], Tl[l], ut, dsc, dsc + 1));
-                DRV_CU(cudaMemcpyAsync(h, dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream), "read J");
-                DRV_CU(cudaStreamSynchronize(stream), "sync");
-                r.ls_trials++;
-                if (h[0] + d.alpha * h[1] <= J0 + o->armijo_c1 * eta * gs) {
-                    accepted = true;
-                    break;
-                }
-                eta *= 0.5;
-            }
+            DRV_TRY(armijo(p, d, o, Rl[l], Tl[l], u, s, ut, J0, gs, dsc, r, accepted));
             if (!accepted) {
                 r.ls_fail++;
                 r.status = NGF_ELINESEARCH;
