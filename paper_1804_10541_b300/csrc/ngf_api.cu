@@ -284,14 +284,15 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
 
     // z-chunking: k chunks per column of tiles, chosen to minimise
     // (rounds of 2 CTAs per SM) x (planes marched per chunk, 5 of them fill
-    // and drain), with at least 8 planes per chunk
+    // and drain); small levels get short chunks, since a CTA's march over
+    // its planes is sequential
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long txy = (long long)((p->m[0] + TX - 1) / TX) * ((p->m[1] + TY - 1) / TY);
     const long long slots = 2LL * sms;
     long long best_k = 1, best_cost = LLONG_MAX;
-    for (long long k = 1; k <= std::max<long long>(1, std::min<long long>(p->m[2] / 8, 256)); ++k) {
+    for (long long k = 1; k <= std::min<long long>(p->m[2], 1024); ++k) {
         const long long zc = (p->m[2] + k - 1) / k;
         const long long chunks = (p->m[2] + zc - 1) / zc;
         const long long cost = ((txy * chunks + slots - 1) / slots) * (zc + 5);
@@ -300,7 +301,7 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
             best_k = k;
         }
     }
-    p->zc = (int)std::max<long long>(std::min<long long>(8, p->m[2]), (p->m[2] + best_k - 1) / best_k);
+    p->zc = (int)((p->m[2] + best_k - 1) / best_k);
     if (zc_req > 0) p->zc = std::min(zc_req, p->m[2]);
 
     std::vector<int> f[3];
