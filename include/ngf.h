@@ -85,6 +85,11 @@ typedef struct ngf_plan ngf_plan;
  * buffers) on the current device and binds the plan to cuda_stream
  * (cudaStream_t; NULL = legacy default stream). */
 ngf_status ngf_plan_create(ngf_plan** plan, const ngf_level_desc* desc, void* cuda_stream);
+/* As ngf_plan_create with a given z-chunk length of the image-pass tiles
+ * (32 x 16 x zc voxels, capped by m[2]; 0 = the default model).  The tile
+ * geometry fixes the summation order of the transposed conversion, so plans
+ * (or batches) with the same zc give bitwise equal results. */
+ngf_status ngf_plan_create_ex(ngf_plan** plan, const ngf_level_desc* desc, int32_t zc, void* cuda_stream);
 ngf_status ngf_plan_destroy(ngf_plan* plan);
 ngf_status ngf_plan_set_stream(ngf_plan* plan, void* cuda_stream);
 /* Message of the last failure of this plan (plan == NULL: of the last failed
@@ -196,6 +201,8 @@ typedef struct {
     int32_t lbfgs_memory; /* stored (s, y) pairs, >= 1                          */
     double  lbfgs_gamma;  /* H0 = alpha grad^2 S + gamma I; <= 0: the mean of
                              the Gauss-Newton diagonal at each level's start   */
+    int32_t zc;           /* z-chunk length of every level's plans; 0 = the
+                             default (per plan; per batch in register_batch)  */
 } ngf_options;
 enum { NGF_METHOD_GN = 0, NGF_METHOD_LBFGS = 1 };
 

@@ -635,6 +635,11 @@ ngf_status ngf_plan_create(ngf_plan** out, const ngf_level_desc* desc, void* cud
     return plan_create(out, desc, (cudaStream_t)cuda_stream, 0);
 }
 
+ngf_status ngf_plan_create_ex(ngf_plan** out, const ngf_level_desc* desc, int32_t zc, void* cuda_stream) {
+    if (zc < 0) return set_error(nullptr, NGF_EINVAL, "zc must be >= 0");
+    return plan_create(out, desc, (cudaStream_t)cuda_stream, zc);
+}
+
 ngf_status ngf_plan_destroy(ngf_plan* plan) {
     if (!plan) return NGF_OK;
     free_plan(&plan->impl);

@@ -131,6 +131,30 @@ static void tile_items(const Batch& b, int p0, int p1, bool halo1, int want_span
     for (auto& e : it) out.push_back(e.second);
 }
 
+// One z-chunk length for all pairs (capped by each pair's depth), chosen to
+// minimise the persistent queue's time: the larger of (all items' marched
+// planes / slots of 2 CTAs per SM) and the longest item (zc + 5 planes).
+static int batch_zc(const ngf_level_desc* descs, int np, int sms) {
+    int best = 1;
+    double best_cost = 1e300;
+    for (int zc : {1, 2, 4, 8, 16, 24, 32, 48, 64, 96, 128, 192, 256}) {
+        double work = 0.0;
+        int longest = 0;
+        for (int k = 0; k < np; ++k) {
+            const int m2 = descs[k].m[2], z = std::min(zc, m2);
+            const long long tiles = (long long)((descs[k].m[0] + TX - 1) / TX) * ((descs[k].m[1] + TY - 1) / TY);
+            work += (double)tiles * ((m2 + z - 1) / z) * (z + 5);
+            longest = std::max(longest, z + 5);
+        }
+        const double cost = std::max(work / (2.0 * sms), (double)longest);
+        if (cost < best_cost) {
+            best_cost = cost;
+            best = zc;
+        }
+    }
+    return best;
+}
+
 static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int zc, cudaStream_t stream) {
     b->clear_plans();
     b->np = np;
@@ -140,6 +164,7 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (zc == 0) zc = batch_zc(descs, np, b->sms);
     for (int k = 0; k < np; ++k) {
         ngf_plan* pl = nullptr;
         const ngf_status s = plan_create(&pl, &descs[k], stream, zc);
@@ -635,7 +660,7 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
         prev_off = off;
 
         Batch b;
-        B_TRY(build_batch(&b, np, D.data(), 0, stream));
+        B_TRY(build_batch(&b, np, D.data(), o->zc, stream));
         auto seg = [&](float* base, int k) { return base + off[k]; };
         if (autotune) {
             B_CU(cudaMemsetAsync(d, 0, total * sizeof(float), stream), "zero d");
@@ -885,6 +910,7 @@ extern "C" ngf_status register_batch(int32_t npairs, const ngf_level_desc* fines
     if (o->u_init) return set_error(nullptr, NGF_EINVAL, "u_init is not supported by the batched registration");
     if (o->method != NGF_METHOD_GN)
         return set_error(nullptr, NGF_EINVAL, "the batched registration runs Gauss-Newton only");
+    if (o->zc < 0) return set_error(nullptr, NGF_EINVAL, "zc must be >= 0");
     for (int k = 0; k < npairs; ++k)
         for (const void* ptr : {(const void*)R[k], (const void*)T[k], (const void*)u_out[k]})
             if (!is_device_ptr(ptr))

@@ -202,6 +202,7 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
     if (o->levels < 1 || o->levels > 16) return set_error(nullptr, NGF_EINVAL, "levels must be in [1, 16]");
     if (o->gn_iters < 0 || o->pcg_iters < 0 || o->ls_max < 1)
         return set_error(nullptr, NGF_EINVAL, "gn_iters, pcg_iters >= 0 and ls_max >= 1 required");
+    if (o->zc < 0) return set_error(nullptr, NGF_EINVAL, "zc must be >= 0");
     if (o->method != NGF_METHOD_GN && o->method != NGF_METHOD_LBFGS)
         return set_error(nullptr, NGF_EINVAL, "method must be NGF_METHOD_GN or NGF_METHOD_LBFGS");
     const bool lbfgs = o->method == NGF_METHOD_LBFGS;
@@ -348,7 +349,7 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
             DRV_CU(cudaStreamSynchronize(stream), "sync");
         }
         PlanGuard pg;
-        DRV_TRY(ngf_plan_create(&pg.p, &d, stream));
+        DRV_TRY(plan_create(&pg.p, &d, stream, o->zc));
         Plan* p = &pg.p->impl;
         ngf_pcg_state st;
         st.x = bx.as<float>();

@@ -25,7 +25,7 @@ EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_la
            "ngf_objective_noalloc", "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count",
            "ngf_batch_create", "ngf_batch_destroy", "ngf_batch_objective", "ngf_batch_gradient",
            "ngf_batch_hessvec", "ngf_batch_diagonal", "ngf_batch_autotune", "ngf_batch_zc", "register_batch",
-           "ngf_h0_solve"]
+           "ngf_h0_solve", "ngf_plan_create_ex"]
 NGF_METHOD_GN, NGF_METHOD_LBFGS = 0, 1
 
 
@@ -50,7 +50,7 @@ class Options(C.Structure):
     _fields_ = [("levels", C.c_int32), ("gn_iters", C.c_int32), ("pcg_iters", C.c_int32), ("ls_max", C.c_int32),
                 ("armijo_c1", C.c_double), ("pcg_rtol", C.c_double), ("start_level", C.c_int32),
                 ("u_init", C.c_void_p), ("use_graph", C.c_int32), ("method", C.c_int32),
-                ("lbfgs_memory", C.c_int32), ("lbfgs_gamma", C.c_double)]
+                ("lbfgs_memory", C.c_int32), ("lbfgs_gamma", C.c_double), ("zc", C.c_int32)]
 
 
 class Report(C.Structure):
@@ -96,6 +96,7 @@ def declare(lib):
         "ngf_batch_autotune": [P, VP, VP, VP, VP, VP, C.POINTER(I32), D],
         "register_batch": [I32, C.POINTER(LevelDesc), C.POINTER(Options), VP, VP, VP, C.POINTER(Report), I32, VP],
         "ngf_h0_solve": [P, C.c_double, VP, VP],
+        "ngf_plan_create_ex": [C.POINTER(C.c_void_p), C.POINTER(LevelDesc), I32, VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -161,6 +162,12 @@ def level_desc(m, h, n, alpha=1.0, tau=0.1, rho=0.1, distance=NGF_DIST_NGF):
 def ngf_plan_create(desc, stream=None):
     h = C.c_void_p()
     _check(lib.ngf_plan_create(C.byref(h), C.byref(desc), _stream(stream)))
+    return h
+
+
+def ngf_plan_create_ex(desc, zc, stream=None):
+    h = C.c_void_p()
+    _check(lib.ngf_plan_create_ex(C.byref(h), C.byref(desc), int(zc), _stream(stream)))
     return h
 
 
@@ -245,13 +252,14 @@ def pcg_read(plan, st):
 
 
 def options(levels, gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rtol=0.0, u_init=None,
-            start_level=0, use_graph=True, method=NGF_METHOD_GN, lbfgs_memory=5, lbfgs_gamma=0.0):
+            start_level=0, use_graph=True, method=NGF_METHOD_GN, lbfgs_memory=5, lbfgs_gamma=0.0, zc=0):
     o = Options()
     o.levels, o.gn_iters, o.pcg_iters, o.ls_max = levels, gn_iters, pcg_iters, ls_max
     o.armijo_c1, o.pcg_rtol, o.start_level = armijo_c1, pcg_rtol, start_level
     o.u_init = _ptr(u_init)
     o.use_graph = 1 if use_graph else 0
     o.method, o.lbfgs_memory, o.lbfgs_gamma = int(method), int(lbfgs_memory), float(lbfgs_gamma)
+    o.zc = int(zc)
     return o
 
 
@@ -370,9 +378,9 @@ class Batch:
 class Plan:
     """Owning wrapper of an ngf_plan."""
 
-    def __init__(self, desc, stream=None):
+    def __init__(self, desc, stream=None, zc=0):
         self.desc = desc
-        self.handle = ngf_plan_create(desc, stream)
+        self.handle = ngf_plan_create_ex(desc, zc, stream) if zc else ngf_plan_create(desc, stream)
 
     def close(self):
         if self.handle:

@@ -1,9 +1,10 @@
 """Batched form: many independent pairs of uneven size in one launch per stage.
 
-Each pair's result from the batched entry points must equal, bit for bit,
-what its own plan gives (same kernels, same tile geometry, same reduction
-order); the batched registration must take each pair's decisions exactly as
-register_multilevel does on that pair alone.  The batched Hessian-vector
+With the same z-chunk length (ZC) on both sides, each pair's result from the
+batched entry points must equal, bit for bit, what its own plan gives (same
+kernels, same tile geometry, same reduction order); the batched registration
+must take each pair's decisions exactly as register_multilevel does on that
+pair alone.  The batched Hessian-vector
 product and gradient are also compared with the FP64 oracle directly.
 """
 import numpy as np
@@ -13,6 +14,8 @@ import torch
 pytestmark = pytest.mark.gpu
 
 import gpu_util as G  # noqa: E402
+
+ZC = 8  # common tile depth of the bitwise comparisons
 
 # uneven sizes, ragged tiles, several z-chunks; the last pair has one voxel
 # per cell in x (four-node span in the diagonal kernel)
@@ -40,14 +43,14 @@ def test_batched_operators_equal_single_plans(ngf):
     cs = _cases()
     R, T, U, P = [c.R for c in cs], [c.T for c in cs], [c.u for c in cs], [c.p for c in cs]
     q, g, dg = [c.empty() for c in cs], [c.empty() for c in cs], [c.empty() for c in cs]
-    with ngf.Batch([c.desc for c in cs]) as b:
+    with ngf.Batch([c.desc for c in cs], ZC) as b:
         ngf.ngf_batch_hessvec(b.handle, R, T, U, P, q)
         ngf.ngf_batch_gradient(b.handle, R, T, U, g)
         ngf.ngf_batch_diagonal(b.handle, R, T, U, dg)
         Db, Sb = ngf.ngf_batch_objective(b.handle, R, T, U)
         torch.cuda.synchronize()
     for k, c in enumerate(cs):
-        with ngf.Plan(c.desc) as pl:
+        with ngf.Plan(c.desc, zc=ZC) as pl:
             q1, g1, d1 = c.empty(), c.empty(), c.empty()
             ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
             ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g1, want_scalars=False)
@@ -104,7 +107,7 @@ def _blob_batch(sizes):
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_register_batch_equals_per_pair_registration(ngf, use_graph):
     pairs = _blob_batch([24, 33, 40, 29])
-    opts = ngf.options(2, gn_iters=4, pcg_iters=8, use_graph=use_graph)
+    opts = ngf.options(2, gn_iters=4, pcg_iters=8, use_graph=use_graph, zc=ZC)
     ub = [torch.zeros(3 * d.n[0] * d.n[1] * d.n[2], device="cuda") for _, _, d in pairs]
     # graphs need a stream other than the legacy default stream
     stream = torch.cuda.Stream() if use_graph else None
@@ -151,13 +154,13 @@ def test_batch_larger_than_one_parameter_table(ngf):
                    0.2 * torch.randn(3 * N, generator=g), torch.randn(3 * N, generator=g))
         cs.append(c)
     q = [c.empty() for c in cs]
-    with ngf.Batch([c.desc for c in cs]) as b:
+    with ngf.Batch([c.desc for c in cs], ZC) as b:
         ngf.ngf_batch_hessvec(b.handle, [c.R for c in cs], [c.T for c in cs], [c.u for c in cs],
                               [c.p for c in cs], q)
         torch.cuda.synchronize()
     for k in (0, 64, 111, 112, 129):
         c = cs[k]
-        with ngf.Plan(c.desc) as pl:
+        with ngf.Plan(c.desc, zc=ZC) as pl:
             q1 = c.empty()
             ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
             torch.cuda.synchronize()
@@ -173,14 +176,14 @@ def test_mixed_ngf_ssd_batch_equals_single_plans(ngf):
         cs[k].desc = ngf.level_desc(cs[k].m, cs[k].h, cs[k].n, 0.7, 0.15, 0.25, distance=ngf.NGF_DIST_SSD)
     R, T, U, P = [c.R for c in cs], [c.T for c in cs], [c.u for c in cs], [c.p for c in cs]
     q, g, dg = [c.empty() for c in cs], [c.empty() for c in cs], [c.empty() for c in cs]
-    with ngf.Batch([c.desc for c in cs]) as b:
+    with ngf.Batch([c.desc for c in cs], ZC) as b:
         ngf.ngf_batch_hessvec(b.handle, R, T, U, P, q)
         ngf.ngf_batch_gradient(b.handle, R, T, U, g)
         ngf.ngf_batch_diagonal(b.handle, R, T, U, dg)
         Db, Sb = ngf.ngf_batch_objective(b.handle, R, T, U)
         torch.cuda.synchronize()
     for k, c in enumerate(cs):
-        with ngf.Plan(c.desc) as pl:
+        with ngf.Plan(c.desc, zc=ZC) as pl:
             q1, g1, d1 = c.empty(), c.empty(), c.empty()
             ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q1)
             ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g1, want_scalars=False)
@@ -192,7 +195,7 @@ def test_mixed_ngf_ssd_batch_equals_single_plans(ngf):
     pairs = _blob_batch([24, 29])
     descs = [pairs[0][2], ngf.level_desc((29, 29, 29), (1.0, 1.0, 1.0), (15, 15, 15), 1.0, 0.1, 0.1,
                                          distance=ngf.NGF_DIST_SSD)]
-    opts = ngf.options(2, gn_iters=3, pcg_iters=6)
+    opts = ngf.options(2, gn_iters=3, pcg_iters=6, zc=ZC)
     ub = [torch.zeros(3 * d.n[0] * d.n[1] * d.n[2], device="cuda") for d in descs]
     reps = ngf.register_batch(descs, opts, [p[0] for p in pairs], [p[1] for p in pairs], ub)
     for k, d in enumerate(descs):
