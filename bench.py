@@ -561,7 +561,9 @@ def run_batch(args):
             "value": voxels / (batch_ms / 1e3) / 1e9, "unit": "Gvoxel/s", "steps": args.steps,
             "warmup": args.warmup, "batched_ms": batch_ms, "sequential_ms": seq_ms,
             "speedup_vs_sequential": seq_ms / batch_ms, "same_u_as_sequential": same_u,
-            "max_rel_J_diff_vs_sequential": j_rel, "total_voxels": total_vox,
+            "max_rel_J_diff_vs_sequential": j_rel,
+            "tile_depth_note": "batched and sequential runs each use their default z-chunk model; "
+                               "with one common zc their results are bitwise equal", "total_voxels": total_vox,
             "autotuned_registration_ms": auto_ms,
             "autotuned_max_rel_J_diff_vs_sequential": max(abs(a.J - b.J) / abs(b.J) for a, b in zip(reps_a, reps1)),
             "batched_hessvec_ms": {"default_zc": ms_default, "autotuned": ms_tuned, "zc": zc},
