@@ -25,7 +25,7 @@ EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_la
            "ngf_objective_noalloc", "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count",
            "ngf_batch_create", "ngf_batch_destroy", "ngf_batch_objective", "ngf_batch_gradient",
            "ngf_batch_hessvec", "ngf_batch_diagonal", "ngf_batch_autotune", "ngf_batch_zc", "register_batch",
-           "ngf_h0_solve", "ngf_plan_create_ex"]
+           "ngf_h0_solve", "ngf_plan_create_ex", "ngf_conv3d_fwd", "ngf_conv3d_check"]
 NGF_METHOD_GN, NGF_METHOD_LBFGS = 0, 1
 
 
@@ -97,6 +97,8 @@ def declare(lib):
         "register_batch": [I32, C.POINTER(LevelDesc), C.POINTER(Options), VP, VP, VP, C.POINTER(Report), I32, VP],
         "ngf_h0_solve": [P, C.c_double, VP, VP],
         "ngf_plan_create_ex": [C.POINTER(C.c_void_p), C.POINTER(LevelDesc), I32, VP],
+        "ngf_conv3d_fwd": [VP, VP, VP, VP, I32, I32, I32, I32, I32, I32, I32, VP],
+        "ngf_conv3d_check": [VP],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -169,6 +171,24 @@ def ngf_plan_create_ex(desc, zc, stream=None):
     h = C.c_void_p()
     _check(lib.ngf_plan_create_ex(C.byref(h), C.byref(desc), int(zc), _stream(stream)))
     return h
+
+
+def ngf_conv3d_fwd(x, w, bias, y, relu=False, stream=None):
+    """3x3x3 convolution on the tensor cores: x [B][D][H][W][Cin] bf16,
+    w [Cout][3][3][3][Cin] bf16, bias [Cout] float or None, y
+    [B][D][H][W][Cout] float (all device, contiguous)."""
+    B, D, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    _check(lib.ngf_conv3d_fwd(_ptr(x), _ptr(w), _ptr(bias) if bias is not None else None, _ptr(y),
+                              B, D, H, W, Cin, Cout, 1 if relu else 0, _stream(stream)))
+
+
+def ngf_conv3d_check(stream=None):
+    """Number of convolution waits that gave up since the last call."""
+    n = lib.ngf_conv3d_check(_stream(stream))
+    if n < 0:
+        _check(n)
+    return n
 
 
 def ngf_plan_destroy(plan):
