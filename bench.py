@@ -614,6 +614,73 @@ def run_thorax(args):
     return 0
 
 
+def run_conv3d(args):
+    """Tensor-core 3x3x3 convolution (learned-initializer building block) on
+    the layer shapes of a 4-level encoder at 128^3 (16 -> 128 channels): per
+    layer the median of `steps` single-launch CUDA-event timings, L2 flushed
+    before each, and sampled outputs checked against the FP64 oracle."""
+    import numpy as np
+    import torch
+    from paper_1804_10541_b300 import ngf
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import cnn_oracle as CO
+    dev = torch.device("cuda", 0)
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        peak = json.load(f)["bf16_tflops"]
+    flush = torch.empty(64 * 1024 * 1024, device=dev, dtype=torch.float32)
+    gen = torch.Generator().manual_seed(41)
+    layers = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    launches0 = ngf.ngf_launch_count()
+    for (S, ci, co) in [(128, 16, 16), (64, 32, 32), (32, 64, 64), (16, 128, 128), (64, 32, 256)]:
+        x = torch.randn(1, S, S, S, ci, generator=gen).to(torch.bfloat16)
+        w = (torch.randn(co, 3, 3, 3, ci, generator=gen) / (27 * ci) ** 0.5).to(torch.bfloat16)
+        xd, wd = x.to(dev), w.to(dev)
+        y = torch.empty(1, S, S, S, co, device=dev)
+        for _ in range(max(3, args.warmup)):
+            ngf.ngf_conv3d_fwd(xd, wd, None, y)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            ngf.ngf_conv3d_fwd(xd, wd, None, y)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        assert ngf.ngf_conv3d_check() == 0
+        ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        flop = 2.0 * S ** 3 * 27 * ci * co
+        # sampled outputs against the oracle (3x3x3 neighbourhood crops)
+        xp = np.pad(x.float().numpy()[0], ((1, 1), (1, 1), (1, 1), (0, 0)))
+        wf = w.float().numpy()
+        yc = y.cpu().numpy()[0]
+        rng = np.random.default_rng(S + ci + co)
+        worst = 0.0
+        for _ in range(16):
+            z, yy, xx = (int(v) for v in rng.integers(0, S, 3))
+            crop = xp[z:z + 3, yy:yy + 3, xx:xx + 3][None]
+            yo = CO.conv3d(crop, wf)[0, 1, 1, 1]
+            scale = CO.conv3d_abs(crop, wf)[0, 1, 1, 1]
+            worst = max(worst, float(np.max(np.abs(yc[z, yy, xx] - yo) / scale)))
+        layers.append({"shape": f"{S}^3 {ci}->{co}", "ms": ms, "gflop": flop / 1e9, "tflops": flop / ms / 1e9,
+                       "frac_of_measured_bf16": flop / ms / 1e9 / peak,
+                       "max_err_over_abs_sum_sampled": worst})
+    launches = ngf.ngf_launch_count() - launches0
+    clocks = sampler.stop()
+    total_flop = sum(l["gflop"] * 1e9 for l in layers)
+    total_ms = sum(l["ms"] for l in layers)
+    line = {"workload": "conv3d: 3x3x3 bf16 convolution layers of a 4-level encoder at 128^3, fp32 out",
+            "metric": "conv3d TFLOP/s", "value": total_flop / total_ms / 1e9, "unit": "TFLOP/s",
+            "steps": args.steps, "warmup": args.warmup, "layers": layers,
+            "roofline": {"bound": "tensor", "achieved": total_flop / total_ms / 1e9, "peak": peak,
+                         "unit": "TFLOP/s", "frac": total_flop / total_ms / 1e9 / peak,
+                         "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)"},
+            "gpu_launches": int(launches), "clocks": clocks, "l2": "flushed before every launch (256 MB write)",
+            "dtype": "bf16 x bf16 -> f32", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -624,9 +691,9 @@ def main():
     ap.add_argument("--kernel-case", default=None, help="profile driver: gn_hessvec only on this workload")
     ap.add_argument("--calls", type=int, default=3)
     ap.add_argument("--distance", default="ngf", choices=["ngf", "ssd"], help="distance of --kernel-case")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_64", "thorax_abd"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_64", "thorax_abd", "conv3d"],
                     help="batch_64: the batched form on 64 uneven pairs; thorax_abd: the 512x512x900 "
-                         "registration (each its own JSON line)")
+                         "registration; conv3d: the tensor-core convolution layers (each its own JSON line)")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
@@ -635,6 +702,8 @@ def main():
         return run_batch_sharded(args, ws, rank) if ws > 1 else run_batch(args)
     if args.workload == "thorax_abd":
         return run_thorax(args)
+    if args.workload == "conv3d":
+        return run_conv3d(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

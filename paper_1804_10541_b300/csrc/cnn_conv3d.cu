@@ -5,10 +5,11 @@
 // consecutive voxels and all Cout channels: one tcgen05.mma of shape
 // M=128 x N=Cout x K=16 per 16 channels of a tap, FP32 accumulator in tensor
 // memory (Cout columns x 128 lanes).  The reduction runs in stages of one tap
-// x up to 64 channels, double-buffered in shared memory: the 128 threads
-// gather the next stage (plain 16-byte loads; zero outside the volume) while
-// the tensor core works on the current one, and an mbarrier signalled by
-// tcgen05.commit tells them when a buffer may be overwritten.
+// x up to 64 channels through 3-6 shared-memory buffers: the 128 threads
+// start asynchronous 16-byte copies (cp.async, zero fill outside the volume)
+// of the stages ahead while the tensor core works on the current one, and
+// one mbarrier per buffer, signalled by tcgen05.commit, tells them when a
+// buffer may be refilled.
 //
 // Shared-memory operand layout (K-major, no swizzle): 8x8 core matrices of
 // 16-byte rows; within one K=16 slab the two K-halves of a row group are
@@ -103,7 +104,12 @@ struct ConvArgs {
     long long V;      // B*D*H*W
     int kst;          // channels per stage
     int cchunks;      // stages per tap
+    int tps;          // taps per stage: 1 (4 taps of 16 channels per stage
+                      // measured slower: fewer CTAs fit on an SM)
+    int nbuf;         // operand buffers in shared memory (3 .. CONV_MAXBUF)
 };
+
+constexpr int CONV_MAXBUF = 6;
 
 // Byte offset of 16-byte chunk q (channels 8q..8q+7 of the stage) of row r
 // in a K-major, no-swizzle operand with `rows` rows.
@@ -111,14 +117,24 @@ __device__ __forceinline__ uint32_t operand_off(int r, int q, int rows) {
     return (uint32_t)((q >> 1) * (rows / 8) * 256 + (r >> 3) * 256 + (q & 1) * 128 + (r & 7) * 16);
 }
 
+// 16-byte asynchronous copy global -> shared; src_bytes = 0 writes zeros
+// and reads nothing.
+__device__ __forceinline__ void cp16_ca(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp16_cg(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
 __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
     NGF_DYNAMIC_SMEM(smem);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t a_bytes = CONV_M * a.kst * 2, b_bytes = a.cout * a.kst * 2;
-    unsigned char* bufA[2] = {smem, smem + a_bytes};
-    unsigned char* bufB[2] = {smem + 2 * a_bytes, smem + 2 * a_bytes + b_bytes};
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * a_bytes + 2 * b_bytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    const int nbuf = a.nbuf;
+    const int kstage = a.tps * a.kst;  // reduction length of one stage
+    const uint32_t a_bytes = CONV_M * kstage * 2, b_bytes = a.cout * kstage * 2;
+    const uint32_t sA = smem_addr(smem), sB = sA + nbuf * a_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + nbuf * (a_bytes + b_bytes));
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + CONV_MAXBUF);
     uint32_t ncols = 32;
     while ((int)ncols < a.cout) ncols <<= 1;
 
@@ -129,8 +145,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(smem_addr(&bars[0]), 1);
-        mbar_init(smem_addr(&bars[1]), 1);
+        for (int i = 0; i < nbuf; ++i) mbar_init(smem_addr(&bars[i]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -149,43 +164,71 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
         vy = (int)(t % a.H); t /= a.H;
         vz = (int)(t % a.D); vb = t / a.D;
     }
-    const int qn = a.kst / 8;  // 16-byte chunks per row per stage
-    const int stages = 27 * a.cchunks;
+    const int qn = a.kst / 8;  // 16-byte chunks per row per tap of a stage
+    const int stages = ((27 + a.tps - 1) / a.tps) * a.cchunks;
     const uint32_t idesc = instr_desc(CONV_M, a.cout);
     bool failed = false;
 
-    for (int s = 0; s < stages; ++s) {
-        const int buf = s & 1;
-        if (s >= 2) {
-            // the MMAs of stage s-2 read this buffer: wait for their commit
-            const bool ok = mbar_wait(smem_addr(&bars[buf]), (uint32_t)(((s - 2) >> 1) & 1));
-            if (__syncthreads_or(!ok)) { failed = true; break; }
-        }
-        const int tap = s / a.cchunks, c0 = (s % a.cchunks) * a.kst;
-        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        // A: this thread's row, channels c0..c0+kst-1 of the shifted voxel
-        {
-            const int xx = vx + dx, yy = vy + dy, zz = vz + dz;
+    // start the copies of stage t into buffer t % nbuf
+    auto load_stage = [&](int t) {
+        const int buf = t % nbuf;
+        const int tap0 = (t / a.cchunks) * a.tps, c0 = (t % a.cchunks) * a.kst;
+        const int ntap = min(a.tps, 27 - tap0);
+        // A: this thread's row, channels c0..c0+kst-1 of each shifted voxel
+        // (8 lanes of a shared-memory phase write 8 rows of one core matrix)
+        const uint32_t dA = sA + buf * a_bytes;
+        for (int i = 0; i < ntap; ++i) {
+            const int tap = tap0 + i;
+            const int xx = vx + tap % 3 - 1, yy = vy + (tap / 3) % 3 - 1, zz = vz + tap / 9 - 1;
             const bool in = row_ok && xx >= 0 && xx < a.W && yy >= 0 && yy < a.H && zz >= 0 && zz < a.D;
             const uint4* src = a.x;
             if (in) src += ((((vb * a.D + zz) * a.H + yy) * a.W + xx) * a.cin + c0) / 8;
-            for (int q = 0; q < qn; ++q) {
-                uint4 val = in ? src[q] : make_uint4(0u, 0u, 0u, 0u);
-                *reinterpret_cast<uint4*>(bufA[buf] + operand_off(tid, q, CONV_M)) = val;
-            }
+            for (int q = 0; q < qn; ++q)
+                cp16_ca(dA + operand_off(tid, i * qn + q, CONV_M), in ? src + q : a.x, in ? 16u : 0u);
         }
-        // B: all Cout rows, same channels of the same tap
-        for (int idx = tid; idx < a.cout * qn; idx += CONV_THREADS) {
-            const int n = idx / qn, q = idx - n * qn;
-            const uint4 val = a.w[(((long long)n * 27 + tap) * a.cin + c0) / 8 + q];
-            *reinterpret_cast<uint4*>(bufB[buf] + operand_off(n, q, a.cout)) = val;
+        // B: all Cout rows, the same channels of the same taps
+        const uint32_t dB = sB + buf * b_bytes;
+        const int per_row = ntap * qn;
+        for (int idx = tid; idx < a.cout * per_row; idx += CONV_THREADS) {
+            const int n = idx / per_row, r = idx - n * per_row, i = r / qn, q = r - i * qn;
+            cp16_cg(dB + operand_off(n, r, a.cout),
+                    a.w + (((long long)n * 27 + tap0 + i) * a.cin + c0) / 8 + q);
+        }
+    };
+
+    // copies run nbuf-2 stages ahead of the tensor core; a buffer is reused
+    // once the MMAs of the stage two before the current one have completed
+    const int ahead = nbuf - 2;
+    for (int t = 0; t < ahead && t < stages; ++t) {
+        load_stage(t);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int s = 0; s < stages; ++s) {
+        const int t = s + ahead;
+        if (t < stages) {
+            if (t >= nbuf) {
+                // buffer t % nbuf was read by the MMAs of stage t - nbuf = s - 2
+                const bool ok = mbar_wait(smem_addr(&bars[t % nbuf]), (uint32_t)(((t - nbuf) / nbuf) & 1));
+                if (__syncthreads_or(!ok)) { failed = true; break; }
+            }
+            load_stage(t);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // all groups but the newest `ahead` ones are complete: stage s is in
+        switch (ahead) {
+            case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+            case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+            case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+            default: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t abase = smem_addr(bufA[buf]), bbase = smem_addr(bufB[buf]);
-            for (int j = 0; j < a.kst / 16; ++j) {
+            const int buf = s % nbuf;
+            const uint32_t abase = sA + buf * a_bytes, bbase = sB + buf * b_bytes;
+            const int slabs = min(a.tps, 27 - (s / a.cchunks) * a.tps) * a.kst / 16;
+            for (int j = 0; j < slabs; ++j) {
                 const uint64_t ad = smem_desc(abase + j * (CONV_M / 8) * 256, 128, 256);
                 const uint64_t bd = smem_desc(bbase + j * (a.cout / 8) * 256, 128, 256);
                 mma_bf16(tmem, ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
@@ -193,12 +236,13 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
             mma_commit(smem_addr(&bars[buf]));
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 
     // wait for the last commit of each buffer (all MMAs complete)
     bool ok = !failed;
-    for (int s = stages - 2; s < stages && !failed; ++s) {
+    for (int s = stages - nbuf; s < stages && !failed; ++s) {
         if (s < 0) continue;
-        ok &= mbar_wait(smem_addr(&bars[s & 1]), (uint32_t)((s >> 1) & 1));
+        ok &= mbar_wait(smem_addr(&bars[s % nbuf]), (uint32_t)((s / nbuf) & 1));
     }
     if (__syncthreads_or(!ok)) failed = true;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -225,7 +269,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
         atomicAdd(&g_conv_timeouts, 1u);
         // give MMAs still in flight a bounded chance to finish before the
         // tensor memory is released
-        mbar_wait(smem_addr(&bars[(stages - 1) & 1]), (uint32_t)(((stages - 1) >> 1) & 1));
+        mbar_wait(smem_addr(&bars[(stages - 1) % nbuf]), (uint32_t)(((stages - 1) / nbuf) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -261,7 +305,11 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     a.V = V;
     a.kst = Cin <= CONV_KMAX ? Cin : CONV_KMAX;
     a.cchunks = Cin / a.kst;
-    size_t smem = 2 * (size_t)CONV_M * a.kst * 2 + 2 * (size_t)Cout * a.kst * 2 + 2 * sizeof(uint64_t) + 16;
+    a.tps = 1;
+    const size_t stage_bytes = ((size_t)CONV_M + Cout) * a.tps * a.kst * 2;
+    a.nbuf = CONV_MAXBUF;
+    while (a.nbuf > 3 && a.nbuf * stage_bytes > 112 * 1024) --a.nbuf;
+    size_t smem = a.nbuf * stage_bytes + CONV_MAXBUF * sizeof(uint64_t) + 16;
     // at most 512 / ncols CTAs per SM, so that every CTA's tensor-memory
     // allocation succeeds at once (228 KB of shared memory per SM, 1 KB of
     // it reserved per CTA)
@@ -272,7 +320,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     if (smem < smem_min) smem = smem_min;
     static bool attr_set = false;
     if (!attr_set) {
-        if (cudaFuncSetAttribute(k_conv3d_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024) !=
+        if (cudaFuncSetAttribute(k_conv3d_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
             cudaSuccess)
             return NGF_ECUDA;
         attr_set = true;
