@@ -279,6 +279,173 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
     }
 }
 
+// ---- brick form (Cin <= 64): the input tile is staged once ---------------
+//
+// A CTA owns an 8 (x) x 16 (y) x P (z) block of output voxels: P MMA row
+// tiles of 128 (row m = voxel (m & 7, m >> 3) of a plane), P accumulators of
+// ncols tensor-memory columns each.  The (8+2) x (16+2) x (P+2) input brick
+// with all Cin channels is copied to shared memory once, stored channel
+// group major ([Cin/8][z][y][x], 16 bytes per voxel and group), so that the
+// operand of tap (dz, dy, dx) is the brick itself at a start address moved
+// by (dz, dy, dx) voxels: rows of a core matrix are 8 consecutive x (16
+// bytes apart), 8-row groups are brick lines (stride 160 bytes), and the two
+// channel groups of a K=16 slab are one channel-group plane apart.  No input
+// voxel is gathered twice; only the weights stream, one tap per stage,
+// shared by the P planes.
+
+constexpr int BR_X = 10, BR_Y = 18;  // brick extent in x and y (tile + halo)
+
+struct BrickArgs {
+    const uint4* x;
+    const uint4* w;
+    const float* bias;
+    float* y;
+    int B, D, H, W, cin, cout, relu;
+    int P;            // output planes per CTA
+    int ncols;        // tensor-memory columns per accumulator
+    int nbuf;         // weight buffers (3 .. CONV_MAXBUF)
+    int tiles_x, tiles_y, tiles_z;
+};
+
+__global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a) {
+    NGF_DYNAMIC_SMEM(smem);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nbuf = a.nbuf, P = a.P, cg = a.cin / 8, qn = a.cin / 8;
+    const int nb = BR_X * BR_Y * (P + 2);           // brick voxels
+    const uint32_t brick_bytes = (uint32_t)cg * nb * 16, b_bytes = (uint32_t)a.cout * a.cin * 2;
+    const uint32_t sBr = smem_addr(smem), sB = sBr + brick_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + brick_bytes + nbuf * b_bytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + CONV_MAXBUF);
+    const uint32_t tcols = (uint32_t)(P * a.ncols);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < nbuf; ++i) mbar_init(smem_addr(&bars[i]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    int t = blockIdx.x;
+    const int tx = t % a.tiles_x; t /= a.tiles_x;
+    const int ty = t % a.tiles_y; t /= a.tiles_y;
+    const int tz = t % a.tiles_z;
+    const int b = t / a.tiles_z;
+    const int x0 = tx * 8, y0 = ty * 16, z0 = tz * P;
+
+    // the brick: one 16-byte copy per (voxel, channel group), channel group
+    // fastest across lanes (contiguous global reads), zero outside
+    for (int idx = tid; idx < cg * nb; idx += CONV_THREADS) {
+        const int g = idx % cg, v = idx / cg;
+        const int bx = v % BR_X, by = (v / BR_X) % BR_Y, bz = v / (BR_X * BR_Y);
+        const int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
+        const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H && gz >= 0 && gz < a.D;
+        const uint4* src = a.x;
+        if (in) src += ((((long long)b * a.D + gz) * a.H + gy) * a.W + gx) * (a.cin / 8) + g;
+        cp16_ca(sBr + (uint32_t)(g * nb + v) * 16, src, in ? 16u : 0u);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
+    // weights of tap s into buffer s % nbuf
+    auto load_w = [&](int s) {
+        const uint32_t dB = sB + (s % nbuf) * b_bytes;
+        for (int idx = tid; idx < a.cout * qn; idx += CONV_THREADS) {
+            const int n = idx / qn, q = idx - n * qn;
+            cp16_cg(dB + operand_off(n, q, a.cout), a.w + ((long long)n * 27 + s) * qn + q);
+        }
+    };
+    const int ahead = nbuf - 2;
+    for (int s = 0; s < ahead; ++s) {
+        load_w(s);
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const uint32_t idesc = instr_desc(CONV_M, a.cout);
+    const uint32_t lbo = (uint32_t)nb * 16;  // one channel group plane
+    bool failed = false;
+    for (int s = 0; s < 27; ++s) {
+        const int tn = s + ahead;
+        if (tn < 27) {
+            if (tn >= nbuf) {
+                const bool ok = mbar_wait(smem_addr(&bars[tn % nbuf]), (uint32_t)(((tn - nbuf) / nbuf) & 1));
+                if (__syncthreads_or(!ok)) { failed = true; break; }
+            }
+            load_w(tn);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        // the brick group and the groups of taps 0..s are complete
+        switch (ahead) {
+            case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+            case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+            case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+            default: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int dz = s / 9, dy = (s / 3) % 3, dx = s % 3;  // brick offsets 0..2
+            const uint32_t bbase = sB + (s % nbuf) * b_bytes;
+            for (int p = 0; p < P; ++p) {
+                const uint32_t abase = sBr + (uint32_t)(((p + dz) * BR_Y + dy) * BR_X + dx) * 16;
+                for (int j = 0; j < a.cin / 16; ++j) {
+                    const uint64_t ad = smem_desc(abase + 2 * j * lbo, lbo, BR_X * 16);
+                    const uint64_t bd = smem_desc(bbase + j * (a.cout / 8) * 256, 128, 256);
+                    mma_bf16(tmem + (uint32_t)(p * a.ncols), ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(smem_addr(&bars[s % nbuf]));
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+
+    bool ok = !failed;
+    for (int s = 27 - nbuf; s < 27 && !failed; ++s)
+        ok &= mbar_wait(smem_addr(&bars[s % nbuf]), (uint32_t)((s / nbuf) & 1));
+    if (__syncthreads_or(!ok)) failed = true;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+    if (!failed) {
+        const int m = warp * 32 + (tid & 31);
+        const int vx = x0 + (m & 7), vy = y0 + (m >> 3);
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        for (int p = 0; p < P; ++p) {
+            const int vz = z0 + p;
+            const bool row_ok = vx < a.W && vy < a.H && vz < a.D;
+            float* out = a.y + (row_ok ? ((((long long)b * a.D + vz) * a.H + vy) * a.W + vx) * a.cout : 0);
+            for (int c = 0; c < a.cout; c += 16) {
+                float r[16];
+                tmem_load16(tmem + lane_base + (uint32_t)(p * a.ncols + c), r);
+                if (row_ok) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float v = r[i] + (a.bias ? a.bias[c + i] : 0.0f);
+                        r[i] = (a.relu && v < 0.0f) ? 0.0f : v;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; i += 4)
+                        *reinterpret_cast<float4*>(out + c + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicAdd(&g_conv_timeouts, 1u);
+        mbar_wait(smem_addr(&bars[26 % nbuf]), (uint32_t)((26 / nbuf) & 1));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+    }
+}
+
 }  // namespace
 }  // namespace ngf
 
@@ -295,6 +462,53 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     if (V == 0) return NGF_OK;
     if (!x || !w || !y) return NGF_EINVAL;
     if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y) & 15u) return NGF_EINVAL;
+    int ncols = 32;
+    while (ncols < Cout) ncols <<= 1;
+    const size_t per_sm = 228 * 1024;
+    if (Cin <= CONV_KMAX) {
+        // brick form: P output planes per CTA, as many as tensor memory (two
+        // CTAs per SM) and about 110 KB of shared memory allow
+        BrickArgs br;
+        br.x = static_cast<const uint4*>(x);
+        br.w = static_cast<const uint4*>(w);
+        br.bias = bias;
+        br.y = y;
+        br.B = B; br.D = D; br.H = H; br.W = W;
+        br.cin = Cin; br.cout = Cout; br.relu = relu ? 1 : 0;
+        br.ncols = ncols;
+        const size_t wst = (size_t)Cout * Cin * 2;
+        br.P = 1;
+        br.nbuf = 3;
+        for (int p = 4; p >= 1; p >>= 1) {
+            if (p * ncols > 256 || (p > 1 && p > D)) continue;
+            const size_t brick = (size_t)(Cin / 8) * BR_X * BR_Y * (p + 2) * 16;
+            int nbf = CONV_MAXBUF;
+            while (nbf > 3 && brick + nbf * wst > 110 * 1024) --nbf;
+            if (brick + nbf * wst <= 110 * 1024 || p == 1) { br.P = p; br.nbuf = nbf; break; }
+        }
+        br.tiles_x = (W + 7) / 8;
+        br.tiles_y = (H + 15) / 16;
+        br.tiles_z = (D + br.P - 1) / br.P;
+        const size_t brick = (size_t)(Cin / 8) * BR_X * BR_Y * (br.P + 2) * 16;
+        size_t smem = brick + br.nbuf * wst + CONV_MAXBUF * sizeof(uint64_t) + 16;
+        // every resident CTA's tensor-memory allocation must fit at once
+        const size_t ctas = 512 / (br.P * ncols);
+        const size_t smem_min = per_sm / (ctas + 1) - 1024 + 16;
+        if (smem < smem_min) smem = smem_min;
+        const long long grid = (long long)br.tiles_x * br.tiles_y * br.tiles_z * B;
+        if (grid >= (1LL << 31) || smem > 200 * 1024) return NGF_EBOUNDS;
+        static bool battr = false;
+        if (!battr) {
+            if (cudaFuncSetAttribute(k_conv3d_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+                cudaSuccess)
+                return NGF_ECUDA;
+            battr = true;
+        }
+        if (launch(k_conv3d_brick, dim3((unsigned)grid), dim3(CONV_THREADS), smem,
+                   static_cast<cudaStream_t>(cuda_stream), br) != cudaSuccess)
+            return NGF_ECUDA;
+        return NGF_OK;
+    }
     ConvArgs a;
     a.x = static_cast<const uint4*>(x);
     a.w = static_cast<const uint4*>(w);
@@ -313,9 +527,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     // at most 512 / ncols CTAs per SM, so that every CTA's tensor-memory
     // allocation succeeds at once (228 KB of shared memory per SM, 1 KB of
     // it reserved per CTA)
-    int ncols = 32;
-    while (ncols < Cout) ncols <<= 1;
-    const size_t per_sm = 228 * 1024, ctas = 512 / ncols;
+    const size_t ctas = 512 / ncols;
     const size_t smem_min = per_sm / (ctas + 1) - 1024 + 16;
     if (smem < smem_min) smem = smem_min;
     static bool attr_set = false;
