@@ -107,6 +107,7 @@ struct ConvArgs {
     int tps;          // taps per stage: 1 (4 taps of 16 channels per stage
                       // measured slower: fewer CTAs fit on an SM)
     int nbuf;         // operand buffers in shared memory (3 .. CONV_MAXBUF)
+    int ns;           // output channels per CTA (blockIdx.y selects the slice)
 };
 
 constexpr int CONV_MAXBUF = 6;
@@ -131,12 +132,13 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nbuf = a.nbuf;
     const int kstage = a.tps * a.kst;  // reduction length of one stage
-    const uint32_t a_bytes = CONV_M * kstage * 2, b_bytes = a.cout * kstage * 2;
+    const int ns = a.ns, n0 = blockIdx.y * a.ns;  // this CTA's output channels
+    const uint32_t a_bytes = CONV_M * kstage * 2, b_bytes = ns * kstage * 2;
     const uint32_t sA = smem_addr(smem), sB = sA + nbuf * a_bytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + nbuf * (a_bytes + b_bytes));
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + CONV_MAXBUF);
     uint32_t ncols = 32;
-    while ((int)ncols < a.cout) ncols <<= 1;
+    while ((int)ncols < ns) ncols <<= 1;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
     }
     const int qn = a.kst / 8;  // 16-byte chunks per row per tap of a stage
     const int stages = ((27 + a.tps - 1) / a.tps) * a.cchunks;
-    const uint32_t idesc = instr_desc(CONV_M, a.cout);
+    const uint32_t idesc = instr_desc(CONV_M, ns);
     bool failed = false;
 
     // start the copies of stage t into buffer t % nbuf
@@ -186,13 +188,13 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
             for (int q = 0; q < qn; ++q)
                 cp16_ca(dA + operand_off(tid, i * qn + q, CONV_M), in ? src + q : a.x, in ? 16u : 0u);
         }
-        // B: all Cout rows, the same channels of the same taps
+        // B: this CTA's ns output channels, the same channels of the same taps
         const uint32_t dB = sB + buf * b_bytes;
         const int per_row = ntap * qn;
-        for (int idx = tid; idx < a.cout * per_row; idx += CONV_THREADS) {
+        for (int idx = tid; idx < ns * per_row; idx += CONV_THREADS) {
             const int n = idx / per_row, r = idx - n * per_row, i = r / qn, q = r - i * qn;
-            cp16_cg(dB + operand_off(n, r, a.cout),
-                    a.w + (((long long)n * 27 + tap0 + i) * a.cin + c0) / 8 + q);
+            cp16_cg(dB + operand_off(n, r, ns),
+                    a.w + (((long long)(n0 + n) * 27 + tap0 + i) * a.cin + c0) / 8 + q);
         }
     };
 
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
             const int slabs = min(a.tps, 27 - (s / a.cchunks) * a.tps) * a.kst / 16;
             for (int j = 0; j < slabs; ++j) {
                 const uint64_t ad = smem_desc(abase + j * (CONV_M / 8) * 256, 128, 256);
-                const uint64_t bd = smem_desc(bbase + j * (a.cout / 8) * 256, 128, 256);
+                const uint64_t bd = smem_desc(bbase + j * (ns / 8) * 256, 128, 256);
                 mma_bf16(tmem, ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
             }
             mma_commit(smem_addr(&bars[buf]));
@@ -250,14 +252,14 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_fwd(const ConvArgs a) {
     if (!failed) {
         // epilogue: warp w holds TMEM lanes 32w..32w+31 = rows of this CTA
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-        float* out = a.y + (row_ok ? v * a.cout : 0);
-        for (int c = 0; c < a.cout; c += 16) {
+        float* out = a.y + (row_ok ? v * a.cout + n0 : 0);
+        for (int c = 0; c < ns; c += 16) {
             float r[16];
             tmem_load16(tmem + lane_base + (uint32_t)c, r);
             if (row_ok) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    float t = r[i] + (a.bias ? a.bias[c + i] : 0.0f);
+                    float t = r[i] + (a.bias ? a.bias[n0 + c + i] : 0.0f);
                     r[i] = (a.relu && t < 0.0f) ? 0.0f : t;
                 }
 #pragma unroll
@@ -466,8 +468,8 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     while (ncols < Cout) ncols <<= 1;
     const size_t per_sm = 228 * 1024;
     if (Cin <= CONV_KMAX) {
-        // brick form: P output planes per CTA, as many as tensor memory (two
-        // CTAs per SM) and about 110 KB of shared memory allow
+        // brick form: P output planes per CTA, as many as tensor memory and
+        // about 110 KB of shared memory allow
         BrickArgs br;
         br.x = static_cast<const uint4*>(x);
         br.w = static_cast<const uint4*>(w);
@@ -480,7 +482,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         br.P = 1;
         br.nbuf = 3;
         for (int p = 4; p >= 1; p >>= 1) {
-            if (p * ncols > 256 || (p > 1 && p > D)) continue;
+            if (p * ncols > 512 || (p > 1 && p > D)) continue;
             const size_t brick = (size_t)(Cin / 8) * BR_X * BR_Y * (p + 2) * 16;
             int nbf = CONV_MAXBUF;
             while (nbf > 3 && brick + nbf * wst > 110 * 1024) --nbf;
@@ -520,7 +522,14 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     a.kst = Cin <= CONV_KMAX ? Cin : CONV_KMAX;
     a.cchunks = Cin / a.kst;
     a.tps = 1;
-    const size_t stage_bytes = ((size_t)CONV_M + Cout) * a.tps * a.kst * 2;
+    // output channels per CTA: split Cout while the grid is under two CTAs
+    // per SM (small volumes)
+    const long long gridm = (V + CONV_M - 1) / CONV_M;
+    a.ns = Cout;
+    while (a.ns % 32 == 0 && gridm * (Cout / a.ns) < 2 * 148) a.ns /= 2;
+    ncols = 32;
+    while (ncols < a.ns) ncols <<= 1;
+    const size_t stage_bytes = ((size_t)CONV_M + a.ns) * a.tps * a.kst * 2;
     a.nbuf = CONV_MAXBUF;
     while (a.nbuf > 3 && a.nbuf * stage_bytes > 112 * 1024) --a.nbuf;
     size_t smem = a.nbuf * stage_bytes + CONV_MAXBUF * sizeof(uint64_t) + 16;
@@ -537,8 +546,8 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
             return NGF_ECUDA;
         attr_set = true;
     }
-    const long long grid = (V + CONV_M - 1) / CONV_M;
-    if (launch(k_conv3d_fwd, dim3((unsigned)grid), dim3(CONV_THREADS), smem,
+    if (gridm >= (1LL << 31)) return NGF_EBOUNDS;
+    if (launch(k_conv3d_fwd, dim3((unsigned)gridm, (unsigned)(Cout / a.ns)), dim3(CONV_THREADS), smem,
                static_cast<cudaStream_t>(cuda_stream), a) != cudaSuccess)
         return NGF_ECUDA;
     return NGF_OK;
