@@ -23,6 +23,7 @@
 #include "ngf.h"
 #include "ngf_cnn.h"
 #include "ngf_launch.cuh"
+#include "ngf_plan.h"
 
 namespace ngf {
 namespace {
@@ -309,15 +310,44 @@ struct BrickArgs {
     int tiles_x, tiles_y, tiles_z;
 };
 
+// Weights of tap s repacked into the exact shared-memory image of the B
+// operand (K-major core matrices), so that one bulk copy moves a whole stage.
+__global__ void k_conv3d_pack_w(const uint4* __restrict__ w, uint4* __restrict__ wp, int cout, int qn) {
+    const int per_tap = cout * qn;
+    const int total = 27 * per_tap;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int s = idx / per_tap, r = idx - s * per_tap, n = r / qn, q = r - n * qn;
+        wp[(size_t)s * per_tap + operand_off(n, q, cout) / 16] = w[((size_t)n * 27 + s) * qn + q];
+    }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Roles after the brick is staged: thread 32 (warp 1) streams the packed
+// weights, one bulk copy per tap, into nbuf buffers (a "full" mbarrier per
+// buffer counts the bytes); thread 0 issues the MMAs of each tap once its
+// buffer is full and commits to the buffer's "empty" mbarrier, and after
+// the last tap to the "done" mbarrier that the whole CTA waits on.
 __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a) {
     NGF_DYNAMIC_SMEM(smem);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const int nbuf = a.nbuf, P = a.P, cg = a.cin / 8, qn = a.cin / 8;
+    const int nbuf = a.nbuf, P = a.P, cg = a.cin / 8;
     const int nb = BR_X * BR_Y * (P + 2);           // brick voxels
     const uint32_t brick_bytes = (uint32_t)cg * nb * 16, b_bytes = (uint32_t)a.cout * a.cin * 2;
     const uint32_t sBr = smem_addr(smem), sB = sBr + brick_bytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + brick_bytes + nbuf * b_bytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + CONV_MAXBUF);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + brick_bytes + nbuf * b_bytes);
+    uint64_t* empty = full + CONV_MAXBUF;
+    uint64_t* done = empty + CONV_MAXBUF;
+    int* flags = reinterpret_cast<int*>(done + 1);  // [0] failed, [1] copies issued, [2] taps consumed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags + 3);
     const uint32_t tcols = (uint32_t)(P * a.ncols);
 
     if (warp == 0) {
@@ -327,13 +357,14 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int i = 0; i < nbuf; ++i) mbar_init(smem_addr(&bars[i]), 1);
+        for (int i = 0; i < nbuf; ++i) {
+            mbar_init(smem_addr(&full[i]), 1);
+            mbar_init(smem_addr(&empty[i]), 1);
+        }
+        mbar_init(smem_addr(done), 1);
+        flags[0] = 0; flags[1] = 0; flags[2] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = *tmem_slot;
 
     int t = blockIdx.x;
     const int tx = t % a.tiles_x; t /= a.tiles_x;
@@ -350,50 +381,43 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         const int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
         const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H && gz >= 0 && gz < a.D;
         const uint4* src = a.x;
-        if (in) src += ((((long long)b * a.D + gz) * a.H + gy) * a.W + gx) * (a.cin / 8) + g;
+        if (in) src += ((((long long)b * a.D + gz) * a.H + gy) * a.W + gx) * cg + g;
         cp16_ca(sBr + (uint32_t)(g * nb + v) * 16, src, in ? 16u : 0u);
     }
-    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
 
-    // weights of tap s into buffer s % nbuf
-    auto load_w = [&](int s) {
-        const uint32_t dB = sB + (s % nbuf) * b_bytes;
-        for (int idx = tid; idx < a.cout * qn; idx += CONV_THREADS) {
-            const int n = idx / qn, q = idx - n * qn;
-            cp16_cg(dB + operand_off(n, q, a.cout), a.w + ((long long)n * 27 + s) * qn + q);
-        }
-    };
-    const int ahead = nbuf - 2;
-    for (int s = 0; s < ahead; ++s) {
-        load_w(s);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    const uint32_t idesc = instr_desc(CONV_M, a.cout);
-    const uint32_t lbo = (uint32_t)nb * 16;  // one channel group plane
-    bool failed = false;
-    for (int s = 0; s < 27; ++s) {
-        const int tn = s + ahead;
-        if (tn < 27) {
-            if (tn >= nbuf) {
-                const bool ok = mbar_wait(smem_addr(&bars[tn % nbuf]), (uint32_t)(((tn - nbuf) / nbuf) & 1));
-                if (__syncthreads_or(!ok)) { failed = true; break; }
+    if (tid == 32) {
+        // weight producer
+        const unsigned char* wp = reinterpret_cast<const unsigned char*>(a.w);
+        for (int s = 0; s < 27; ++s) {
+            const int buf = s % nbuf;
+            if (s >= nbuf && !mbar_wait(smem_addr(&empty[buf]), (uint32_t)(((s - nbuf) / nbuf) & 1))) {
+                atomicExch(&flags[0], 1);
+                break;
             }
-            load_w(tn);
+            if (*(volatile int*)&flags[0]) break;
+            mbar_expect_tx(smem_addr(&full[buf]), b_bytes);
+            bulk_copy(sB + buf * b_bytes, wp + (size_t)s * b_bytes, b_bytes, smem_addr(&full[buf]));
+            flags[1] = s + 1;
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        // the brick group and the groups of taps 0..s are complete
-        switch (ahead) {
-            case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-            case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-            case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-            default: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+    } else if (tid == 0) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc(CONV_M, a.cout);
+        const uint32_t lbo = (uint32_t)nb * 16;  // one channel group plane
+        for (int s = 0; s < 27; ++s) {
+            const int buf = s % nbuf;
+            if (!mbar_wait(smem_addr(&full[buf]), (uint32_t)((s / nbuf) & 1))) {
+                atomicExch(&flags[0], 1);
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int dz = s / 9, dy = (s / 3) % 3, dx = s % 3;  // brick offsets 0..2
-            const uint32_t bbase = sB + (s % nbuf) * b_bytes;
+            const uint32_t bbase = sB + buf * b_bytes;
             for (int p = 0; p < P; ++p) {
                 const uint32_t abase = sBr + (uint32_t)(((p + dz) * BR_Y + dy) * BR_X + dx) * 16;
                 for (int j = 0; j < a.cin / 16; ++j) {
@@ -402,15 +426,15 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
                     mma_bf16(tmem + (uint32_t)(p * a.ncols), ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
                 }
             }
-            mma_commit(smem_addr(&bars[s % nbuf]));
+            mma_commit(smem_addr(&empty[buf]));
+            flags[2] = s + 1;
         }
+        mma_commit(smem_addr(done));  // all MMAs issued above are complete
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-
-    bool ok = !failed;
-    for (int s = 27 - nbuf; s < 27 && !failed; ++s)
-        ok &= mbar_wait(smem_addr(&bars[s % nbuf]), (uint32_t)((s / nbuf) & 1));
-    if (__syncthreads_or(!ok)) failed = true;
+    __syncwarp();
+    const bool ok = mbar_wait(smem_addr(done), 0u);
+    __syncthreads();
+    const bool failed = __syncthreads_or(!ok || flags[0] != 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (!failed) {
@@ -438,7 +462,8 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         }
     } else if (tid == 0) {
         atomicAdd(&g_conv_timeouts, 1u);
-        mbar_wait(smem_addr(&bars[26 % nbuf]), (uint32_t)((26 / nbuf) & 1));
+        // bounded waits for bulk copies still in flight (issued, not consumed)
+        for (int s = flags[2]; s < flags[1]; ++s) mbar_wait(smem_addr(&full[s % nbuf]), (uint32_t)((s / nbuf) & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -492,7 +517,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         br.tiles_y = (H + 15) / 16;
         br.tiles_z = (D + br.P - 1) / br.P;
         const size_t brick = (size_t)(Cin / 8) * BR_X * BR_Y * (br.P + 2) * 16;
-        size_t smem = brick + br.nbuf * wst + CONV_MAXBUF * sizeof(uint64_t) + 16;
+        size_t smem = brick + br.nbuf * wst + (2 * CONV_MAXBUF + 1) * sizeof(uint64_t) + 32;
         // every resident CTA's tensor-memory allocation must fit at once
         const size_t ctas = 512 / (br.P * ncols);
         const size_t smem_min = per_sm / (ctas + 1) - 1024 + 16;
@@ -506,10 +531,19 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
                 return NGF_ECUDA;
             battr = true;
         }
-        if (launch(k_conv3d_brick, dim3((unsigned)grid), dim3(CONV_THREADS), smem,
-                   static_cast<cudaStream_t>(cuda_stream), br) != cudaSuccess)
-            return NGF_ECUDA;
-        return NGF_OK;
+        // weights repacked per tap into the B operand's shared-memory image
+        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+        void* wp = nullptr;
+        if (dev_alloc(&wp, 27 * wst, st) != cudaSuccess) return NGF_ENOMEM;
+        const int chunks = 27 * Cout * (Cin / 8);
+        const bool ok = launch(k_conv3d_pack_w, dim3((chunks + 255) / 256), dim3(256), 0, st,
+                               static_cast<const uint4*>(w), static_cast<uint4*>(wp), (int)Cout,
+                               (int)(Cin / 8)) == cudaSuccess &&
+                        (br.w = static_cast<const uint4*>(wp),
+                         launch(k_conv3d_brick, dim3((unsigned)grid), dim3(CONV_THREADS), smem, st, br) ==
+                             cudaSuccess);
+        dev_free(wp, st);
+        return ok ? NGF_OK : NGF_ECUDA;
     }
     ConvArgs a;
     a.x = static_cast<const uint4*>(x);
