@@ -493,8 +493,11 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     while (ncols < Cout) ncols <<= 1;
     const size_t per_sm = 228 * 1024;
     if (Cin <= CONV_KMAX) {
-        // brick form: P output planes per CTA, as many as tensor memory and
-        // about 110 KB of shared memory allow
+        // brick form: P output planes per CTA, as many as leave room for two
+        // CTAs per SM (256 tensor-memory columns, about 110 KB of shared
+        // memory each): a second CTA stages its brick and drains its
+        // accumulators while the other one's MMAs run (measured faster than
+        // twice the planes in one CTA per SM)
         BrickArgs br;
         br.x = static_cast<const uint4*>(x);
         br.w = static_cast<const uint4*>(w);
@@ -507,7 +510,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         br.P = 1;
         br.nbuf = 3;
         for (int p = 4; p >= 1; p >>= 1) {
-            if (p * ncols > 512 || (p > 1 && p > D)) continue;
+            if (p * ncols > 256 || (p > 1 && p > D)) continue;
             const size_t brick = (size_t)(Cin / 8) * BR_X * BR_Y * (p + 2) * 16;
             int nbf = CONV_MAXBUF;
             while (nbf > 3 && brick + nbf * wst > 110 * 1024) --nbf;
