@@ -107,3 +107,23 @@ def test_size_limit_and_distance_validation(ngf):
     assert ngf.lib.register_multilevel(C.byref(ok), C.byref(opts), buf, buf, buf, C.byref(rep), None) == -1
     bh = C.c_void_p()
     assert ngf.lib.ngf_batch_create(C.byref(bh), 0, C.byref(ok), 0, None) == -1 and not bh.value
+
+
+def test_tile_depth_and_convolution_validation(ngf):
+    """A negative z-chunk length and convolution shapes outside the documented
+    limits are rejected before any CUDA call."""
+    h = C.c_void_p()
+    ok = ngf.level_desc((8, 8, 8), (1, 1, 1), (5, 5, 5))
+    assert ngf.lib.ngf_plan_create_ex(C.byref(h), C.byref(ok), -1, None) == -1 and not h.value
+    assert "zc" in ngf.ngf_last_error(None)
+    buf = (C.c_float * 600)()
+    rep = ngf.Report()
+    opts = ngf.options(2, zc=-2)
+    assert ngf.lib.register_multilevel(C.byref(ok), C.byref(opts), buf, buf, buf, C.byref(rep), None) == -1
+    assert "zc" in ngf.ngf_last_error(None)
+    conv = ngf.lib.ngf_conv3d_fwd
+    for cin, cout in ((8, 16), (80, 16), (16, 8), (16, 24), (16, 272)):
+        assert conv(buf, buf, None, buf, 1, 2, 2, 2, cin, cout, 0, None) == -1, (cin, cout)
+    assert conv(buf, buf, None, buf, 1, -1, 2, 2, 16, 16, 0, None) == -1
+    assert conv(buf, buf, None, buf, 1, 2048, 2048, 1024, 16, 16, 0, None) == -8
+    assert conv(None, None, None, None, 1, 0, 4, 4, 16, 16, 0, None) == 0  # empty volume
