@@ -35,14 +35,14 @@
 extern "C" {
 #endif
 
-/* 3x3x3 convolution forward (see above).  Cin <= 64: the weights are first
- * repacked into a temporary of 27*Cout*Cin*2 bytes taken from the library's
+/* 3x3x3 convolution forward (see above).  The weights are first repacked
+ * into a temporary of 27*Cout*Cin*2 bytes taken from the library's
  * stream-ordered pool (NGF_ENOMEM if that fails; released on the stream
- * after the launch), then one CTA computes an 8 x 16 x P block of output
- * voxels (P = 1, 2 or 4) from an input brick staged once in shared memory.
- * Cin > 64: one CTA per 128 consecutive output voxels and a slice of the
- * output channels.  Repeated calls with the same arguments give identical
- * results (no atomics; each output accumulates taps in a fixed order). */
+ * after the launch); then one CTA computes an 8 x 16 x P block of output
+ * voxels (P = 1, 2 or 4) for a slice of the output channels from an input
+ * brick staged in shared memory once per 64 input channels.  Repeated calls
+ * with the same arguments give identical results (no atomics; each output
+ * accumulates (channel chunk, tap) in a fixed order). */
 ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* bias, float* y,
                           int32_t B, int32_t D, int32_t H, int32_t W,
                           int32_t Cin, int32_t Cout, int32_t relu, void* cuda_stream);
