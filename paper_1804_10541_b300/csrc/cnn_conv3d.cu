@@ -135,7 +135,8 @@ struct BrickArgs {
     int ncols;        // tensor-memory columns per accumulator
     int kc;           // input channels per chunk
     int nch;          // chunks
-    int nbuf;         // weight buffers (3 .. CONV_MAXBUF)
+    int tps;          // taps per weight stage: 1, 3, 9 or 27
+    int nbuf;         // weight buffers (1 .. CONV_MAXBUF)
     int tiles_x, tiles_y, tiles_z;
 };
 
@@ -178,8 +179,10 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
     const int nbuf = a.nbuf, P = a.P, cg = a.kc / 8, ns = a.ns, n0 = blockIdx.y * a.ns;
     const int nb = BR_X * BR_Y * (P + 2);           // brick voxels
     const uint32_t brick_bytes = (uint32_t)cg * nb * 16, b_bytes = (uint32_t)ns * a.kc * 2;
+    const uint32_t st_bytes = a.tps * b_bytes;     // one weight stage
+    const int spc = 27 / a.tps;                    // stages per chunk
     const uint32_t sBr = smem_addr(smem), sB = sBr + brick_bytes;
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + brick_bytes + nbuf * b_bytes);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + brick_bytes + nbuf * st_bytes);
     uint64_t* empty = full + CONV_MAXBUF;
     uint64_t* chunk_bar = empty + CONV_MAXBUF;
     int* flags = reinterpret_cast<int*>(chunk_bar + 1);  // [0] failed, [1] copies issued, [2] stages consumed
@@ -240,36 +243,40 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
 
         if (tid == 32) {
             // weight producer: stages s = 27c .. 27c + 26
-            for (int s = 27 * c; s < 27 * c + 27; ++s) {
+            for (int s = spc * c; s < spc * c + spc; ++s) {
                 const int buf = s % nbuf;
                 if (s >= nbuf && !mbar_wait(smem_addr(&empty[buf]), (uint32_t)(((s - nbuf) / nbuf) & 1))) {
                     atomicExch(&flags[0], 1);
                     break;
                 }
                 if (*(volatile int*)&flags[0]) break;
-                mbar_expect_tx(smem_addr(&full[buf]), b_bytes);
-                bulk_copy(sB + buf * b_bytes, wp + (size_t)s * b_bytes, b_bytes, smem_addr(&full[buf]));
+                mbar_expect_tx(smem_addr(&full[buf]), st_bytes);
+                bulk_copy(sB + buf * st_bytes, wp + (size_t)s * st_bytes, st_bytes, smem_addr(&full[buf]));
                 flags[1] = s + 1;
             }
         } else if (tid == 0) {
             // MMA issuer
             const uint32_t idesc = instr_desc(CONV_M, ns);
             const uint32_t lbo = (uint32_t)nb * 16;  // one channel group plane
-            for (int s = 27 * c; s < 27 * c + 27; ++s) {
-                const int buf = s % nbuf, tap = s - 27 * c;
+            for (int s = spc * c; s < spc * c + spc; ++s) {
+                const int buf = s % nbuf;
                 if (!mbar_wait(smem_addr(&full[buf]), (uint32_t)((s / nbuf) & 1))) {
                     atomicExch(&flags[0], 1);
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // brick offsets 0..2
-                const uint32_t bbase = sB + buf * b_bytes;
-                for (int p = 0; p < P; ++p) {
-                    const uint32_t abase = sBr + (uint32_t)(((p + dz) * BR_Y + dy) * BR_X + dx) * 16;
-                    for (int j = 0; j < a.kc / 16; ++j) {
-                        const uint64_t ad = smem_desc(abase + 2 * j * lbo, lbo, BR_X * 16);
-                        const uint64_t bd = smem_desc(bbase + j * (ns / 8) * 256, 128, 256);
-                        mma_bf16(tmem + (uint32_t)(p * a.ncols), ad, bd, idesc, (s > 0 || j > 0) ? 1u : 0u);
+                for (int i = 0; i < a.tps; ++i) {
+                    const int tap = (s - spc * c) * a.tps + i;
+                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // brick offsets 0..2
+                    const uint32_t bbase = sB + buf * st_bytes + i * b_bytes;
+                    for (int p = 0; p < P; ++p) {
+                        const uint32_t abase = sBr + (uint32_t)(((p + dz) * BR_Y + dy) * BR_X + dx) * 16;
+                        for (int j = 0; j < a.kc / 16; ++j) {
+                            const uint64_t ad = smem_desc(abase + 2 * j * lbo, lbo, BR_X * 16);
+                            const uint64_t bd = smem_desc(bbase + j * (ns / 8) * 256, 128, 256);
+                            mma_bf16(tmem + (uint32_t)(p * a.ncols), ad, bd, idesc,
+                                     (s > 0 || i > 0 || j > 0) ? 1u : 0u);
+                        }
                     }
                 }
                 mma_commit(smem_addr(&empty[buf]));
@@ -377,7 +384,15 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         while (br.ncols < br.ns) br.ncols <<= 1;
         const size_t wst = (size_t)br.ns * br.kc * 2;
         const size_t brick = (size_t)(br.kc / 8) * BR_X * BR_Y * (br.P + 2) * 16;
-        size_t smem = brick + br.nbuf * wst + (2 * CONV_MAXBUF + 1) * sizeof(uint64_t) + 32;
+        // taps per weight stage: small weight images are moved several taps
+        // per bulk copy (fewer waits in the MMA thread's chain)
+        br.tps = 1;
+        for (int tp : {27, 9, 3})
+            if (tp * wst <= 24 * 1024 && brick + tp * wst <= 110 * 1024) { br.tps = tp; break; }
+        const int stages = br.nch * (27 / br.tps);
+        br.nbuf = stages < CONV_MAXBUF ? stages : CONV_MAXBUF;
+        while (br.nbuf > 1 && brick + br.nbuf * br.tps * wst > 110 * 1024) --br.nbuf;
+        size_t smem = brick + br.nbuf * br.tps * wst + (2 * CONV_MAXBUF + 1) * sizeof(uint64_t) + 32;
         // every resident CTA's tensor-memory allocation must fit at once
         const size_t ctas = 512 / (br.P * br.ncols);
         const size_t smem_min = per_sm / (ctas + 1) - 1024 + 16;
