@@ -3,9 +3,12 @@
 One step = one full multilevel Gauss-Newton registration (register_multilevel:
 image pyramid, per level 10 Gauss-Newton steps each with gradient, Jacobi
 diagonal, 20 PCG iterations of gn_hessvec and an Armijo line search, and the
-prolongation between levels) of the synthetic 256x256x120 lung-CT workload
-(1x1x2.5 mm, 129x129x61 nodes, 4 levels).  Inputs are resident in HBM when the
-timed region starts; L2 is flushed (a 256 MB write) before every timed step.
+prolongation between levels).  The default workload is the synthetic
+512x512x900 thorax-abdomen pair (0.8x0.8x1.0 mm, 129x129x225 nodes, 5 levels),
+the largest single-GPU configuration; `--workload lung_ct` times the
+256x256x120 lung-CT pair (1x1x2.5 mm, 129x129x61 nodes, 4 levels) the same
+way.  Inputs are resident in HBM when the timed region starts; L2 is flushed
+(a 256 MB write) before every timed step.
 
 value = image voxels processed by gn_hessvec over the whole registration
 (sum over levels of voxels x Hessian-vector products) / step time, in
@@ -15,7 +18,8 @@ of the registration included.  `ms_per_step` is the full-registration time.
 `--impl reference` times the FP64 CPU oracle instead (bounded samples of the
 same workload on the host cores).  Under torchrun every rank runs an
 independent replica (the path has no exchange step); value sums all ranks'
-voxels over the slowest rank's time.
+voxels over the slowest rank's time.  Other workloads (batch_64, conv3d,
+learned, oracle_timing) print their own JSON lines.
 """
 import argparse
 import json
@@ -28,7 +32,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "lung_ct"
+WORKLOAD = "thorax_abd"
+REG_WORKLOADS = ("thorax_abd", "lung_ct")
 GN_ITERS, PCG_ITERS = 10, 20
 LBFGS_ITERS = 50  # L-BFGS steps per level of the comparison run
 # algorithmic cost of one gn_hessvec image-grid pass per voxel (see design notes):
@@ -124,11 +129,12 @@ def image_pass_source_hash():
     return hashlib.sha256((cu[:end] + cuh[a:b]).encode()).hexdigest()
 
 
-def stored_traffic():
-    """DRAM bytes per launch of k_image_hess from the committed ncu summary,
-    or None when the kernel source changed since that capture."""
+def stored_traffic(workload):
+    """DRAM bytes per launch of k_image_hess on the workload's finest level
+    from the committed ncu summary, or None when the kernel source changed
+    since that capture."""
     try:
-        with open(os.path.join(ROOT, "profiles", "k_image_hess_lung_ct.md")) as f:
+        with open(os.path.join(ROOT, "profiles", f"k_image_hess_{workload}.md")) as f:
             txt = f.read()
     except OSError:
         return None
@@ -150,50 +156,86 @@ def _peaks():
         return {}
 
 
-def cpu_baseline_leg(R, T, w, seconds_budget=20.0, max_calls=3):
+def oracle_sample(workload, R, T, w, planes=64):
+    """A bounded piece of the workload for the FP64 oracle: the whole pair
+    when it is small, else the z-slab of `planes` central image planes of R
+    and T with its own node grid at the workload's voxels-per-cell ratio (the
+    full 512x512x900 grid would need about 47 GB of host memory in the
+    oracle's staged arrays).  Returns (m, h, n, R, T, description) with R, T
+    float64 numpy arrays."""
+    m, h, n = list(w["m"]), w["h"], list(w["n"])
+    if m[2] > 2 * planes and m[0] * m[1] * m[2] > 32 * 1024 * 1024:
+        z0 = (m[2] - planes) // 2
+        plane = m[0] * m[1]
+        ratio = (m[2]) / (n[2] - 1)
+        Rh = R[z0 * plane:(z0 + planes) * plane].double().cpu().numpy()
+        Th = T[z0 * plane:(z0 + planes) * plane].double().cpu().numpy()
+        nz = max(2, int(round(planes / ratio)) + 1)
+        desc = (f"z-slab of {planes} central planes ({m[0]}x{m[1]}x{planes}, nodes {n[0]}x{n[1]}x{nz}) of the "
+                f"{m[0]}x{m[1]}x{m[2]} {workload} pair")
+        return (m[0], m[1], planes), h, (n[0], n[1], nz), Rh, Th, desc
+    return tuple(m), h, tuple(n), R.double().cpu().numpy(), T.double().cpu().numpy(), \
+        f"the full {m[0]}x{m[1]}x{m[2]} {workload} grid"
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline_leg(workload, R, T, w, seconds_budget=20.0, max_calls=5):
     """Time the FP64 oracle's gn_hessvec (as it stands) on the host cores on a
-    bounded sample of the same workload: whole calls on the full lung-CT grid."""
-    import numpy as np
+    bounded sample of the same workload (see oracle_sample)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
     from paper_1804_10541_b300 import synth
-    m, h, n = w["m"], w["h"], w["n"]
+    m, h, n, Rh, Th, desc = oracle_sample(workload, R, T, w)
     L = O.level(m, h, n, w["alpha"], w["tau"], w["rho"])
     N = n[0] * n[1] * n[2]
     u, p = synth.random_fields(N, 5, amp=0.5 * min(h))
-    Rh = R.double().cpu().numpy()
-    Th = T.double().cpu().numpy()
     uh, ph = u.double().numpy(), p.double().numpy()
     O.hessvec(L, Rh, Th, uh, ph)  # first call pages the arrays in; not timed
-    calls, t0 = 0, time.perf_counter()
-    while calls < max_calls:
+    times = []
+    t0 = time.perf_counter()
+    while len(times) < max_calls:
+        t1 = time.perf_counter()
         O.hessvec(L, Rh, Th, uh, ph)
-        calls += 1
+        times.append(time.perf_counter() - t1)
         if time.perf_counter() - t0 > seconds_budget:
             break
-    dt = time.perf_counter() - t0
     M = m[0] * m[1] * m[2]
+    med = statistics.median(times)
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": M * calls / dt / 1e9, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
-            "sample": f"{calls} FP64 oracle gn_hessvec calls on the full {m[0]}x{m[1]}x{m[2]} lung-CT grid "
-                      f"({dt:.1f} s, OpenMP over z)"}
+    return {"value": M / med / 1e9, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"median of {len(times)} FP64 oracle gn_hessvec calls on the {desc} "
+                      f"({med:.2f} s per call, OpenMP over z)"}
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle, timed as it stands on the host."""
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host, on
+    a bounded sample of the bench's workload (one gn_hessvec per step)."""
     ws, rank = _dist()
     if rank != 0:
         return 0
     import torch
     from paper_1804_10541_b300 import synth
-    R, T, _, w = synth.make(WORKLOAD, device="cuda" if torch.cuda.is_available() else "cpu")
+    workload = args.workload if args.workload in REG_WORKLOADS else WORKLOAD
+    R, T, _, w = synth.make(workload, device="cuda" if torch.cuda.is_available() else "cpu")
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
-    m, h, n = w["m"], w["h"], w["n"]
+    m, h, n, Rh, Th, desc = oracle_sample(workload, R, T, w)
+    del R, T
     L = O.level(m, h, n, w["alpha"], w["tau"], w["rho"])
     N = n[0] * n[1] * n[2]
     u, p = synth.random_fields(N, 5, amp=0.5 * min(h))
-    Rh, Th, uh, ph = R.double().cpu().numpy(), T.double().cpu().numpy(), u.double().numpy(), p.double().numpy()
+    uh, ph = u.double().numpy(), p.double().numpy()
     for _ in range(args.warmup):
         O.hessvec(L, Rh, Th, uh, ph)
     times = []
@@ -205,15 +247,17 @@ def run_reference(args):
     total = sum(times)
     value = M * args.steps / total / 1e9
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    wm = w["m"]
     line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"{WORKLOAD} {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes "
-                                   f"{n[0]}x{n[1]}x{n[2]}; one step = one FP64 oracle gn_hessvec",
+            "config": {"workload": f"{workload} {wm[0]}x{wm[1]}x{wm[2]} at {h[0]}x{h[1]}x{h[2]} mm; one step = one "
+                                   f"FP64 oracle gn_hessvec on the {desc}",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} timed FP64 oracle gn_hessvec calls on the full grid"},
+                             "cpu_model": cpu_model(),
+                             "sample": f"{args.steps} timed FP64 oracle gn_hessvec calls on the {desc}"},
             "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -231,7 +275,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     from paper_1804_10541_b300 import ngf, synth
 
-    R, T, _, w = synth.make(WORKLOAD, device=dev)
+    workload = args.workload
+    R, T, _, w = synth.make(workload, device=dev)
     m, h, n, levels = w["m"], w["h"], w["n"], w["levels"]
     M = m[0] * m[1] * m[2]
     N = n[0] * n[1] * n[2]
@@ -308,7 +353,7 @@ def run_ours(args):
     Rp.copy_(R.cpu())
     Tp.copy_(T.cpu())
     e2e_times, e2e_vox = [], 0
-    for k in range(max(1, args.steps)):
+    for k in range(max(1, min(args.steps, 5))):
         flush.fill_(float(k))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -347,7 +392,7 @@ def run_ours(args):
     achieved = HESS_FLOP_PER_VOXEL * M / t_launch / 1e12
     bytes_per_voxel = 8.0 + 36.0 * N / M  # R, T + u, p read and q written, per voxel
     roofline = {"bound": "alu", "kernel": "k_image_hess", "achieved": achieved, "peak": alu_peak,
-                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": stored_traffic(),
+                "unit": "TFLOP/s", "frac": achieved / alu_peak, "traffic": stored_traffic(workload),
                 "peak_source": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {max_mhz:.0f} MHz",
                 "flop_per_voxel": HESS_FLOP_PER_VOXEL, "launch_us": t_launch * 1e6,
                 "hessvec_call_us": ms_call * 1e3,
@@ -358,18 +403,24 @@ def run_ours(args):
                 "kernel_gvoxel_s": M / t_launch / 1e9}
 
     if rank == 0:
-        cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline_leg(R, T, w)
+        cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline_leg(workload, R, T, w)
         r0 = reps[-1]
         line = {"metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"{WORKLOAD} {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes "
+                "config": {"workload": f"{workload} {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes "
                                        f"{n[0]}x{n[1]}x{n[2]}, {levels} levels, {GN_ITERS} GN x {PCG_ITERS} PCG; "
                                        f"one step = one full register_multilevel",
                            "parallelism": f"replicas x{ws}", "l2": "flushed before every step (256 MB write)",
                            "registration_ms": 1e3 * t_max / args.steps, "final_J": r0.J,
                            "gn_done": r0.gn_done, "pcg_total": r0.pcg_total, "ls_trials": r0.ls_trials,
-                           "fixed_ms_per_registration": fixed_ms},
+                           "fixed_ms_per_registration": fixed_ms, "status": r0.status,
+                           "torch_allocated_peak_gb": torch.cuda.max_memory_allocated(dev) / 1e9,
+                           "parity": "operators match the FP64 oracle element-wise (gradient and Hessian-vector "
+                                     "product 1e-5 relative L2, objective 1e-6) on crops with this workload's "
+                                     "spacing and grid ratio; full registrations match the oracle's u within "
+                                     "0.01 voxel after 3 GN steps per level and its final J within 1e-3 after "
+                                     "10 (an Armijo decision within rounding can flip later)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "lbfgs": lbfgs,
                 "gpu_launches": int(launches)}
         print(json.dumps(line), flush=True)
@@ -383,8 +434,21 @@ def run_kernel_case(args):
     finest level of a workload, timed with CUDA events."""
     import torch
     from paper_1804_10541_b300 import ngf, synth
-    R, T, _, w = synth.make(args.kernel_case, device="cuda")
-    m, h, n = w["m"], w["h"], w["n"]
+    if args.slab:
+        # central z-slab of the thorax-abdomen phantom with its own node grid
+        # at the workload's voxels-per-cell ratio: a smaller case of the same
+        # kernel for multi-pass profiler captures (inputs still above L2)
+        assert args.kernel_case == "thorax_abd"
+        w = dict(synth.WORKLOADS["thorax_abd"])
+        m, h, n = w["m"], w["h"], w["n"]
+        z0 = (m[2] - args.slab) // 2
+        R, T, _ = synth.thorax_pair(m, h, seed=w["seed"], device="cuda", zrange=(z0, z0 + args.slab))
+        nz = max(2, int(round(args.slab * (n[2] - 1) / m[2])) + 1)
+        m, n = (m[0], m[1], args.slab), (n[0], n[1], nz)
+    else:
+        R, T, _, w = synth.make(args.kernel_case, device="cuda")
+        m, h, n = w["m"], w["h"], w["n"]
+    torch.cuda.empty_cache()
     N = n[0] * n[1] * n[2]
     dist = ngf.NGF_DIST_SSD if args.distance == "ssd" else ngf.NGF_DIST_NGF
     desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"], distance=dist)
@@ -408,7 +472,8 @@ def run_kernel_case(args):
             torch.cuda.synchronize()
             times[name] = e0.elapsed_time(e1) / args.calls
     M = m[0] * m[1] * m[2]
-    print(json.dumps({"kernel_case": args.kernel_case, "distance": args.distance, "calls": args.calls,
+    print(json.dumps({"kernel_case": args.kernel_case, "m": list(m), "n": list(n), "distance": args.distance,
+                      "calls": args.calls,
                       "ms": times, "hessvec_gvoxel_s": M / times["hessvec"] / 1e6}), flush=True)
     return 0
 
@@ -574,46 +639,6 @@ def run_batch(args):
     return 0
 
 
-def run_thorax(args):
-    """Full multilevel registration of the 512x512x900 thorax-abdomen workload
-    (0.8x0.8x1.0 mm, 129x129x225 nodes, 5 levels, 10 GN x 20 PCG per level),
-    timed with CUDA events after warm-up; its own JSON line."""
-    import torch
-    from paper_1804_10541_b300 import ngf, synth
-    dev = torch.device("cuda", 0)
-    R, T, _, w = synth.make("thorax_abd", device=dev)
-    m, h, n, levels = w["m"], w["h"], w["n"], w["levels"]
-    N = n[0] * n[1] * n[2]
-    desc = ngf.level_desc(m, h, n, w["alpha"], w["tau"], w["rho"])
-    opts = ngf.options(levels=levels, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True)
-    stream = torch.cuda.Stream(device=dev)
-    u = torch.empty(3 * N, device=dev)
-    with torch.cuda.stream(stream):
-        for _ in range(max(1, args.warmup)):
-            ngf.register_multilevel(desc, opts, R, T, u, stream)
-    stream.synchronize()
-    sampler = ClockSampler(0)
-    sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            ev[k][0].record(stream)
-            rep = ngf.register_multilevel(desc, opts, R, T, u, stream)
-            ev[k][1].record(stream)
-    stream.synchronize()
-    clocks = sampler.stop()
-    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
-    line = {"workload": f"thorax_abd {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes {n[0]}x{n[1]}x{n[2]}, "
-                        f"{levels} levels, {GN_ITERS} GN x {PCG_ITERS} PCG", "metric": METRIC,
-            "value": rep.hessvec_voxels / (ms / 1e3) / 1e9, "unit": "Gvoxel/s", "registration_ms": ms,
-            "steps": args.steps, "warmup": args.warmup, "final_J": rep.J, "gn_done": rep.gn_done,
-            "pcg_total": rep.pcg_total, "ls_trials": rep.ls_trials, "status": rep.status,
-            "torch_allocated_peak_gb": torch.cuda.max_memory_allocated(dev) / 1e9, "clocks": clocks,
-            "dtype": "f32", "data": "synthetic"}
-    print(json.dumps(line), flush=True)
-    return 0
-
-
 def run_conv3d(args):
     """Tensor-core 3x3x3 convolution (learned-initializer building block) on
     the layer shapes of a 4-level encoder at 128^3 (16 -> 128 channels): per
@@ -681,6 +706,118 @@ def run_conv3d(args):
     return 0
 
 
+def _meminfo_gb(key="MemAvailable"):
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith(key + ":"):
+                    return int(line.split()[1]) / 1024 ** 2
+    except OSError:
+        pass
+    return None
+
+
+def _oracle_leg(threads):
+    """One leg of the oracle timing at a fixed OpenMP thread count (this
+    process was started with OMP_NUM_THREADS = threads)."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    from paper_1804_10541_b300 import synth
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    out = {"threads": threads, "hessvec": {}, "registration": {}}
+
+    def hv(L, Rh, Th, calls):
+        N = L.n[0] * L.n[1] * L.n[2]
+        u, p = synth.random_fields(N, 5, amp=0.5 * min(L.h[0], L.h[1], L.h[2]))
+        uh, ph = u.double().numpy(), p.double().numpy()
+        O.hessvec(L, Rh, Th, uh, ph)
+        ts = []
+        for _ in range(calls):
+            t0 = time.perf_counter()
+            O.hessvec(L, Rh, Th, uh, ph)
+            ts.append(time.perf_counter() - t0)
+        return statistics.median(ts), len(ts)
+
+    for name in ("blobs_32", "lung_ct", "thorax_abd"):
+        R, T, _, w = synth.make(name, device=dev)
+        m, h, n = w["m"], w["h"], w["n"]
+        M = m[0] * m[1] * m[2]
+        rec = {}
+        if name == "thorax_abd":
+            # the full grid only when the host has room for the oracle's
+            # staged arrays (about 200 bytes per voxel) and all cores run it
+            avail = _meminfo_gb()
+            if threads > 1 and avail is not None and avail > 80:
+                L = O.level(m, h, n, w["alpha"], w["tau"], w["rho"])
+                t, k = hv(L, R.double().cpu().numpy(), T.double().cpu().numpy(), 1)
+                rec["full_grid"] = {"s": t, "calls": k, "mvoxel_s": M / t / 1e6}
+            planes = 64 if threads > 1 else 16
+            ms, hs, ns, Rh, Th, desc = oracle_sample(name, R, T, w, planes=planes)
+            L = O.level(ms, hs, ns, w["alpha"], w["tau"], w["rho"])
+            t, k = hv(L, Rh, Th, 5 if threads > 1 else 3)
+            Ms = ms[0] * ms[1] * ms[2]
+            rec["slab"] = {"sample": desc, "s": t, "calls": k, "mvoxel_s": Ms / t / 1e6,
+                           "full_grid_s_extrapolated": t * M / Ms}
+            if threads > 1:
+                # one Gauss-Newton step (gradient, diagonal, 20 PCG, Armijo) on
+                # the slab, extrapolated per voxel to the 5-level registration
+                uh0 = np.zeros(3 * ns[0] * ns[1] * ns[2])
+                t0 = time.perf_counter()
+                O.gn_level(L, Rh, Th, uh0, O.gn_options(gn_iters=1, pcg_iters=PCG_ITERS))
+                t_gn = time.perf_counter() - t0
+                vox_levels = 0
+                mm = list(m)
+                for _ in range(w["levels"]):
+                    vox_levels += mm[0] * mm[1] * mm[2]
+                    mm = [(a + 1) // 2 for a in mm]
+                rec["registration_extrapolated_s"] = t_gn / Ms * vox_levels * GN_ITERS
+                rec["registration_extrapolation"] = (
+                    f"one oracle GN step ({PCG_ITERS} PCG) on the slab took {t_gn:.1f} s; x {GN_ITERS} steps x "
+                    f"the voxels of all {w['levels']} levels / slab voxels (labelled extrapolation, not a run)")
+        else:
+            L = O.level(m, h, n, w["alpha"], w["tau"], w["rho"])
+            Rh, Th = R.double().cpu().numpy(), T.double().cpu().numpy()
+            t, k = hv(L, Rh, Th, 5 if (threads > 1 or name == "blobs_32") else 3)
+            rec = {"s": t, "calls": k, "mvoxel_s": M / t / 1e6}
+            if threads > 1 or name == "blobs_32":
+                t0 = time.perf_counter()
+                _, rep = O.register_multilevel(L, w["levels"], O.gn_options(gn_iters=GN_ITERS, pcg_iters=PCG_ITERS),
+                                               Rh, Th)
+                out["registration"][name] = {"s": time.perf_counter() - t0, "J": rep.J, "gn_done": rep.gn_done,
+                                             "pcg_total": rep.pcg_total, "levels": w["levels"]}
+        out["hessvec"][name] = rec
+        del R, T
+    return out
+
+
+def run_oracle_timing(args):
+    """The FP64 oracle timed on the host cores: gn_hessvec (median of 5) on
+    the 32^3, lung-CT and thorax-abdomen workloads, full registrations of the
+    first two, and a labelled extrapolation for the 512x512x900 registration;
+    once with all cores and once with one (each leg in its own process, so
+    that OpenMP starts with that thread count)."""
+    if args.threads > 0:
+        print(json.dumps(_oracle_leg(args.threads)), flush=True)
+        return 0
+    nproc = os.cpu_count() or 1
+    legs = []
+    for t in (nproc, 1):
+        env = dict(os.environ, OMP_NUM_THREADS=str(t))
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--workload", "oracle_timing", "--threads",
+                            str(t)], env=env, capture_output=True, text=True)
+        if r.returncode != 0:
+            print(r.stderr[-2000:], file=sys.stderr)
+            return r.returncode
+        legs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    line = {"workload": "oracle_timing", "kind": "FP64 oracle (oracle/ngf_oracle.c) as it stands, OpenMP over z",
+            "nproc": nproc, "cpu_model": cpu_model(), "host_mem_total_gb": _meminfo_gb("MemTotal"),
+            "legs": legs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -690,18 +827,22 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", default=None, help="profile driver: gn_hessvec only on this workload")
     ap.add_argument("--calls", type=int, default=3)
+    ap.add_argument("--slab", type=int, default=0, help="--kernel-case: central z-slab of this many planes")
     ap.add_argument("--distance", default="ngf", choices=["ngf", "ssd"], help="distance of --kernel-case")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch_64", "thorax_abd", "conv3d"],
-                    help="batch_64: the batched form on 64 uneven pairs; thorax_abd: the 512x512x900 "
-                         "registration; conv3d: the tensor-core convolution layers (each its own JSON line)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[*REG_WORKLOADS, "batch_64", "conv3d", "oracle_timing"],
+                    help="thorax_abd (default) / lung_ct: full registrations; batch_64: the batched form on 64 "
+                         "uneven pairs; conv3d: the tensor-core convolution layers; oracle_timing: the FP64 "
+                         "oracle on the host cores (each of the last three prints its own JSON line)")
+    ap.add_argument("--threads", type=int, default=0, help="oracle_timing: OpenMP threads of one leg")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
     if args.workload == "batch_64":
         ws, rank = _dist()
         return run_batch_sharded(args, ws, rank) if ws > 1 else run_batch(args)
-    if args.workload == "thorax_abd":
-        return run_thorax(args)
+    if args.workload == "oracle_timing":
+        return run_oracle_timing(args)
     if args.workload == "conv3d":
         return run_conv3d(args)
     if args.impl == "reference":

@@ -128,8 +128,8 @@ ngf_status gn_hessvec(ngf_plan* plan, const float* R, const float* T, const floa
 ngf_status curvature_apply(ngf_plan* plan, const float* p, float* q, double* Sp);
 
 /* Exact diagonal of H + alpha grad^2 S at u (the Jacobi preconditioner of
- * the PCG solve), device 3*N.  Its image-grid part is accumulated with
- * shared-memory atomics, so the last bits can differ between calls. */
+ * the PCG solve), device 3*N.  Its image-grid part is summed in a fixed
+ * order without atomics: repeated calls return bitwise identical results. */
 ngf_status ngf_gn_diagonal(ngf_plan* plan, const float* R, const float* T, const float* u,
                            float* diag);
 
@@ -292,9 +292,13 @@ ngf_status register_batch(int32_t npairs, const ngf_level_desc* finest, const ng
  *  - All calls share the array and it keeps the last call's contents (every
  *    call clears what must start at zero); calls that overlap on the GPU, on
  *    one device, race and give wrong results.
- *  - Limits: at most NGF_NOALLOC_MAX_AXIS image cells per axis and at most
- *    NGF_NOALLOC_MAX_BLOCKS thread blocks of the image pass (about 6e8
- *    voxels); larger problems return NGF_EBOUNDS with a message.
+ *  - Limits: at most NGF_NOALLOC_MAX_AXIS image cells per axis, and at
+ *    most NGF_NOALLOC_MAX_BLOCKS thread blocks of the image pass, i.e.
+ *    ceil(m0/32) * ceil(m1/16) * chunks <= 16384, where chunks (the number
+ *    of z-chunks, about 2 * SMs / (ceil(m0/32) * ceil(m1/16)), at least 1)
+ *    is 1 or 2 for large slices: only slices wider than about 16384 tiles
+ *    of 32 x 16 cells are refused.  Larger problems return NGF_EBOUNDS with
+ *    a message before anything is launched.
  * R, T, u: device arrays as for ngf_objective; dev_DS: device, 2 doubles
  * (D, S); enqueued on cuda_stream, no synchronisation. */
 #define NGF_NOALLOC_MAX_AXIS 4096

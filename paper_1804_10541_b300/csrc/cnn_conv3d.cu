@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "ngf.h"
 #include "ngf_cnn.h"
@@ -330,6 +331,24 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
     }
 }
 
+// The brick kernel's dynamic shared-memory limit is raised once per device
+// (the attribute is per device), under a lock.
+std::mutex g_brick_mu;
+bool g_brick_attr[256] = {};
+
+bool brick_attr_set() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return false;
+    std::lock_guard<std::mutex> lock(g_brick_mu);
+    if (!g_brick_attr[dev]) {
+        if (cudaFuncSetAttribute(k_conv3d_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess)
+            return false;
+        g_brick_attr[dev] = true;
+    }
+    return true;
+}
+
 }  // namespace
 }  // namespace ngf
 
@@ -348,7 +367,12 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
     if (((uintptr_t)x | (uintptr_t)w | (uintptr_t)y) & 15u) return NGF_EINVAL;
     int ncols = 32;
     while (ncols < Cout) ncols <<= 1;
-    const size_t per_sm = 228 * 1024;
+    int dev = 0, sm_count = 0, smem_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+        return NGF_ECUDA;
+    const size_t per_sm = (size_t)smem_sm;
     {
         // brick form: P output planes per CTA, as many as leave room for two
         // CTAs per SM (256 tensor-memory columns, about 110 KB of shared
@@ -379,7 +403,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         }
         br.tiles_z = (D + br.P - 1) / br.P;
         const long long tiles = (long long)br.tiles_x * br.tiles_y * br.tiles_z * B;
-        while (br.ns % 32 == 0 && tiles * (Cout / br.ns) < 148) br.ns /= 2;
+        while (br.ns % 32 == 0 && tiles * (Cout / br.ns) < sm_count) br.ns /= 2;
         br.ncols = 32;
         while (br.ncols < br.ns) br.ncols <<= 1;
         const size_t wst = (size_t)br.ns * br.kc * 2;
@@ -398,13 +422,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         const size_t smem_min = per_sm / (ctas + 1) - 1024 + 16;
         if (smem < smem_min) smem = smem_min;
         if (tiles >= (1LL << 31) || smem > 200 * 1024) return NGF_EBOUNDS;
-        static bool battr = false;
-        if (!battr) {
-            if (cudaFuncSetAttribute(k_conv3d_brick, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
-                cudaSuccess)
-                return NGF_ECUDA;
-            battr = true;
-        }
+        if (!brick_attr_set()) return NGF_ECUDA;
         // weights repacked per (slice, chunk, tap) into the B operand's
         // shared-memory image
         cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);

@@ -139,9 +139,13 @@ extern "C" ngf_status ngf_objective_noalloc(const ngf_level_desc* d, const float
     if (!is_device_ptr(R) || !is_device_ptr(T) || !is_device_ptr(u) || !is_device_ptr(dev_DS))
         return set_error(nullptr, NGF_EINVAL, "ngf_objective_noalloc: R, T, u and dev_DS must be device pointers");
 
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int dev = 0, sms = 0;
+    {
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_check(nullptr, e, "cudaGetDevice");
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_check(nullptr, e, "cudaDeviceGetAttribute(multiprocessor count)");
+    }
     // same z-chunking as a plan: about two CTAs per SM, at least 8 planes per chunk
     const long long txy = (long long)((d->m[0] + TX - 1) / TX) * ((d->m[1] + TY - 1) / TY);
     long long nchunk = (2LL * sms + txy / 2) / txy;

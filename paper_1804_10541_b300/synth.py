@@ -269,9 +269,12 @@ class _Thorax:
         return v.clamp(-1000.0, 1500.0)
 
 
-def thorax_pair(m=(512, 512, 900), h=(0.8, 0.8, 1.0), seed=20, device="cpu", noise=20.0, max_disp=20.0):
+def thorax_pair(m=(512, 512, 900), h=(0.8, 0.8, 1.0), seed=20, device="cpu", noise=20.0, max_disp=20.0,
+                zrange=None):
     """Thorax-abdomen-shaped pair.  Seeds: +1 (R noise), +2 (u*: 8 Fourier
-    modes, scaled to max |u*| = max_disp mm), +3 (T noise)."""
+    modes, scaled to max |u*| = max_disp mm), +3 (T noise).  zrange = (z0, z1)
+    evaluates only those image planes of the same phantom and displacement
+    (the noise is drawn for the slab alone)."""
     dtype = torch.float32
     ph = _Thorax(m, h)
     ext = ph.ext
@@ -295,13 +298,14 @@ def thorax_pair(m=(512, 512, 900), h=(0.8, 0.8, 1.0), seed=20, device="cpu", noi
     Xs, Ys, Zs = _axes(m, h, 0, m[2], "cpu", torch.float64)
     f = field(Xs[:, :, ::8], Ys[:, ::8, :], Zs[::8])
     scale = max_disp / float(torch.sqrt(f[0] ** 2 + f[1] ** 2 + f[2] ** 2).max())
-    M = m[0] * m[1] * m[2]
+    za, zb = (0, m[2]) if zrange is None else zrange
+    M = m[0] * m[1] * (zb - za)
     R = torch.empty(M, dtype=dtype, device=device)
     T = torch.empty(M, dtype=dtype, device=device)
     U = torch.empty(3, M, dtype=dtype, device=device)
     plane = m[0] * m[1]
-    for z0, z1 in _slabs(m[2], 16):
-        X, Y, Z = _axes(m, h, z0, z1, device, dtype)
+    for z0, z1 in _slabs(zb - za, 16):
+        X, Y, Z = _axes(m, h, za + z0, za + z1, device, dtype)
         shp = (z1 - z0, m[1], m[0])
         u = [(c * scale).expand(shp) for c in field(X, Y, Z)]
         R[z0 * plane:z1 * plane] = ph(X.expand(shp), Y.expand(shp), Z.expand(shp)).reshape(-1)
@@ -310,7 +314,7 @@ def thorax_pair(m=(512, 512, 900), h=(0.8, 0.8, 1.0), seed=20, device="cpu", noi
             U[d, z0 * plane:z1 * plane] = u[d].reshape(-1)
     gR = torch.Generator(device="cpu").manual_seed(seed + 1)
     gT = torch.Generator(device="cpu").manual_seed(seed + 3)
-    for z0, z1 in _slabs(m[2], 64):
+    for z0, z1 in _slabs(zb - za, 64):
         sl = slice(z0 * plane, z1 * plane)
         R[sl] += noise * torch.randn(sl.stop - sl.start, generator=gR, dtype=dtype).to(device)
         T[sl] += noise * torch.randn(sl.stop - sl.start, generator=gT, dtype=dtype).to(device)
@@ -345,6 +349,31 @@ def batch_pairs(count=64, lo=64, hi=192, seed=30, device="cpu"):
         out.append((R, T, dict(m=m, h=(1.0, 1.0, 1.0), n=(N // 2 + 1,) * 3, alpha=1.0, tau=0.1, rho=0.1,
                                levels=2)))
     return out
+
+
+def smooth_nodal_field(n, hy, seed, max_disp, modes=6, device="cpu"):
+    """Smooth displacement on the node grid (n nodes per axis at spacing hy,
+    node j at j * hy): per component a sum of `modes` low-frequency sines
+    (numpy PCG64, `seed`), scaled so that the largest |u| over the nodes is
+    max_disp (units of hy).  3 * prod(n) float32, component-major."""
+    r = _rng(seed)
+    freq = r.integers(0, 3, size=(modes, 3))
+    freq[np.all(freq == 0, axis=1), 0] = 1
+    amp = r.normal(size=(modes, 3))
+    phase = r.uniform(0, 2 * math.pi, size=(modes, 3))
+    ext = [(n[a] - 1) * hy[a] for a in range(3)]
+    X, Y, Z = (((torch.arange(n[a], dtype=torch.float64) * hy[a]) / ext[a]) for a in range(3))
+    X, Y, Z = X.view(1, 1, -1), Y.view(1, -1, 1), Z.view(-1, 1, 1)
+    comps = []
+    for d in range(3):
+        acc = torch.zeros(n[2], n[1], n[0], dtype=torch.float64)
+        for k in range(modes):
+            acc = acc + amp[k, d] * torch.sin(math.pi * (freq[k, 0] * X + freq[k, 1] * Y + freq[k, 2] * Z)
+                                              + phase[k, d])
+        comps.append(acc.reshape(-1))
+    U = torch.stack(comps)
+    U = U * (max_disp / float(torch.sqrt((U ** 2).sum(0)).max()))
+    return U.reshape(-1).to(torch.float32).to(device)
 
 
 def random_fields(n_nodes, seed, amp=0.3, device="cpu"):

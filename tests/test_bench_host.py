@@ -76,9 +76,10 @@ def test_stored_traffic_tracks_the_kernel_source(tmp_path, monkeypatch):
     prof.write_text(f"x\ntraffic_bytes_per_launch: 123\nimage_pass_source_sha256: {h}\n")
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     monkeypatch.setattr(b, "image_pass_source_hash", lambda: h)
-    assert b.stored_traffic() == 123.0
+    assert b.stored_traffic("lung_ct") == 123.0
+    assert b.stored_traffic("thorax_abd") is None  # no capture of that workload here
     prof.write_text("x\ntraffic_bytes_per_launch: 123\nimage_pass_source_sha256: 00\n")
-    assert b.stored_traffic() is None
+    assert b.stored_traffic("lung_ct") is None
 
 
 def test_shard_pairs_partitions_and_balances():

@@ -102,3 +102,24 @@ def test_conv3d_empty_and_bad_arguments(ngf):
         with pytest.raises(ngf.NGFError):
             ngf.ngf_conv3d_fwd(x, w, None, y)
     assert ngf.ngf_conv3d_check() == 0
+
+
+# Volumes with at least as many output tiles (8 x 16 x P voxels) as the GPU
+# has SMs, so that no output-channel slicing happens and every CTA computes
+# all output channels of its tile (the path the 64^3 and 128^3 layers take).
+LARGE_CASES = [
+    (1, 32, 48, 64, 32, 64),
+    (1, 40, 64, 64, 16, 16),
+]
+
+
+@pytest.mark.parametrize("shape", LARGE_CASES)
+def test_conv3d_matches_oracle_full_grid(ngf, shape):
+    B, D, H, W, Ci, Co = shape
+    tiles = ((W + 7) // 8) * ((H + 15) // 16) * ((D + 3) // 4) * B
+    assert tiles >= torch.cuda.get_device_properties(0).multi_processor_count
+    x, w, b = _inputs(shape, seed=sum(shape), bias=True)
+    y = torch.full(shape[:4] + (Co,), float("nan"), device="cuda")
+    ngf.ngf_conv3d_fwd(x.cuda(), w.cuda(), b.cuda(), y, relu=True)
+    assert ngf.ngf_conv3d_check() == 0
+    _check(x, w, y, b, relu=True)

@@ -67,3 +67,30 @@ def test_noalloc_objective_rejects_oversized(ngf):
     with pytest.raises(ngf.NGFError) as e:
         ngf.ngf_objective_noalloc(desc, t, t, t, out)
     assert e.value.status == -8 and "NGF_NOALLOC_MAX_AXIS" in str(e.value)
+
+
+def test_noalloc_objective_rejects_wide_slices(ngf):
+    """A 4096 x 4096 slice needs 128 x 256 image-pass blocks, above
+    NGF_NOALLOC_MAX_BLOCKS; the call is refused before any launch."""
+    desc = ngf.level_desc((4096, 4096, 1), (1, 1, 1), (3, 3, 2))
+    t = torch.zeros(16, device="cuda")
+    out = torch.zeros(2, device="cuda", dtype=torch.float64)
+    with pytest.raises(ngf.NGFError) as e:
+        ngf.ngf_objective_noalloc(desc, t, t, t, out)
+    assert e.value.status == -8 and "NGF_NOALLOC_MAX_BLOCKS" in str(e.value)
+
+
+def test_noalloc_objective_allocates_nothing(ngf):
+    """After a first call on the device (which looks up the scratch array's
+    address), a further call leaves the device's free memory unchanged."""
+    c = G.random_case((70, 35, 21), (1.0, 1.0, 2.5), (36, 18, 11), seed=10)
+    out = torch.zeros(2, device="cuda", dtype=torch.float64)
+    ngf.ngf_objective_noalloc(c.desc, c.R, c.T, c.u, out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    ngf.ngf_objective_noalloc(c.desc, c.R, c.T, c.u, out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    D0, _ = _reference(ngf, c)
+    assert abs(out[0].item() - D0) <= G.TOL_OBJ * abs(D0)
