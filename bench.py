@@ -706,6 +706,83 @@ def run_conv3d(args):
     return 0
 
 
+def run_learned(args):
+    """Learned initializer (the encoder-decoder of ngf_cnn.h) end to end:
+    `--learned-train` + `--learned-test` lung-CT-like pairs at 128^3
+    (2 x 2 x 2.34 mm, 65^3 nodes, 4 levels) generated on the device, all
+    registered by plain multilevel Gauss-Newton (batched, 10 GN x 20 PCG per
+    level) for the training targets, training on the GPU (Adam, batch 8), and
+    on the held-out pairs plain Gauss-Newton from zero against the network's
+    start refined by Gauss-Newton, both to the same final objective (within
+    0.1% of plain Gauss-Newton's full-schedule J)."""
+    import numpy as np
+    import torch
+    from paper_1804_10541_b300 import learned as LR, ngf
+    dev = torch.device("cuda", 0)
+    s, ntr, nte = 128, args.learned_train, args.learned_test
+    w = LR.workload(s)
+    t0 = time.perf_counter()
+    R, T = LR.make_pairs(s, 0, ntr + nte, dev)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    U0, Jb = LR.register_all(R, T, w)
+    torch.cuda.synchronize()
+    t_reg = time.perf_counter() - t0
+    U1 = LR.level1_targets(U0, w["n"][0])
+    del U0
+    Rtr, Ttr, U1tr = R[:ntr], T[:ntr], U1[:ntr].contiguous()
+    Rte, Tte, U1te = R[ntr:], T[ntr:], U1[ntr:].contiguous()
+    batch = 8
+    d = ngf.net_desc(s, batch, LR.IN_SHIFT, LR.IN_SCALE, LR.OUT_SCALE)
+    launches0 = ngf.ngf_launch_count()
+    with ngf.Net(d) as net:
+        ngf.ngf_net_set_params(net.handle, torch.from_numpy(LR.init_params(7)))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        losses = LR.train(net, Rtr, Ttr, U1tr, epochs=args.learned_epochs, batch=batch, lr0=1e-3,
+                          log=lambda m: print(m, file=sys.stderr, flush=True))
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        assert ngf.ngf_conv3d_check() == 0
+        pred = LR.predict(net, Rte, Tte, batch)
+        mse_net = float(((pred - U1te) ** 2).mean())
+        mse_zero = float((U1te ** 2).mean())
+        rows = LR.compare(net, Rte, Tte, w, k1=args.learned_k1, finest_cap=30)
+    launches = ngf.ngf_launch_count() - launches0
+    # training throughput in tensor-core FLOP: forward over all layers, data
+    # gradient of all but the first, weight gradient of all
+    vol = [s ** 3, (s // 2) ** 3, (s // 4) ** 3, (s // 8) ** 3, (s // 4) ** 3, (s // 4) ** 3, (s // 4) ** 3]
+    fwd = [2.0 * 27 * v * ci * co for v, (ci, co) in zip(vol, LR.LAYERS)]
+    step_flop = batch * (2 * sum(fwd) + sum(fwd[1:]))
+    steps = args.learned_epochs * ((ntr + batch - 1) // batch)
+    reached = [r for r in rows if r["learned_reached"]]
+    line = {"workload": f"learned initializer: {ntr} training + {nte} held-out lung-CT-like pairs at {s}^3 "
+                        f"(2x2x2.34 mm, 65^3 nodes, 4 levels, 10 GN x 20 PCG); 4-level encoder-decoder 16..128 "
+                        f"channels, bf16 activations, FP32 accumulation; Adam batch {batch}, "
+                        f"{args.learned_epochs} epochs",
+            "metric": "full-registration seconds at equal NGF", "unit": "s", "higher_is_better": False,
+            "value": float(np.mean([r["learned_s"] for r in reached])) if reached else None,
+            "plain_gn_s_mean": float(np.mean([r["plain_s"] for r in rows])),
+            "plain_gn_full_schedule_s_mean": float(np.mean([r["full_s"] for r in rows])),
+            "learned_s_mean_over_reached": float(np.mean([r["learned_s"] for r in reached])) if reached else None,
+            "plain_s_mean_over_reached": float(np.mean([r["plain_s"] for r in reached])) if reached else None,
+            "speedup_at_equal_J": (float(np.mean([r["plain_s"] for r in reached]) /
+                                         np.mean([r["learned_s"] for r in reached])) if reached else None),
+            "gn_steps_plain_mean": float(np.mean([r["plain_gn"] for r in rows])),
+            "gn_steps_learned_mean_over_reached": float(np.mean([r["learned_gn"] for r in reached])) if reached else None,
+            "held_out_reached_J_within_0.1pct": len(reached), "held_out": len(rows),
+            "learned_J_rel_to_ref_median": float(np.median([(r["learned_J"] - r["J_ref"]) / r["J_ref"] for r in rows])),
+            "held_out_mse_mm2": {"network": mse_net, "zero_start": mse_zero},
+            "train_loss_first_last_epoch": [losses[0], losses[-1]],
+            "seconds": {"generate": t_gen, "register_targets": t_reg, "train": t_train},
+            "train_tflops": step_flop * steps / t_train / 1e12, "train_pairs_per_s": ntr * args.learned_epochs / t_train,
+            "gpu_launches": int(launches), "dtype": "bf16 x bf16 -> f32 (network), f32 (registration)",
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _meminfo_gb(key="MemAvailable"):
     try:
         with open("/proc/meminfo") as f:
@@ -830,11 +907,15 @@ def main():
     ap.add_argument("--slab", type=int, default=0, help="--kernel-case: central z-slab of this many planes")
     ap.add_argument("--distance", default="ngf", choices=["ngf", "ssd"], help="distance of --kernel-case")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[*REG_WORKLOADS, "batch_64", "conv3d", "oracle_timing"],
+                    choices=[*REG_WORKLOADS, "batch_64", "conv3d", "oracle_timing", "learned"],
                     help="thorax_abd (default) / lung_ct: full registrations; batch_64: the batched form on 64 "
                          "uneven pairs; conv3d: the tensor-core convolution layers; oracle_timing: the FP64 "
                          "oracle on the host cores (each of the last three prints its own JSON line)")
     ap.add_argument("--threads", type=int, default=0, help="oracle_timing: OpenMP threads of one leg")
+    ap.add_argument("--learned-train", type=int, default=4000)
+    ap.add_argument("--learned-test", type=int, default=500)
+    ap.add_argument("--learned-epochs", type=int, default=8)
+    ap.add_argument("--learned-k1", type=int, default=3, help="learned: Gauss-Newton steps on level 1")
     args = ap.parse_args()
     if args.kernel_case:
         return run_kernel_case(args)
@@ -843,6 +924,8 @@ def main():
         return run_batch_sharded(args, ws, rank) if ws > 1 else run_batch(args)
     if args.workload == "oracle_timing":
         return run_oracle_timing(args)
+    if args.workload == "learned":
+        return run_learned(args)
     if args.workload == "conv3d":
         return run_conv3d(args)
     if args.impl == "reference":

@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define NGF_ABI_VERSION 2
+#define NGF_ABI_VERSION 3
 
 typedef enum {
     NGF_OK = 0,
@@ -203,6 +203,12 @@ typedef struct {
                              the Gauss-Newton diagonal at each level's start   */
     int32_t zc;           /* z-chunk length of every level's plans; 0 = the
                              default (per plan; per batch in register_batch)  */
+    int32_t gn_iters_finest; /* > 0: Gauss-Newton steps on level 0 instead of
+                             gn_iters (coarser levels keep gn_iters); GN only  */
+    double  j_target;     /* > 0: stop level 0 once J <= j_target (checked at
+                             the start of each of its steps, i.e. after every
+                             accepted step); 0 = off.  Used to compare starts
+                             at equal final objective.  GN only.              */
 } ngf_options;
 enum { NGF_METHOD_GN = 0, NGF_METHOD_LBFGS = 1 };
 

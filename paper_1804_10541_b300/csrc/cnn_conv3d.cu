@@ -129,8 +129,8 @@ struct BrickArgs {
     const uint4* x;
     const uint4* w;   // packed: [slice][chunk][tap] images of ns x kc
     const float* bias;
-    float* y;
-    int B, D, H, W, cin, cout, relu;
+    void* y;          // float, or bf16 when out_bf16
+    int B, D, H, W, cin, cout, relu, out_bf16;
     int P;            // output planes per CTA
     int ns;           // output channels per CTA
     int ncols;        // tensor-memory columns per accumulator
@@ -155,6 +155,33 @@ __global__ void k_conv3d_pack_w(const uint4* __restrict__ w, uint4* __restrict__
         const int tap = (int)(st % 27), chunk = (int)((st / 27) % nch), slice = (int)(st / (27LL * nch));
         wp[st * per_stage + operand_off(n, q, ns) / 16] =
             w[((long long)(slice * ns + n) * 27 + tap) * (cin / 8) + chunk * qk + q];
+    }
+}
+
+// Data-gradient weights: the data gradient of y = conv(x, w) is the
+// convolution of dy with the taps mirrored and the channel roles swapped,
+// w'[c][tap][o] = w[o][26 - tap][c]; this packs w' (read element by element
+// from the forward layout w[cout][27][cin]) into the same shared-memory image
+// as k_conv3d_pack_w, for a convolution with cin' = cout and cout' = cin.
+__global__ void k_conv3d_pack_wT(const __nv_bfloat16* __restrict__ w, uint4* __restrict__ wp, int cout_f,
+                                 int cin_f, int ns, int kc) {
+    const int cinp = cout_f, coutp = cin_f;  // channels of the mirrored convolution
+    const int qk = kc / 8, per_stage = ns * qk, nch = cinp / kc;
+    const long long total = (long long)(coutp / ns) * nch * 27 * per_stage;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long st = idx / per_stage;
+        const int r = (int)(idx - st * per_stage), n = r / qk, q = r - n * qk;
+        const int tap = (int)(st % 27), chunk = (int)((st / 27) % nch), slice = (int)(st / (27LL * nch));
+        const int oc = slice * ns + n;  // output channel of the mirrored convolution = forward input channel
+        uint32_t pk[4];
+        for (int e = 0; e < 8; e += 2) {
+            const int ic0 = chunk * kc + 8 * q + e;  // input channel = forward output channel
+            const __nv_bfloat16 lo = w[((long long)ic0 * 27 + (26 - tap)) * cin_f + oc];
+            const __nv_bfloat16 hi = w[((long long)(ic0 + 1) * 27 + (26 - tap)) * cin_f + oc];
+            pk[e / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+        }
+        wp[st * per_stage + operand_off(n, q, ns) / 16] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
 }
 
@@ -301,8 +328,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         for (int p = 0; p < P; ++p) {
             const int vz = z0 + p;
             const bool row_ok = vx < a.W && vy < a.H && vz < a.D;
-            float* out =
-                a.y + (row_ok ? ((((long long)b * a.D + vz) * a.H + vy) * a.W + vx) * a.cout + n0 : 0);
+            const long long obase = row_ok ? ((((long long)b * a.D + vz) * a.H + vy) * a.W + vx) * a.cout + n0 : 0;
             for (int cc = 0; cc < ns; cc += 16) {
                 float r[16];
                 tmem_load16(tmem + lane_base + (uint32_t)(p * a.ncols + cc), r);
@@ -312,9 +338,22 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
                         float v = r[i] + (a.bias ? a.bias[n0 + cc + i] : 0.0f);
                         r[i] = (a.relu && v < 0.0f) ? 0.0f : v;
                     }
+                    if (a.out_bf16) {
+                        uint32_t pk[8];
 #pragma unroll
-                    for (int i = 0; i < 16; i += 4)
-                        *reinterpret_cast<float4*>(out + cc + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
+                        for (int i = 0; i < 8; ++i) {
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(r[2 * i], r[2 * i + 1]);
+                            pk[i] = *reinterpret_cast<const uint32_t*>(&h2);
+                        }
+                        uint4* out = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.y) + obase + cc);
+                        out[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                        out[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    } else {
+                        float* out = static_cast<float*>(a.y) + obase + cc;
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4*>(out + i) = make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
+                    }
                 }
             }
         }
@@ -354,9 +393,236 @@ bool brick_attr_set() {
 
 using namespace ngf;
 
-extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* bias, float* y, int32_t B,
-                                     int32_t D, int32_t H, int32_t W, int32_t Cin, int32_t Cout, int32_t relu,
-                                     void* cuda_stream) {
+namespace ngf {
+namespace {
+
+// ---- weight gradient ------------------------------------------------------
+//
+// dw[o][tap][c] = sum_v dy[v][o] x[v + tap][c] is a GEMM with rows o (M),
+// columns c (N) and the voxels as the reduction (K), one accumulator per
+// tap.  A CTA owns one column group (an input-channel chunk of kc channels
+// and a group of tg taps: tg * kc <= 256 tensor-memory columns) and a range
+// of output tiles of 16 (x) x TY x TZ voxels, and accumulates over all its
+// tiles in tensor memory.  Per tile, the dy tile and the x brick (tile plus
+// a one-voxel halo, kc channels) are copied to shared memory once, both
+// channel-group major with 16 bytes (8 channels) per voxel, which makes
+// both operands MN-major: a core matrix is 8 consecutive voxels (K) x 8
+// channels (M or N), 128 contiguous bytes.  The K = 16 slab of one MMA is
+// one x line of the tile; the B operand of tap (dz, dy, dx) is the brick
+// line moved by (dz, dy, dx) voxels.  M is 128 (output channels beyond cout
+// read neighbouring shared memory and their accumulator lanes are never
+// read).  The CTA's partial sums go to global memory and a second kernel
+// adds the CTAs of each column group in a fixed order (deterministic).
+
+constexpr int WG_TX = 16;
+
+struct WgradArgs {
+    const uint4* x;    // [V][cin / 8]
+    const uint4* dy;   // [V][cout / 8]
+    float* part;       // [split][ngroups][cout][gcols]
+    int B, D, H, W, cin, cout;
+    int kc;            // input channels per chunk (N of the MMA)
+    int tg, ntg;       // taps per group, tap groups
+    int ngroups;       // chunks x tap groups
+    int gcols;         // tg * kc
+    int tcols;         // tensor-memory columns allocated
+    int TY, TZ;        // tile extent in y and z (x: WG_TX)
+    int tiles_x, tiles_y, tiles_z, ntiles;
+    int split;         // CTAs per column group
+    uint32_t a_bytes;  // shared-memory bytes of the dy tile region (with slack)
+};
+
+// Instruction descriptor of kind::f16 with both operands MN-major
+// ("transposed" A and B bits set), FP32 accumulator, BF16 inputs.
+__host__ __device__ constexpr uint32_t instr_desc_mn(int m, int n) {
+    return instr_desc(m, n) | (1u << 15) | (1u << 16);
+}
+
+__global__ void __launch_bounds__(CONV_THREADS) k_conv3d_wgrad(const WgradArgs a) {
+    NGF_DYNAMIC_SMEM(smem);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int cgo = a.cout / 8, cgi = a.kc / 8;
+    const int bx = WG_TX + 2, by = a.TY + 2, bz = a.TZ + 2, nbv = bx * by * bz;
+    const int ntv = WG_TX * a.TY * a.TZ, lines = a.TY * a.TZ;
+    const uint32_t sA = smem_addr(smem), sB = sA + a.a_bytes;
+    const uint32_t b_bytes = (uint32_t)(cgi + 1) * nbv * 16;  // one channel-group plane of slack
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + a.a_bytes + b_bytes);
+    int* flags = reinterpret_cast<int*>(bar + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags + 2);
+
+    const int grp = blockIdx.y, chunk = grp / a.ntg, tgi = grp % a.ntg;
+    const int tap0 = tgi * a.tg, ntap = min(a.tg, 27 - tap0);
+    const int t0 = (int)((long long)blockIdx.x * a.ntiles / a.split);
+    const int t1 = (int)((long long)(blockIdx.x + 1) * a.ntiles / a.split);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"((uint32_t)a.tcols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_addr(bar), 1);
+        flags[0] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t tmem = 0;
+    bool failed = false;
+    int issued = 0;  // tiles whose MMAs were committed
+    for (int t = t0; t < t1; ++t) {
+        if (t > t0) {
+            // the previous tile's MMAs have read shared memory
+            const bool ok = mbar_wait(smem_addr(bar), (uint32_t)((issued - 1) & 1));
+            if (__syncthreads_or(!ok || flags[0] != 0)) { failed = true; break; }
+        }
+        int r = t;
+        const int tx = r % a.tiles_x; r /= a.tiles_x;
+        const int ty = r % a.tiles_y; r /= a.tiles_y;
+        const int tz = r % a.tiles_z;
+        const int b = r / a.tiles_z;
+        const int x0 = tx * WG_TX, y0 = ty * a.TY, z0 = tz * a.TZ;
+        // dy tile: voxel v = (z * TY + y) * 16 + x at ((v / 8) * cgo + g) * 128 + (v % 8) * 16
+        for (int idx = tid; idx < ntv * cgo; idx += CONV_THREADS) {
+            const int g = idx % cgo, v = idx / cgo;
+            const int vx = v % WG_TX, vy = (v / WG_TX) % a.TY, vz = v / (WG_TX * a.TY);
+            const int gx = x0 + vx, gy = y0 + vy, gz = z0 + vz;
+            const bool in = gx < a.W && gy < a.H && gz < a.D;
+            const uint4* src = a.dy;
+            if (in) src += ((((long long)b * a.D + gz) * a.H + gy) * a.W + gx) * cgo + g;
+            cp16_ca(sA + (uint32_t)(((v >> 3) * cgo + g) * 128 + (v & 7) * 16), src, in ? 16u : 0u);
+        }
+        // x brick of this chunk, channel-group planes of nbv voxels, zero outside
+        for (int idx = tid; idx < nbv * cgi; idx += CONV_THREADS) {
+            const int g = idx % cgi, v = idx / cgi;
+            const int ux = v % bx, uy = (v / bx) % by, uz = v / (bx * by);
+            const int gx = x0 - 1 + ux, gy = y0 - 1 + uy, gz = z0 - 1 + uz;
+            const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H && gz >= 0 && gz < a.D;
+            const uint4* src = a.x;
+            if (in) src += ((((long long)b * a.D + gz) * a.H + gy) * a.W + gx) * (a.cin / 8) + chunk * cgi + g;
+            cp16_ca(sB + (uint32_t)(g * nbv + v) * 16, src, in ? 16u : 0u);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = *tmem_slot;
+        if (tid == 0) {
+            const uint32_t idesc = instr_desc_mn(128, a.kc);
+            // no swizzle, MN-major as K-major: the stride byte offset steps
+            // between core matrices along M/N, the leading byte offset along K
+            const uint32_t a_mn = 128, a_k = (uint32_t)cgo * 128;
+            const uint32_t b_mn = (uint32_t)nbv * 16, b_k = 128;
+            for (int j = 0; j < ntap; ++j) {
+                const int tap = tap0 + j;
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                for (int l = 0; l < lines; ++l) {
+                    const int yy = l % a.TY, zz = l / a.TY;
+                    const uint64_t ad = smem_desc(sA + (uint32_t)(2 * l * cgo) * 128, a_k, a_mn);
+                    const uint64_t bd =
+                        smem_desc(sB + (uint32_t)(((zz + dz) * by + (yy + dy)) * bx + dx) * 16, b_k, b_mn);
+                    mma_bf16(tmem + (uint32_t)(j * a.kc), ad, bd, idesc, (t > t0 || l > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(smem_addr(bar));
+        }
+        __syncwarp();
+        ++issued;
+    }
+    if (!failed && issued > 0) {
+        const bool ok = mbar_wait(smem_addr(bar), (uint32_t)((issued - 1) & 1));
+        failed = __syncthreads_or(!ok || flags[0] != 0);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tmem = *tmem_slot;
+    if (!failed) {
+        const int co = warp * 32 + (tid & 31);
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float* out = a.part + (((long long)blockIdx.x * a.ngroups + grp) * a.cout + (co < a.cout ? co : 0)) * a.gcols;
+        for (int c = 0; c < ntap * a.kc; c += 16) {
+            float v[16];
+            if (issued > 0) {
+                tmem_load16(tmem + lane_base + (uint32_t)c, v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+            }
+            if (co < a.cout) {
+#pragma unroll
+                for (int i = 0; i < 16; i += 4)
+                    *reinterpret_cast<float4*>(out + c + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+        }
+    } else if (tid == 0) {
+        atomicAdd(&g_conv_timeouts, 1u);
+        mbar_wait(smem_addr(bar), (uint32_t)((issued - 1) & 1));  // MMAs still in flight (bounded)
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tcols)
+                     : "memory");
+    }
+}
+
+// dw[o][tap][c] = sum over the split CTAs of their partial sums, in order.
+__global__ void k_conv3d_wgrad_reduce(const float* __restrict__ part, float* __restrict__ dw, int cout, int cin,
+                                      int kc, int tg, int ntg, int ngroups, int gcols, int split) {
+    const long long total = (long long)cout * 27 * cin;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % cin), tap = (int)((i / cin) % 27), o = (int)(i / (27LL * cin));
+        const int grp = (c / kc) * ntg + tap / tg, col = (tap % tg) * kc + c % kc;
+        float acc = 0.0f;
+        for (int s = 0; s < split; ++s) acc += part[(((long long)s * ngroups + grp) * cout + o) * gcols + col];
+        dw[i] = acc;
+    }
+}
+
+// db[o] = sum_v dy[v][o]: per block a float partial over a contiguous voxel
+// range (thread o sums channel o), then the blocks in order.
+__global__ void k_bias_grad_part(const __nv_bfloat16* __restrict__ dy, float* __restrict__ part, long long V,
+                                 int cout, int per_block) {
+    const long long v0 = (long long)blockIdx.x * per_block;
+    const long long v1 = v0 + per_block < V ? v0 + per_block : V;
+    for (int o = threadIdx.x; o < cout; o += blockDim.x) {
+        float acc = 0.0f;
+        for (long long v = v0; v < v1; ++v) acc += __bfloat162float(dy[v * cout + o]);
+        part[(long long)blockIdx.x * cout + o] = acc;
+    }
+}
+
+__global__ void k_bias_grad_sum(const float* __restrict__ part, float* __restrict__ db, int nblocks, int cout) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < cout; o += gridDim.x * blockDim.x) {
+        float acc = 0.0f;
+        for (int k = 0; k < nblocks; ++k) acc += part[(long long)k * cout + o];
+        db[o] = acc;
+    }
+}
+
+std::mutex g_wg_mu;
+bool g_wg_attr[256] = {};
+
+bool wgrad_attr_set() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) return false;
+    std::lock_guard<std::mutex> lock(g_wg_mu);
+    if (!g_wg_attr[dev]) {
+        if (cudaFuncSetAttribute(k_conv3d_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess)
+            return false;
+        g_wg_attr[dev] = true;
+    }
+    return true;
+}
+
+// Brick-form convolution of x [V][cin] with packed weights: w is either the
+// layer's own weights [cout][27][cin] or, when mirrored, the weights of a
+// forward layer with cin_f = cout and cout_f = cin (the data gradient).
+ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bias, void* y, bool out_bf16,
+                    int32_t B, int32_t D, int32_t H, int32_t W, int32_t Cin, int32_t Cout, int32_t relu,
+                    void* cuda_stream) {
     if (B < 0 || D < 0 || H < 0 || W < 0) return NGF_EINVAL;
     if (Cin < 16 || Cin % 16 != 0 || (Cin > CONV_KMAX && Cin % CONV_KMAX != 0)) return NGF_EINVAL;
     if (Cout < 16 || Cout > 256 || Cout % 16 != 0) return NGF_EINVAL;
@@ -384,6 +650,7 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         br.x = static_cast<const uint4*>(x);
         br.bias = bias;
         br.y = y;
+        br.out_bf16 = out_bf16 ? 1 : 0;
         br.B = B; br.D = D; br.H = H; br.W = W;
         br.cin = Cin; br.cout = Cout; br.relu = relu ? 1 : 0;
         br.kc = Cin <= CONV_KMAX ? Cin : CONV_KMAX;
@@ -429,15 +696,135 @@ extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* 
         void* wp = nullptr;
         if (dev_alloc(&wp, 27 * (size_t)Cout * Cin * 2, st) != cudaSuccess) return NGF_ENOMEM;
         const long long chunks = 27LL * Cout * (Cin / 8);
-        const bool ok = launch(k_conv3d_pack_w, dim3((unsigned)((chunks + 255) / 256)), dim3(256), 0, st,
-                               static_cast<const uint4*>(w), static_cast<uint4*>(wp), (int)Cout, (int)Cin,
-                               br.ns, br.kc) == cudaSuccess &&
+        const dim3 pg((unsigned)((chunks + 255) / 256));
+        const cudaError_t pe =
+            mirrored ? launch(k_conv3d_pack_wT, pg, dim3(256), 0, st, static_cast<const __nv_bfloat16*>(w),
+                              static_cast<uint4*>(wp), (int)Cin, (int)Cout, br.ns, br.kc)
+                     : launch(k_conv3d_pack_w, pg, dim3(256), 0, st, static_cast<const uint4*>(w),
+                              static_cast<uint4*>(wp), (int)Cout, (int)Cin, br.ns, br.kc);
+        const bool ok = pe == cudaSuccess &&
                         (br.w = static_cast<const uint4*>(wp),
                          launch(k_conv3d_brick, dim3((unsigned)tiles, (unsigned)(Cout / br.ns)), dim3(CONV_THREADS),
                                 smem, st, br) == cudaSuccess);
         dev_free(wp, st);
         return ok ? NGF_OK : NGF_ECUDA;
     }
+}
+
+}  // namespace
+}  // namespace ngf
+
+extern "C" ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* bias, float* y, int32_t B,
+                                     int32_t D, int32_t H, int32_t W, int32_t Cin, int32_t Cout, int32_t relu,
+                                     void* cuda_stream) {
+    return conv_run(x, w, false, bias, y, false, B, D, H, W, Cin, Cout, relu, cuda_stream);
+}
+
+extern "C" ngf_status ngf_conv3d_fwd_ex(const void* x, const void* w, const float* bias, void* y, int32_t B,
+                                        int32_t D, int32_t H, int32_t W, int32_t Cin, int32_t Cout, int32_t flags,
+                                        void* cuda_stream) {
+    if (flags & ~(NGF_CONV_RELU | NGF_CONV_OUT_BF16)) return NGF_EINVAL;
+    return conv_run(x, w, false, bias, y, (flags & NGF_CONV_OUT_BF16) != 0, B, D, H, W, Cin, Cout,
+                    (flags & NGF_CONV_RELU) != 0, cuda_stream);
+}
+
+extern "C" ngf_status ngf_conv3d_dgrad(const void* dy, const void* w, void* dx, int32_t B, int32_t D, int32_t H,
+                                       int32_t W, int32_t Cin, int32_t Cout, int32_t flags, void* cuda_stream) {
+    if (flags & ~NGF_CONV_OUT_BF16) return NGF_EINVAL;
+    // the mirrored convolution reads Cout channels and writes Cin
+    return conv_run(dy, w, true, nullptr, dx, (flags & NGF_CONV_OUT_BF16) != 0, B, D, H, W, Cout, Cin, 0,
+                    cuda_stream);
+}
+
+extern "C" ngf_status ngf_conv3d_wgrad(const void* dy, const void* x, float* dw, float* db, int32_t B, int32_t D,
+                                       int32_t H, int32_t W, int32_t Cin, int32_t Cout, void* cuda_stream) {
+    if (B < 0 || D < 0 || H < 0 || W < 0) return NGF_EINVAL;
+    if (Cin < 16 || Cin % 16 != 0 || (Cin > CONV_KMAX && Cin % CONV_KMAX != 0)) return NGF_EINVAL;
+    if (Cout < 16 || Cout > 128 || Cout % 16 != 0) return NGF_EINVAL;
+    const long long V = (long long)B * D * H * W;
+    if (V >= (1LL << 31)) return NGF_EBOUNDS;
+    if (!dy || !x || !dw) return NGF_EINVAL;
+    if (((uintptr_t)dy | (uintptr_t)x | (uintptr_t)dw) & 15u) return NGF_EINVAL;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    if (V == 0) {
+        if (cudaMemsetAsync(dw, 0, 27 * (size_t)Cout * Cin * sizeof(float), st) != cudaSuccess) return NGF_ECUDA;
+        if (db && cudaMemsetAsync(db, 0, (size_t)Cout * sizeof(float), st) != cudaSuccess) return NGF_ECUDA;
+        return NGF_OK;
+    }
+    int dev = 0, sm_count = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return NGF_ECUDA;
+    WgradArgs a;
+    a.x = static_cast<const uint4*>(x);
+    a.dy = static_cast<const uint4*>(dy);
+    a.B = B; a.D = D; a.H = H; a.W = W; a.cin = Cin; a.cout = Cout;
+    a.kc = Cin <= CONV_KMAX ? Cin : CONV_KMAX;
+    const int nch = Cin / a.kc;
+    a.tcols = 256;  // two CTAs per SM
+    a.tg = a.tcols / a.kc;
+    if (a.tg > 27) a.tg = 27;
+    a.ntg = (27 + a.tg - 1) / a.tg;
+    a.ngroups = nch * a.ntg;
+    a.gcols = a.tg * a.kc;
+    // the largest tile whose operands fit about 100 KB of shared memory
+    const int cand[][2] = {{8, 4}, {8, 2}, {4, 4}, {4, 2}, {2, 2}, {2, 1}, {1, 1}};
+    size_t smem = 0;
+    for (const auto& c : cand) {
+        const int TY = c[0], TZ = c[1];
+        const int lines = TY * TZ, cgo = Cout / 8, cgi = a.kc / 8;
+        // dy tile, plus the rows of the 128-row A operand beyond cout (they
+        // alias the next voxel groups, up to 16 channel groups past the last
+        // line's start)
+        const size_t ab = (size_t)2 * lines * cgo * 128 + (size_t)16 * cgo * 128 + 256;
+        const size_t nbv = (size_t)(WG_TX + 2) * (TY + 2) * (TZ + 2);
+        const size_t bb = (size_t)(cgi + 1) * nbv * 16;
+        smem = ab + bb + 64;
+        a.TY = TY; a.TZ = TZ; a.a_bytes = (uint32_t)ab;
+        if (smem <= 100 * 1024) break;
+    }
+    // at most two resident CTAs per SM, so that both tensor-memory
+    // allocations (256 columns each) always fit at once
+    int smem_sm = 0;
+    if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+        return NGF_ECUDA;
+    const size_t smem_min = (size_t)smem_sm / 3 - 1024 + 16;
+    if (smem < smem_min) smem = smem_min;
+    if (smem > 200 * 1024) return NGF_EBOUNDS;
+    a.tiles_x = (W + WG_TX - 1) / WG_TX;
+    a.tiles_y = (H + a.TY - 1) / a.TY;
+    a.tiles_z = (D + a.TZ - 1) / a.TZ;
+    const long long ntiles = (long long)a.tiles_x * a.tiles_y * a.tiles_z * B;
+    if (ntiles >= (1LL << 31)) return NGF_EBOUNDS;
+    a.ntiles = (int)ntiles;
+    long long split = (2LL * sm_count + a.ngroups - 1) / a.ngroups;
+    if (split > ntiles) split = ntiles;
+    if (split < 1) split = 1;
+    a.split = (int)split;
+    if (!wgrad_attr_set()) return NGF_ECUDA;
+    void* part = nullptr;
+    const size_t part_bytes = (size_t)a.split * a.ngroups * Cout * a.gcols * sizeof(float);
+    if (dev_alloc(&part, part_bytes, st) != cudaSuccess) return NGF_ENOMEM;
+    a.part = static_cast<float*>(part);
+    const long long total = 27LL * Cout * Cin;
+    bool ok = launch(k_conv3d_wgrad, dim3((unsigned)a.split, (unsigned)a.ngroups), dim3(CONV_THREADS), smem, st,
+                     a) == cudaSuccess &&
+              launch(k_conv3d_wgrad_reduce, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, st,
+                     (const float*)a.part, dw, (int)Cout, (int)Cin, a.kc, a.tg, a.ntg, a.ngroups, a.gcols,
+                     a.split) == cudaSuccess;
+    dev_free(part, st);
+    if (ok && db) {
+        const int per_block = 2048;
+        const long long nb = (V + per_block - 1) / per_block;
+        void* bp = nullptr;
+        if (dev_alloc(&bp, (size_t)nb * Cout * sizeof(float), st) != cudaSuccess) return NGF_ENOMEM;
+        ok = launch(k_bias_grad_part, dim3((unsigned)nb), dim3(128), 0, st, static_cast<const __nv_bfloat16*>(dy),
+                    static_cast<float*>(bp), V, (int)Cout, per_block) == cudaSuccess &&
+             launch(k_bias_grad_sum, dim3(1), dim3(256), 0, st, (const float*)bp, db, (int)nb, (int)Cout) ==
+                 cudaSuccess;
+        dev_free(bp, st);
+    }
+    return ok ? NGF_OK : NGF_ECUDA;
 }
 
 extern "C" int32_t ngf_conv3d_check(void* cuda_stream) {

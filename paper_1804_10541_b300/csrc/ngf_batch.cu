@@ -908,6 +908,8 @@ extern "C" ngf_status register_batch(int32_t npairs, const ngf_level_desc* fines
     if (o->gn_iters < 0 || o->pcg_iters < 0 || o->ls_max < 1)
         return set_error(nullptr, NGF_EINVAL, "gn_iters, pcg_iters >= 0 and ls_max >= 1 required");
     if (o->u_init) return set_error(nullptr, NGF_EINVAL, "u_init is not supported by the batched registration");
+    if (o->gn_iters_finest != 0 || o->j_target != 0.0)
+        return set_error(nullptr, NGF_EINVAL, "gn_iters_finest and j_target are not supported by the batched registration");
     if (o->method != NGF_METHOD_GN)
         return set_error(nullptr, NGF_EINVAL, "the batched registration runs Gauss-Newton only");
     if (o->zc < 0) return set_error(nullptr, NGF_EINVAL, "zc must be >= 0");

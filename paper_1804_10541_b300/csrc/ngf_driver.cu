@@ -203,6 +203,8 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
     if (o->gn_iters < 0 || o->pcg_iters < 0 || o->ls_max < 1)
         return set_error(nullptr, NGF_EINVAL, "gn_iters, pcg_iters >= 0 and ls_max >= 1 required");
     if (o->zc < 0) return set_error(nullptr, NGF_EINVAL, "zc must be >= 0");
+    if (o->gn_iters_finest < 0 || !(o->j_target >= 0.0))
+        return set_error(nullptr, NGF_EINVAL, "gn_iters_finest and j_target must be >= 0");
     if (o->method != NGF_METHOD_GN && o->method != NGF_METHOD_LBFGS)
         return set_error(nullptr, NGF_EINVAL, "method must be NGF_METHOD_GN or NGF_METHOD_LBFGS");
     const bool lbfgs = o->method == NGF_METHOD_LBFGS;
@@ -366,7 +368,8 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
             DRV_TRY(lbfgs_level(p, d, o, Rl[l], Tl[l], u, ut, g, bdiag.as<float>(), bgp.as<float>(), bsl.as<float>(),
                                 byt.as<float>(), bS.as<float>(), bY.as<float>(), blb.as<double>(), dsc, r));
         }
-        for (int k = 0; k < (lbfgs ? 0 : o->gn_iters); ++k) {
+        const int iters = (l == 0 && o->gn_iters_finest > 0) ? o->gn_iters_finest : o->gn_iters;
+        for (int k = 0; k < (lbfgs ? 0 : iters); ++k) {
             DRV_TRY(gradient_impl(p, Rl[l], Tl[l], u, g, dsc, dsc + 1));
             DRV_TRY(dot_impl(p, n, g, g, dsc + 2));
             double h[3];
@@ -374,6 +377,7 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
             DRV_CU(cudaStreamSynchronize(stream), "sync");
             const double J0 = h[0] + d.alpha * h[1], gg = h[2];
             if (gg == 0.0) break;  // stationary point
+            if (l == 0 && o->j_target > 0.0 && J0 <= o->j_target) break;  // target objective reached
             DRV_TRY(diagonal_impl(p, Rl[l], Tl[l], u, bdiag.as<float>()));
             DRV_CU(launch(k_scale, dim3(p->node_blocks), dim3(NT), 0, stream, n, -1.0f, (const float*)g, st.r),
                    "k_scale");

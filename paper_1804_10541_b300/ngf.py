@@ -25,7 +25,10 @@ EXPORTS = ["ngf_plan_create", "ngf_plan_destroy", "ngf_plan_set_stream", "ngf_la
            "ngf_objective_noalloc", "ngf_profile_enable", "ngf_profile_read", "ngf_launch_count",
            "ngf_batch_create", "ngf_batch_destroy", "ngf_batch_objective", "ngf_batch_gradient",
            "ngf_batch_hessvec", "ngf_batch_diagonal", "ngf_batch_autotune", "ngf_batch_zc", "register_batch",
-           "ngf_h0_solve", "ngf_plan_create_ex", "ngf_conv3d_fwd", "ngf_conv3d_check"]
+           "ngf_h0_solve", "ngf_plan_create_ex", "ngf_conv3d_fwd", "ngf_conv3d_check", "ngf_conv3d_fwd_ex",
+           "ngf_conv3d_dgrad", "ngf_conv3d_wgrad", "ngf_net_param_count", "ngf_net_create", "ngf_net_destroy",
+           "ngf_net_set_params", "ngf_net_get_params", "ngf_net_forward", "ngf_net_grad", "ngf_net_train_step",
+           "ngf_net_train"]
 NGF_METHOD_GN, NGF_METHOD_LBFGS = 0, 1
 
 
@@ -50,13 +53,19 @@ class Options(C.Structure):
     _fields_ = [("levels", C.c_int32), ("gn_iters", C.c_int32), ("pcg_iters", C.c_int32), ("ls_max", C.c_int32),
                 ("armijo_c1", C.c_double), ("pcg_rtol", C.c_double), ("start_level", C.c_int32),
                 ("u_init", C.c_void_p), ("use_graph", C.c_int32), ("method", C.c_int32),
-                ("lbfgs_memory", C.c_int32), ("lbfgs_gamma", C.c_double), ("zc", C.c_int32)]
+                ("lbfgs_memory", C.c_int32), ("lbfgs_gamma", C.c_double), ("zc", C.c_int32),
+                ("gn_iters_finest", C.c_int32), ("j_target", C.c_double)]
 
 
 class Report(C.Structure):
     _fields_ = [("J", C.c_double), ("D", C.c_double), ("S", C.c_double), ("gn_done", C.c_int32),
                 ("pcg_total", C.c_int32), ("ls_trials", C.c_int32), ("ls_fail", C.c_int32),
                 ("status", C.c_int32), ("seconds", C.c_double), ("hessvec_voxels", C.c_int64)]
+
+
+class NetDesc(C.Structure):
+    _fields_ = [("s", C.c_int32), ("max_batch", C.c_int32), ("in_shift", C.c_float), ("in_scale", C.c_float),
+                ("out_scale", C.c_float)]
 
 
 class NGFError(RuntimeError):
@@ -99,6 +108,17 @@ def declare(lib):
         "ngf_plan_create_ex": [C.POINTER(C.c_void_p), C.POINTER(LevelDesc), I32, VP],
         "ngf_conv3d_fwd": [VP, VP, VP, VP, I32, I32, I32, I32, I32, I32, I32, VP],
         "ngf_conv3d_check": [VP],
+        "ngf_conv3d_fwd_ex": [VP, VP, VP, VP, I32, I32, I32, I32, I32, I32, I32, VP],
+        "ngf_conv3d_dgrad": [VP, VP, VP, I32, I32, I32, I32, I32, I32, I32, VP],
+        "ngf_conv3d_wgrad": [VP, VP, VP, VP, I32, I32, I32, I32, I32, I32, VP],
+        "ngf_net_create": [C.POINTER(C.c_void_p), C.POINTER(NetDesc), VP],
+        "ngf_net_destroy": [P],
+        "ngf_net_set_params": [P, VP],
+        "ngf_net_get_params": [P, VP],
+        "ngf_net_forward": [P, VP, VP, I32, VP],
+        "ngf_net_grad": [P, VP, VP, VP, I32, VP, D],
+        "ngf_net_train_step": [P, VP, VP, VP, I32, C.c_double, D],
+        "ngf_net_train": [P, VP, VP, VP, I32, C.POINTER(I32), I32, I32, C.c_double, D],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -108,6 +128,8 @@ def declare(lib):
     lib.ngf_last_error.restype = C.c_char_p
     lib.ngf_launch_count.argtypes = []
     lib.ngf_launch_count.restype = C.c_int64
+    lib.ngf_net_param_count.argtypes = [C.POINTER(NetDesc)]
+    lib.ngf_net_param_count.restype = C.c_int64
     lib.ngf_batch_zc.argtypes = [P]
     lib.ngf_batch_zc.restype = C.c_int32
     return lib
@@ -181,6 +203,36 @@ def ngf_conv3d_fwd(x, w, bias, y, relu=False, stream=None):
     Cout = w.shape[0]
     _check(lib.ngf_conv3d_fwd(_ptr(x), _ptr(w), _ptr(bias) if bias is not None else None, _ptr(y),
                               B, D, H, W, Cin, Cout, 1 if relu else 0, _stream(stream)))
+
+
+NGF_CONV_RELU, NGF_CONV_OUT_BF16 = 1, 2
+
+
+def ngf_conv3d_fwd_ex(x, w, bias, y, flags=0, stream=None):
+    """3x3x3 convolution with flags (NGF_CONV_RELU, NGF_CONV_OUT_BF16): y is
+    float, or bf16 with NGF_CONV_OUT_BF16."""
+    B, D, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    _check(lib.ngf_conv3d_fwd_ex(_ptr(x), _ptr(w), _ptr(bias) if bias is not None else None, _ptr(y),
+                                 B, D, H, W, Cin, Cout, int(flags), _stream(stream)))
+
+
+def ngf_conv3d_dgrad(dy, w, dx, flags=0, stream=None):
+    """Data gradient of a layer with weights w [Cout][3][3][3][Cin]: dy
+    [B][D][H][W][Cout] bf16 -> dx [B][D][H][W][Cin] float (bf16 with
+    NGF_CONV_OUT_BF16)."""
+    B, D, H, W, Cout = dy.shape
+    Cin = w.shape[4]
+    _check(lib.ngf_conv3d_dgrad(_ptr(dy), _ptr(w), _ptr(dx), B, D, H, W, Cin, Cout, int(flags), _stream(stream)))
+
+
+def ngf_conv3d_wgrad(dy, x, dw, db=None, stream=None):
+    """Weight (and bias) gradient: dy [..][Cout] bf16, x [..][Cin] bf16 ->
+    dw [Cout][3][3][3][Cin] float, db [Cout] float (optional)."""
+    B, D, H, W, Cin = x.shape
+    Cout = dy.shape[4]
+    _check(lib.ngf_conv3d_wgrad(_ptr(dy), _ptr(x), _ptr(dw), _ptr(db) if db is not None else None,
+                                B, D, H, W, Cin, Cout, _stream(stream)))
 
 
 def ngf_conv3d_check(stream=None):
@@ -272,7 +324,8 @@ def pcg_read(plan, st):
 
 
 def options(levels, gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rtol=0.0, u_init=None,
-            start_level=0, use_graph=True, method=NGF_METHOD_GN, lbfgs_memory=5, lbfgs_gamma=0.0, zc=0):
+            start_level=0, use_graph=True, method=NGF_METHOD_GN, lbfgs_memory=5, lbfgs_gamma=0.0, zc=0,
+            gn_iters_finest=0, j_target=0.0):
     o = Options()
     o.levels, o.gn_iters, o.pcg_iters, o.ls_max = levels, gn_iters, pcg_iters, ls_max
     o.armijo_c1, o.pcg_rtol, o.start_level = armijo_c1, pcg_rtol, start_level
@@ -280,6 +333,7 @@ def options(levels, gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rt
     o.use_graph = 1 if use_graph else 0
     o.method, o.lbfgs_memory, o.lbfgs_gamma = int(method), int(lbfgs_memory), float(lbfgs_gamma)
     o.zc = int(zc)
+    o.gn_iters_finest, o.j_target = int(gn_iters_finest), float(j_target)
     return o
 
 
@@ -405,6 +459,95 @@ class Plan:
     def close(self):
         if self.handle:
             ngf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+# ---- learned initializer (encoder-decoder network) ---------------------------
+
+def net_desc(s, max_batch, in_shift, in_scale, out_scale):
+    d = NetDesc()
+    d.s, d.max_batch = int(s), int(max_batch)
+    d.in_shift, d.in_scale, d.out_scale = float(in_shift), float(in_scale), float(out_scale)
+    return d
+
+
+def ngf_net_param_count(desc):
+    n = int(lib.ngf_net_param_count(C.byref(desc)))
+    if n < 0:
+        raise NGFError(-1, "bad network descriptor")
+    return n
+
+
+def ngf_net_create(desc, stream=None):
+    h = C.c_void_p()
+    _check(lib.ngf_net_create(C.byref(h), C.byref(desc), _stream(stream)))
+    return h
+
+
+def ngf_net_destroy(net):
+    _check(lib.ngf_net_destroy(net))
+
+
+def ngf_net_set_params(net, params):
+    _check(lib.ngf_net_set_params(net, _ptr(params)))
+
+
+def ngf_net_get_params(net, params):
+    _check(lib.ngf_net_get_params(net, _ptr(params)))
+
+
+def ngf_net_forward(net, R, T, B, u):
+    _check(lib.ngf_net_forward(net, _ptr(R), _ptr(T), int(B), _ptr(u)))
+
+
+def ngf_net_grad(net, R, T, u_target, B, grads=None):
+    loss = C.c_double()
+    _check(lib.ngf_net_grad(net, _ptr(R), _ptr(T), _ptr(u_target), int(B), _ptr(grads), C.byref(loss)))
+    return loss.value
+
+
+def ngf_net_train_step(net, R, T, u_target, B, lr, want_loss=True):
+    loss = C.c_double()
+    _check(lib.ngf_net_train_step(net, _ptr(R), _ptr(T), _ptr(u_target), int(B), float(lr),
+                                  C.byref(loss) if want_loss else None))
+    return loss.value if want_loss else None
+
+
+def ngf_net_train(net, R, T, u_target, npairs, order, batch, lr):
+    """Adam steps over the pairs in `order` (batches of `batch`); returns the
+    per-batch losses."""
+    order = [int(k) for k in order]
+    arr = (C.c_int32 * max(1, len(order)))(*order)
+    nb = (len(order) + batch - 1) // batch
+    losses = (C.c_double * max(1, nb))()
+    _check(lib.ngf_net_train(net, _ptr(R), _ptr(T), _ptr(u_target), int(npairs), arr, len(order), int(batch),
+                             float(lr), losses))
+    return list(losses)[:nb]
+
+
+class Net:
+    """Owning wrapper of an ngf_net."""
+
+    def __init__(self, desc, stream=None):
+        self.desc = desc
+        self.handle = ngf_net_create(desc, stream)
+        self.nparams = ngf_net_param_count(desc)
+
+    def close(self):
+        if self.handle:
+            ngf_net_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -233,6 +233,102 @@ def lung_pair(m=(256, 256, 120), h=(1.0, 1.0, 2.5), seed=10, device="cpu", noise
     return R, T, U
 
 
+def _lung_field(m, h, seed, max_dz):
+    """Breathing displacement of lung_pair: (ux, uy, uz)(X, Y, Z) in mm."""
+    ext = np.asarray(m, float) * np.asarray(h, float)
+    r = _rng(seed + 2)
+    sx, sy = r.uniform(50, 80), r.uniform(45, 70)
+    ax_, ay_ = r.uniform(1.0, 3.0, 2)
+    ph_x, ph_y = r.uniform(0, 2 * math.pi, 2)
+    cx, cy = ext[0] / 2, ext[1] / 2
+
+    def field(X, Y, Z):
+        lat = torch.exp(-((X - cx) ** 2) / (2 * sx * sx) - ((Y - cy) ** 2) / (2 * sy * sy))
+        uz = max_dz * lat * torch.sin(math.pi * Z / ext[2])
+        ux = ax_ * torch.sin(2 * math.pi * Y / ext[1] + ph_x) * torch.sin(math.pi * X / ext[0]) * torch.sin(math.pi * Z / ext[2])
+        uy = ay_ * torch.sin(2 * math.pi * X / ext[0] + ph_y) * torch.sin(math.pi * Y / ext[1]) * torch.sin(math.pi * Z / ext[2])
+        return ux, uy, uz
+
+    return field
+
+
+def lung_pair_windowed(m, h, seed, device="cpu", noise=10.0, max_dz=15.0, chunk=256):
+    """The lung_pair phantom and displacement, evaluated faster for many
+    pairs: each vessel segment is evaluated only on the voxels of a box
+    around it (R) or around its pre-image under the displacement (T: the
+    box moved by -u* at the segment's centre and widened by the change of
+    u* across it), and the vessel term takes the maximum over segments by
+    a scatter.  Beyond the box a segment's smooth indicator is below 1e-3,
+    so the noise-free pair differs from lung_pair's by a few hundredths of a
+    HU; the noise comes from a generator on `device`.
+    Returns R, T (float32, m_x m_y m_z) on `device`."""
+    dtype = torch.float32
+    ph = _Lung(m, h, seed)
+    field = _lung_field(m, h, seed, max_dz)
+    hh = torch.tensor(h, dtype=dtype, device=device)
+    mm = torch.tensor(m, device=device)
+    X, Y, Z = _axes(m, h, 0, m[2], device, dtype)
+    shp = (m[2], m[1], m[0])
+    Xb, Yb, Zb = X.expand(shp), Y.expand(shp), Z.expand(shp)
+    ux, uy, uz = (c.expand(shp) for c in field(X, Y, Z))
+    w = 0.75
+
+    def base(Xq, Yq, Zq):
+        v = -1000.0 + 1040.0 * _step(_ellipsoid_depth(Xq, Yq, Zq, *ph.body), w)
+        lung = 0.0
+        for c, a in ph.lungs:
+            lung = lung + _step(_ellipsoid_depth(Xq, Yq, Zq, c, a), w)
+        return v - 890.0 * lung, lung
+
+    P0 = torch.tensor(np.stack([sg[0] for sg in ph.segs]), dtype=dtype, device=device)
+    P1 = torch.tensor(np.stack([sg[1] for sg in ph.segs]), dtype=dtype, device=device)
+    rad = torch.tensor([sg[2] for sg in ph.segs], dtype=dtype, device=device)
+    lo_mm = torch.minimum(P0, P1) - rad[:, None] - 2.0
+    hi_mm = torch.maximum(P0, P1) + rad[:, None] + 2.0
+    ctr = 0.5 * (P0 + P1)
+    cu = torch.stack(field(ctr[:, 0], ctr[:, 1], ctr[:, 2]), dim=1)
+    # u* changes by at most |grad u*| * half the box across it: widen the T box by that
+    span = 0.5 * (hi_mm - lo_mm).max(dim=1).values
+    gmax = max_dz * (1.0 / 50.0 + math.pi / (m[2] * h[2])) + 6.0 * math.pi / min(m[0] * h[0], m[1] * h[1])
+    marg = (gmax * span)[:, None] + 1.0
+
+    def vessels(lo, hi, warped):
+        i0 = torch.floor(lo / hh - 0.5).to(torch.int64)
+        i1 = torch.ceil(hi / hh - 0.5).to(torch.int64)
+        size = (i1 - i0 + 1).max(dim=0).values.tolist()
+        ar = [torch.arange(size[a], device=device) for a in range(3)]
+        off = torch.stack(torch.meshgrid(ar[2], ar[1], ar[0], indexing="ij"), dim=-1).reshape(-1, 3).flip(-1)
+        ves = torch.zeros(m[0] * m[1] * m[2], dtype=dtype, device=device)
+        for c0 in range(0, len(rad), chunk):
+            sl = slice(c0, c0 + chunk)
+            idx = i0[sl, None, :] + off[None]                        # [S, V, 3] voxel (x, y, z)
+            ok = ((idx >= 0) & (idx < mm)).all(-1)
+            idx = torch.minimum(torch.maximum(idx, torch.zeros_like(mm)), mm - 1)
+            flat = (idx[..., 2] * m[1] + idx[..., 1]) * m[0] + idx[..., 0]
+            q = (idx.to(dtype) + 0.5) * hh
+            if warped:
+                q = q + torch.stack([ux.reshape(-1)[flat], uy.reshape(-1)[flat], uz.reshape(-1)[flat]], dim=-1)
+            d = (P1 - P0)[sl, None, :]
+            t = (((q - P0[sl, None, :]) * d).sum(-1) / (d * d).sum(-1)).clamp(0.0, 1.0)
+            dist = torch.linalg.vector_norm(q - P0[sl, None, :] - t[..., None] * d, dim=-1)
+            val = torch.where(ok, _step(rad[sl, None] - dist, 0.3), torch.zeros_like(dist))
+            ves.scatter_reduce_(0, flat.reshape(-1), val.reshape(-1), reduce="amax")
+        return ves.reshape(shp)
+
+    vR, lR = base(Xb, Yb, Zb)
+    R = (vR + 890.0 * vessels(lo_mm, hi_mm, False) * lR).clamp(-1000.0, 400.0).reshape(-1)
+    vT, lT = base(Xb + ux, Yb + uy, Zb + uz)
+    T = (vT + 890.0 * vessels(lo_mm - cu - marg, hi_mm - cu + marg, True) * lT).clamp(-1000.0, 400.0).reshape(-1)
+    M = m[0] * m[1] * m[2]
+    # noise drawn by a generator on the device itself (seeded, so each pair
+    # is reproducible on a given device type)
+    gR = torch.Generator(device=device).manual_seed(seed + 1)
+    gT = torch.Generator(device=device).manual_seed(seed + 3)
+    R = R + noise * torch.randn(M, generator=gR, dtype=dtype, device=device)
+    T = T + noise * torch.randn(M, generator=gT, dtype=dtype, device=device)
+    return R, T
+
+
 # ------------------------------------------------------------------ thorax-abdomen
 
 

@@ -38,8 +38,9 @@ def test_struct_layouts_match_header(ngf, tmp_path):
     the header's structs."""
     import subprocess
     structs = {"ngf_level_desc": ngf.LevelDesc, "ngf_pcg_state": ngf.PcgState, "ngf_options": ngf.Options,
-               "ngf_report": ngf.Report, "ngf_pcg_info": ngf.PcgInfo}
-    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ngf.h"', "int main(void) {"]
+               "ngf_report": ngf.Report, "ngf_pcg_info": ngf.PcgInfo, "ngf_net_desc": ngf.NetDesc}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ngf.h"', '#include "ngf_cnn.h"',
+             "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
         for fname, _ in py._fields_:
@@ -127,3 +128,17 @@ def test_tile_depth_and_convolution_validation(ngf):
     assert conv(buf, buf, None, buf, 1, -1, 2, 2, 16, 16, 0, None) == -1
     assert conv(buf, buf, None, buf, 1, 2048, 2048, 1024, 16, 16, 0, None) == -8
     assert conv(None, None, None, None, 1, 0, 4, 4, 16, 16, 0, None) == 0  # empty volume
+
+
+def test_net_parameter_count_and_validation(ngf):
+    """The network's parameter count is the sum over its seven layers of
+    27 Cin Cout weights and Cout biases; bad descriptors are refused before
+    any CUDA call."""
+    d = ngf.net_desc(32, 2, -500.0, 1.0 / 500.0, 5.0)
+    layers = [(16, 16), (16, 32), (32, 64), (64, 128), (128, 64), (64, 64), (64, 16)]
+    assert ngf.ngf_net_param_count(d) == sum(27 * ci * co + co for ci, co in layers)
+    for bad in (ngf.net_desc(12, 1, 0.0, 1.0, 1.0), ngf.net_desc(16, 0, 0.0, 1.0, 1.0),
+                ngf.net_desc(16, 1, 0.0, 1.0, 0.0), ngf.net_desc(16, 1, 0.0, 0.0, 1.0)):
+        assert ngf.lib.ngf_net_param_count(C.byref(bad)) == -1
+        h = C.c_void_p()
+        assert ngf.lib.ngf_net_create(C.byref(h), C.byref(bad), None) == -1 and not h.value
