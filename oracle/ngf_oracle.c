@@ -19,10 +19,20 @@
 
 static long nvox(const orc_level* L) { return (long)L->m[0] * L->m[1] * L->m[2]; }
 static long nnod(const orc_level* L) { return (long)L->n[0] * L->n[1] * L->n[2]; }
-static double hbar(const orc_level* L) { return L->h[0] * L->h[1] * L->h[2]; }
-/* node spacing: the nodal grid spans the image domain [0, m h] (Sec. 2.2) */
-static double hy(const orc_level* L, int l) { return (double)L->m[l] * L->h[l] / (double)(L->n[l] - 1); }
-static double hbary(const orc_level* L) { return hy(L, 0) * hy(L, 1) * hy(L, 2); }
+/* The 2-D method (one image plane, one node plane): the paper states every
+ * operator for d = 2 and d = 3 alike (Sec. 2.2); in 2-D the cell volumes are
+ * h_x h_y and hy_x hy_y, the template is interpolated bilinearly in the
+ * plane, and there are no z differences (the clamped ones below vanish). */
+static int planar(const orc_level* L) { return L->m[2] == 1 && L->n[2] == 1; }
+static double hbar(const orc_level* L) { return planar(L) ? L->h[0] * L->h[1] : L->h[0] * L->h[1] * L->h[2]; }
+/* node spacing: the nodal grid spans the image domain [0, m h] (Sec. 2.2);
+ * the single node plane of the 2-D method has no spacing (1 is a placeholder) */
+static double hy(const orc_level* L, int l) {
+    return L->n[l] > 1 ? (double)L->m[l] * L->h[l] / (double)(L->n[l] - 1) : 1.0;
+}
+static double hbary(const orc_level* L) { return hy(L, 0) * hy(L, 1) * (planar(L) ? 1.0 : hy(L, 2)); }
+/* node planes touched by one image plane: 1 in 2-D, 2 (trilinear) in 3-D */
+static int zspan(const orc_level* L) { return planar(L) ? 1 : 2; }
 
 static long clampl(long v, long lo, long hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
@@ -70,7 +80,7 @@ void orc_P(const orc_level* L, const double* u, double* uh) {
                 long i = x + (long)m0 * (y + (long)m1 * z);
                 for (int d = 0; d < 3; ++d) {
                     double acc = 0.0;
-                    for (int c = 0; c < 2; ++c)
+                    for (int c = 0; c < zspan(L); ++c)
                         for (int b = 0; b < 2; ++b)
                             for (int a = 0; a < 2; ++a) {
                                 double w = (a ? wx : 1.0 - wx) * (b ? wy : 1.0 - wy) * (c ? wz : 1.0 - wz);
@@ -97,7 +107,7 @@ void orc_PT(const orc_level* L, const double* uh, double* out) {
                 pw(y, m1, L->n[1], &fy, &wy);
                 pw(z, m2, L->n[2], &fz, &wz);
                 long i = x + (long)m0 * (y + (long)m1 * z);
-                for (int c = 0; c < 2; ++c)
+                for (int c = 0; c < zspan(L); ++c)
                     for (int b = 0; b < 2; ++b)
                         for (int a = 0; a < 2; ++a) {
                             double w = (a ? wx : 1.0 - wx) * (b ? wy : 1.0 - wy) * (c ? wz : 1.0 - wz);
@@ -131,7 +141,8 @@ void orc_warp(const orc_level* L, const double* T, const double* uh, double* Tw,
                 /* continuous voxel coordinate xi = index + (P u)/h (displacement
                  * form); the cell is floor(xi), so knots take the forward cell */
                 for (int l = 0; l < 3; ++l) {
-                    double d = uh[l * M + i] / L->h[l];
+                    /* 2-D: the sample stays in the image plane */
+                    double d = (l == 2 && planar(L)) ? 0.0 : uh[l * M + i] / L->h[l];
                     if (!(fabs(d) < 1.0e9)) { inside = 0; c[l] = 0; t[l] = 0.0; continue; }
                     double fl = floor(d);
                     c[l] = coord[l] + (long)fl;
@@ -162,7 +173,7 @@ void orc_warp(const orc_level* L, const double* T, const double* uh, double* Tw,
                 Tw[i] = val;
                 dT[i] = gx / L->h[0];
                 dT[M + i] = gy / L->h[1];
-                dT[2 * M + i] = gz / L->h[2];
+                dT[2 * M + i] = planar(L) ? 0.0 : gz / L->h[2];  /* 2-D: bilinear, no z derivative */
             }
 }
 
@@ -477,7 +488,7 @@ void orc_gn_diagonal(const orc_level* L, const double* R, const double* T, const
                         pw((int)jx, m0, L->n[0], &fx, &wx);
                         pw((int)jy, m1, L->n[1], &fy, &wy);
                         pw((int)jz, m2, L->n[2], &fz, &wz);
-                        for (int cc = 0; cc < 2; ++cc)
+                        for (int cc = 0; cc < zspan(L); ++cc)
                             for (int b = 0; b < 2; ++b)
                                 for (int a = 0; a < 2; ++a) {
                                     double w = (a ? wx : 1.0 - wx) * (b ? wy : 1.0 - wy) * (cc ? wz : 1.0 - wz);
@@ -808,7 +819,7 @@ double orc_lbfgs_level(const orc_level* L, const double* R, const double* T, dou
 void orc_level_at(const orc_level* finest, int32_t level, orc_level* out) {
     *out = *finest;
     for (int k = 0; k < level; ++k) {
-        for (int l = 0; l < 3; ++l) {
+        for (int l = 0; l < (planar(finest) ? 2 : 3); ++l) {  /* 2-D levels stay planar */
             int m = out->m[l];
             int mc = (m + 1) / 2;
             int cells = out->n[l] - 1;
@@ -852,16 +863,17 @@ void orc_prolongate(const int32_t nc[3], const double* uc, const int32_t nf[3], 
                 for (int l = 0; l < 3; ++l) {
                     /* same physical position: fine node i sits at coarse
                      * coordinate i (nc-1)/(nf-1) */
-                    double c = (double)idx[l] * (double)(nc[l] - 1) / (double)(nf[l] - 1);
+                    double c = nf[l] > 1 ? (double)idx[l] * (double)(nc[l] - 1) / (double)(nf[l] - 1) : 0.0;
                     double fl = floor(c);
                     if (fl > nc[l] - 2) fl = nc[l] - 2;
+                    if (fl < 0) fl = 0; /* a single node plane (2-D) */
                     f[l] = (long)fl;
                     w[l] = c - fl;
                 }
                 long o = x + (long)nf[0] * (y + (long)nf[1] * z);
                 for (int d = 0; d < 3; ++d) {
                     double acc = 0.0;
-                    for (int c = 0; c < 2; ++c)
+                    for (int c = 0; c < (nc[2] > 1 ? 2 : 1); ++c)
                         for (int b = 0; b < 2; ++b)
                             for (int a = 0; a < 2; ++a) {
                                 double ww = (a ? w[0] : 1.0 - w[0]) * (b ? w[1] : 1.0 - w[1]) * (c ? w[2] : 1.0 - w[2]);

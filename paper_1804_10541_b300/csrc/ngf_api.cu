@@ -74,7 +74,10 @@ ngf_status validate_desc(const ngf_level_desc* d, std::string& why) {
     for (int a = 0; a < 3; ++a) {
         if (d->m[a] < 1) { why = "image cells m must be >= 1 on every axis"; return NGF_EINVAL; }
         if (!(d->h[a] > 0.0) || !std::isfinite(d->h[a])) { why = "spacing h must be finite and > 0"; return NGF_EINVAL; }
-        if (d->n[a] < 2) { why = "deformation nodes n must be >= 2 on every axis"; return NGF_EINVAL; }
+        if (d->n[a] < 2 && !(a == 2 && d->m[2] == 1 && d->n[2] == 1)) {
+            why = "deformation nodes n must be >= 2 on every axis (n[2] == 1 only with m[2] == 1: a 2-D level)";
+            return NGF_EINVAL;
+        }
         if (d->n[a] - 1 > d->m[a]) {
             why = "deformation grid finer than the image grid: need n_k - 1 <= m_k (Sec. 2.2)";
             return NGF_EINVAL;
@@ -149,7 +152,7 @@ static void axis_geometry(int m, int n, const std::vector<int>& f, int TL, int h
     lo.assign(n, INT_MAX);
     hi.assign(n, -1);
     for (int t = 0; t < ntiles; ++t)
-        for (int k = b0[t]; k <= b1[t]; ++k) {
+        for (int k = b0[t]; k <= std::min(b1[t], n - 1); ++k) {  // a planar level's box has a second, empty plane
             lo[k] = std::min(lo[k], t);
             hi[k] = std::max(hi[k], t);
         }
@@ -275,12 +278,12 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     for (int a = 0; a < 3; ++a) {
         p->m[a] = d->m[a];
         p->n[a] = d->n[a];
-        p->hy[a] = (double)d->m[a] * d->h[a] / (double)(d->n[a] - 1);
+        p->hy[a] = node_spacing(*d, a);
     }
     p->M = (long long)p->m[0] * p->m[1] * p->m[2];
     p->N = (long long)p->n[0] * p->n[1] * p->n[2];
-    p->hbar = d->h[0] * d->h[1] * d->h[2];
-    p->hbary = p->hy[0] * p->hy[1] * p->hy[2];
+    p->hbar = cell_volume(*d);
+    p->hbary = node_cell_volume(*d);
 
     // z-chunking: k chunks per column of tiles, chosen to minimise
     // (rounds of 2 CTAs per SM) x (planes marched per chunk, 5 of them fill

@@ -637,9 +637,11 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
                 std::vector<float> tw;
                 for (int a = 0; a < 3; ++a)
                     for (int i = 0; i < D[k].n[a]; ++i) {
-                        const double cc = (double)i * (double)(c.n[a] - 1) / (double)(D[k].n[a] - 1);
+                        const double cc =
+                            D[k].n[a] > 1 ? (double)i * (double)(c.n[a] - 1) / (double)(D[k].n[a] - 1) : 0.0;
                         double fl = std::floor(cc);
                         if (fl > c.n[a] - 2) fl = c.n[a] - 2;
+                    if (fl < 0) fl = 0;  // a single node plane (planar level): weight 0
                         tf.push_back((int)fl);
                         tw.push_back((float)(cc - fl));
                     }

@@ -17,8 +17,9 @@ namespace ngf {
 // deformation cells (ceil) and keeps the physical extent of the domain
 ngf_level_desc level_at(const ngf_level_desc& finest, int level) {
     ngf_level_desc d = finest;
+    const bool flat = planar(finest);  // a 2-D level stays planar on every level
     for (int k = 0; k < level; ++k)
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a < (flat ? 2 : 3); ++a) {
             const int m = d.m[a], mc = (m + 1) / 2;
             int cc = d.n[a] / 2;  // ceil((n - 1) / 2) deformation cells
             if (cc > mc) cc = mc;
@@ -332,9 +333,10 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
             std::vector<float> tw;
             for (int a = 0; a < 3; ++a)
                 for (int i = 0; i < d.n[a]; ++i) {
-                    const double cc = (double)i * (double)(c.n[a] - 1) / (double)(d.n[a] - 1);
+                    const double cc = d.n[a] > 1 ? (double)i * (double)(c.n[a] - 1) / (double)(d.n[a] - 1) : 0.0;
                     double fl = std::floor(cc);
                     if (fl > c.n[a] - 2) fl = c.n[a] - 2;
+                    if (fl < 0) fl = 0;  // a single node plane (planar level): weight 0
                     tf.push_back((int)fl);
                     tw.push_back((float)(cc - fl));
                 }

@@ -83,6 +83,10 @@ __device__ __forceinline__ void grid_sum_finish(double blocksum, double* part, u
 __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy, int gz, float d0, float d1,
                                              float d2, float& g0, float& g1, float& g2) {
     g0 = g1 = g2 = 0.f;
+    // a planar (2-D) level samples its one plane bilinearly: no z displacement,
+    // no zero-padded neighbour plane, no z derivative
+    const bool planar = P.m2 == 1 && P.n2 == 1;
+    if (planar) d2 = 0.f;
     if (!(fabsf(d0) < 1.0e9f) || !(fabsf(d1) < 1.0e9f) || !(fabsf(d2) < 1.0e9f)) return 0.f;
     const float f0 = floorf(d0), f1 = floorf(d1), f2 = floorf(d2);
     const int cx = gx + (int)f0, cy = gy + (int)f1, cz = gz + (int)f2;
@@ -129,7 +133,7 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
     const float q1 = fmaf(ty, (v111 - v011) - (v101 - v001), v101 - v001);
     g0 = fmaf(tz, q1 - q0, q0) * P.ih[0];
     g1 = fmaf(tz, (e11 - e01) - (e10 - e00), e10 - e00) * P.ih[1];
-    g2 = (a1 - a0) * P.ih[2];
+    g2 = planar ? 0.f : (a1 - a0) * P.ih[2];
     return fmaf(tz, a1 - a0, a0);
 }
 
@@ -268,7 +272,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
 #pragma unroll
             for (int c = 0; c < NVEC; ++c) {
                 const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
-                const float a = __ldg(src + o), b = __ldg(src + o + plane_n);
+                const float a = __ldg(src + o), b = P.n2 > 1 ? __ldg(src + o + plane_n) : a;
                 (&S.Uz[c][0][0])[s0_s[k]] = fmaf(wzz, b - a, a);
             }
         }
@@ -600,7 +604,7 @@ __device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, i
 #pragma unroll
             for (int c = 0; c < NVEC; ++c) {
                 const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
-                const float a = __ldg(src + o), b = __ldg(src + o + plane_n);
+                const float a = __ldg(src + o), b = P.n2 > 1 ? __ldg(src + o + plane_n) : a;
                 (&S.Uz[c][0][0])[s0_s[k]] = fmaf(wzz, b - a, a);
             }
         }
@@ -820,7 +824,7 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
                 const int by = rem / UXn, bx = rem - by * UXn;
                 const float* src = P.u + c * P.N;
                 const long long o = pl0 + (UX0 + bx) + (long long)P.n0 * (UY0 + by);
-                const float a = __ldg(src + o), b = __ldg(src + o + plane);
+                const float a = __ldg(src + o), b = P.n2 > 1 ? __ldg(src + o + plane) : a;
                 S.Uz[c][by][bx] = fmaf(wzz, b - a, a);
             }
         }
@@ -1363,9 +1367,14 @@ __global__ void __launch_bounds__(NT) k_prolong(int f0, int f1, int f2, int c0, 
         const long long sy = c0, sz = (long long)c0 * c1;
         const float e00 = fmaf(wx, u[o + 1] - u[o], u[o]);
         const float e10 = fmaf(wx, u[o + sy + 1] - u[o + sy], u[o + sy]);
+        const float a0 = fmaf(wy, e10 - e00, e00);
+        if (Nc == sz) {  // one coarse node plane (planar level)
+            uf[i] = a0;
+            continue;
+        }
         const float e01 = fmaf(wx, u[o + sz + 1] - u[o + sz], u[o + sz]);
         const float e11 = fmaf(wx, u[o + sz + sy + 1] - u[o + sz + sy], u[o + sz + sy]);
-        const float a0 = fmaf(wy, e10 - e00, e00), a1 = fmaf(wy, e11 - e01, e01);
+        const float a1 = fmaf(wy, e11 - e01, e01);
         uf[i] = fmaf(wz, a1 - a0, a0);
     }
 }

@@ -195,7 +195,7 @@ extern "C" ngf_status ngf_objective_noalloc(const ngf_level_desc* d, const float
     P.tr = (float)(d->tau * d->rho);
     P.tau2 = (float)(d->tau * d->tau);
     P.rho2 = (float)(d->rho * d->rho);
-    P.hbar = d->h[0] * d->h[1] * d->h[2];
+    P.hbar = cell_volume(*d);
     P.qscale = (float)(2.0 * P.hbar);
     P.R = R;
     P.T = T;
@@ -225,11 +225,11 @@ extern "C" ngf_status ngf_objective_noalloc(const ngf_level_desc* d, const float
     G.N = N;
     double hy[3];
     for (int a = 0; a < 3; ++a) {
-        hy[a] = (double)d->m[a] * d->h[a] / (double)(d->n[a] - 1);
+        hy[a] = node_spacing(*d, a);
         G.ihy2[a] = (float)(1.0 / (hy[a] * hy[a]));
     }
     e = launch(k_na_curv_energy, dim3(node_blocks), dim3(256), 0, stream, G, u, part, count + 1, dev_DS + 1,
-               hy[0] * hy[1] * hy[2]);
+               node_cell_volume(*d));
     if (e != cudaSuccess) return cuda_check(nullptr, e, "k_na_curv_energy");
     return NGF_OK;
 }

@@ -99,6 +99,26 @@ int grid_for(long long n, int max_blocks);
 ngf_status plan_create(ngf_plan** out, const ngf_level_desc* desc, cudaStream_t stream, int zc);
 ngf_level_desc level_at(const ngf_level_desc& finest, int level);
 
+// The 2-D method (a planar level): one image plane and one node plane
+// (m[2] == 1 and n[2] == 1).  Images are m0 x m1, u has the in-plane
+// components x and y (the z component of the 3N layout is carried along and
+// stays zero from a zero start), the template is interpolated bilinearly in
+// the plane, short differences and the curvature stencil act in x and y
+// only, and the cell volumes are hbar = h0 h1, hbar^y = hy0 hy1 (h[2] is not
+// used).
+inline bool planar(const ngf_level_desc& d) { return d.m[2] == 1 && d.n[2] == 1; }
+// node spacing per axis: the nodes span the image domain [0, m h]; the
+// single node plane of a planar level has unit spacing (it is never used)
+inline double node_spacing(const ngf_level_desc& d, int a) {
+    return d.n[a] > 1 ? (double)d.m[a] * d.h[a] / (double)(d.n[a] - 1) : 1.0;
+}
+inline double cell_volume(const ngf_level_desc& d) {
+    return planar(d) ? d.h[0] * d.h[1] : d.h[0] * d.h[1] * d.h[2];
+}
+inline double node_cell_volume(const ngf_level_desc& d) {
+    return node_spacing(d, 0) * node_spacing(d, 1) * (planar(d) ? 1.0 : node_spacing(d, 2));
+}
+
 }  // namespace ngf
 
 struct ngf_plan {

@@ -172,3 +172,99 @@ class Assembled:
         Jc = self.J_chain()
         H = 2.0 * self.hbar * Jc.T @ Jc
         return H + self.alpha * 2.0 * self.hbary * self.Lap.T @ self.Lap
+
+
+# ---------------------------------------------------------------------------
+# The 2-D method, assembled on its own: pixels m0 x m1, nodes n0 x n1, two
+# displacement components, bilinear hat functions, four short differences
+# per pixel and the 2-D Laplacian.  Vectors are 2N long (x components, then
+# y); the oracle's planar level carries a third (z) block that must vanish.
+
+def P_dense_2d(m, h, n):
+    xs = [(np.arange(m[a]) + 0.5) * h[a] for a in range(2)]
+    hy = [m[a] * h[a] / (n[a] - 1) for a in range(2)]
+    Xs = [np.arange(n[a]) * hy[a] for a in range(2)]
+    Pa = [hat((xs[a][:, None] - Xs[a][None, :]) / hy[a]) for a in range(2)]
+    return np.kron(Pa[1], Pa[0]), hy
+
+
+def interp_padded_2d(T, m, xi):
+    T2 = T.reshape(m[1], m[0])
+    out = np.zeros(xi.shape[0], dtype=np.result_type(xi, T))
+    for cy in range(m[1]):
+        wy = hat(xi[:, 1] - cy)
+        for cx in range(m[0]):
+            out = out + T2[cy, cx] * hat(xi[:, 0] - cx) * wy
+    return out
+
+
+def short_grad_2d(I, m, h):
+    I2 = I.reshape(m[1], m[0])
+    out = []
+    for sgn in (-1, 1):
+        for a, ax in ((0, 1), (1, 0)):
+            sl = np.arange(I2.shape[ax])
+            nb = np.clip(sl + sgn, 0, I2.shape[ax] - 1)
+            J = np.take(I2, nb, axis=ax)
+            d = (I2 - J) if sgn < 0 else (J - I2)
+            out.append((d / h[a]).reshape(-1))
+    return np.stack(out, axis=1)
+
+
+def residual_2d(R, Tw, m, h, tau, rho):
+    gT = short_grad_2d(Tw, m, h)
+    gR = short_grad_2d(R, m, h)
+    num = 0.5 * np.sum(gT * gR, axis=1) + tau * rho
+    return num / (np.sqrt(0.5 * np.sum(gT * gT, axis=1) + tau * tau) * np.sqrt(0.5 * np.sum(gR * gR, axis=1) + rho * rho))
+
+
+class Assembled2D:
+    """All factors of the 2-D method at one (R, T, u), u given as 2N."""
+
+    def __init__(self, m, h, n, alpha, tau, rho, R, T, u, eps=1e-6):
+        self.m, self.h, self.n = m, h, n
+        self.alpha = alpha
+        M, N = m[0] * m[1], n[0] * n[1]
+        self.M, self.N = M, N
+        self.hbar = h[0] * h[1]
+        Ps, hy = P_dense_2d(m, h, n)
+        self.hbary = hy[0] * hy[1]
+        Z = np.zeros_like(Ps)
+        self.P = np.block([[Ps, Z], [Z, Ps]])
+        u = np.asarray(u, float)
+        self.u = u
+        uh = np.stack([Ps @ u[:N], Ps @ u[N:]], axis=1)
+        idx = np.stack(np.meshgrid(np.arange(m[0]), np.arange(m[1]), indexing="ij"), -1)
+        idx = idx.transpose(1, 0, 2).reshape(-1, 2).astype(float)
+        xi = idx + uh / np.asarray(h[:2])[None, :]
+        T = np.asarray(T, float)
+        self.Tw = interp_padded_2d(T, m, xi)
+        dT = np.zeros((M, 2))
+        for a in range(2):
+            e = np.zeros(2)
+            e[a] = eps
+            dT[:, a] = (interp_padded_2d(T, m, xi + e) - interp_padded_2d(T, m, xi - e)) / (2 * eps * h[a])
+        self.dT = np.hstack([np.diag(dT[:, 0]), np.diag(dT[:, 1])])
+        R = np.asarray(R, float)
+        self.r = residual_2d(R, self.Tw, m, h, tau, rho)
+        J = np.zeros((M, M))
+        for j in range(M):
+            Tc = self.Tw.astype(complex)
+            Tc[j] += 1e-30j
+            J[:, j] = residual_2d(R.astype(complex), Tc, m, h, tau, rho).imag / 1e-30
+        self.dr = J
+        Lx, Ly = lap1d(n[0], hy[0]), lap1d(n[1], hy[1])
+        Ls = np.kron(np.eye(n[1]), Lx) + np.kron(Ly, np.eye(n[0]))
+        Zl = np.zeros_like(Ls)
+        self.Lap = np.block([[Ls, Zl], [Zl, Ls]])
+
+    def D(self):
+        return self.hbar * np.sum(1.0 - self.r ** 2)
+
+    def gradient(self):
+        gD = (-2.0 * self.hbar * self.r) @ self.dr @ self.dT @ self.P
+        return gD + self.alpha * 2.0 * self.hbary * (self.Lap.T @ (self.Lap @ self.u))
+
+    def hess_matrix(self):
+        Jc = self.dr @ self.dT @ self.P
+        return 2.0 * self.hbar * Jc.T @ Jc + self.alpha * 2.0 * self.hbary * self.Lap.T @ self.Lap
