@@ -586,7 +586,7 @@ def run_batch(args):
         ea1.record(stream)
     stream.synchronize()
     auto_ms = ea0.elapsed_time(ea1)
-    # the same pairs one at a time
+    # the same pairs one at a time, each with its own default z-chunk model
     U1 = [torch.zeros(k, device=dev) for k in nn]
     with torch.cuda.stream(stream):
         flush.fill_(0.0)
@@ -598,6 +598,33 @@ def run_batch(args):
     seq_ms = e0.elapsed_time(e1)
     same_u = all(torch.equal(a, b) for a, b in zip(U, U1))
     j_rel = max(abs(a.J - b.J) / abs(b.J) for a, b in zip(reps, reps1))
+    # at equal final NGF: one common z-chunk (the batch's default at the
+    # finest level) for both arms, so every pair takes identical decisions
+    with ngf.Batch(descs, 0, stream) as b0:
+        zc_eq = ngf.ngf_batch_zc(b0.handle)
+    opts_eq = ngf.options(levels=2, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True, zc=zc_eq)
+    Ue = [torch.zeros(k, device=dev) for k in nn]
+    Us = [torch.zeros(k, device=dev) for k in nn]
+    with torch.cuda.stream(stream):
+        ngf.register_batch(descs, opts_eq, R, T, Ue, stream=stream)  # warm-up (plans, graphs)
+        ev_eq = []
+        for k in range(max(1, min(args.steps, 3))):
+            flush.fill_(float(k))
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            reps_e = ngf.register_batch(descs, opts_eq, R, T, Ue, stream=stream)
+            b_.record(stream)
+            ev_eq.append((a_, b_))
+        flush.fill_(0.25)
+        es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        es0.record(stream)
+        reps_s = [ngf.register_multilevel(d, opts_eq, r, t, u, stream) for d, r, t, u in zip(descs, R, T, Us)]
+        es1.record(stream)
+    stream.synchronize()
+    batch_eq_ms = statistics.median(a_.elapsed_time(b_) for a_, b_ in ev_eq)
+    seq_eq_ms = es0.elapsed_time(es1)
+    eq_same_u = all(torch.equal(a_, b_) for a_, b_ in zip(Ue, Us))
+    eq_j_rel = max(abs(a_.J - b_.J) / abs(b_.J) for a_, b_ in zip(reps_e, reps_s))
     # tile autotuner on the finest level, then per-pair parity with the oracle
     import oracle as O
     gen = torch.Generator(device="cpu").manual_seed(31)
@@ -624,11 +651,16 @@ def run_batch(args):
     line = {"workload": "batch_64: 64 blob pairs, cubic N ~ U{64..192} (seed 30), nodes N/2+1, 2 levels, "
                         f"{GN_ITERS} GN x {PCG_ITERS} PCG", "metric": METRIC,
             "value": voxels / (batch_ms / 1e3) / 1e9, "unit": "Gvoxel/s", "steps": args.steps,
-            "warmup": args.warmup, "batched_ms": batch_ms, "sequential_ms": seq_ms,
-            "speedup_vs_sequential": seq_ms / batch_ms, "same_u_as_sequential": same_u,
-            "max_rel_J_diff_vs_sequential": j_rel,
-            "tile_depth_note": "batched and sequential runs each use their default z-chunk model; "
-                               "with one common zc their results are bitwise equal", "total_voxels": total_vox,
+            "warmup": args.warmup,
+            "at_equal_NGF": {"zc": zc_eq, "batched_ms": batch_eq_ms, "sequential_ms": seq_eq_ms,
+                             "speedup_vs_sequential": seq_eq_ms / batch_eq_ms, "same_u_as_sequential": eq_same_u,
+                             "max_rel_J_diff_vs_sequential": eq_j_rel},
+            "default_zc": {"batched_ms": batch_ms, "sequential_ms": seq_ms,
+                           "speedup_vs_sequential": seq_ms / batch_ms, "same_u_as_sequential": same_u,
+                           "max_rel_J_diff_vs_sequential": j_rel,
+                           "note": "each arm with its own default z-chunk model: other tile depths round "
+                                   "differently and the nonconvex problem can follow other trajectories"},
+            "total_voxels": total_vox,
             "autotuned_registration_ms": auto_ms,
             "autotuned_max_rel_J_diff_vs_sequential": max(abs(a.J - b.J) / abs(b.J) for a, b in zip(reps_a, reps1)),
             "batched_hessvec_ms": {"default_zc": ms_default, "autotuned": ms_tuned, "zc": zc},
@@ -783,6 +815,82 @@ def run_learned(args):
     return 0
 
 
+# The paper's 2-D GPU numbers (GeForce GTX 980, FP32, reductions FP64): the
+# objective-gradient time per image and grid size (Sec. 6.4, table of 2-D
+# gradient runtimes) and the 3-level L-BFGS registration time (Sec. 6.4,
+# figure of 2-D registration runtimes), in milliseconds; context, not targets.
+PAPER_2D_GRADIENT_MS = {(4096, 2049): 35.3, (4096, 1025): 33.5, (4096, 513): 32.3, (2048, 1025): 10.0,
+                        (2048, 513): 9.38, (2048, 257): 9.32, (1024, 513): 3.66, (1024, 257): 3.53,
+                        (1024, 129): 2.93, (512, 257): 2.29, (512, 129): 1.67, (512, 65): 1.67, (256, 129): 1.04,
+                        (256, 65): 1.03, (256, 33): 1.07}
+PAPER_2D_LBFGS_S = {4096: 1.51, 2048: 0.560, 1024: 0.267, 512: 0.143, 256: 0.0833}
+
+
+def run_plane_2d(args):
+    """The 2-D method (planar levels) on the paper's 2-D sizes: objective
+    gradient (ngf_gradient_dev: the NGF gradient and D, S on the device) for
+    m^2 images, m in 256..4096, with m/2+1, m/4+1 and m/8+1 nodes per axis
+    (median of `steps` calls after warm-up, CUDA events), and the 3-level
+    L-BFGS registration with nodes m/4+1 and 20 steps per level (median of
+    3), on synthetic tissue-like pairs (the histology data is not available)."""
+    import numpy as np
+    import torch
+    from paper_1804_10541_b300 import ngf, synth
+    dev = torch.device("cuda", 0)
+    sizes = [256, 512, 1024, 2048, 4096]
+    grad_rows, reg_rows = [], []
+    launches0 = ngf.ngf_launch_count()
+    for M in sizes:
+        R, T = synth.tissue_pair_2d((M, M), seed=60 + M, device=dev)
+        for k in (2, 4, 8):
+            nn = M // k + 1
+            desc = ngf.level_desc((M, M, 1), (1.0, 1.0, 1.0), (nn, nn, 1), 1.0, 0.05, 0.05)
+            N = nn * nn
+            g = torch.Generator().manual_seed(M + k)
+            u = torch.cat([0.5 * torch.randn(2 * N, generator=g), torch.zeros(N)]).to(dev)
+            grad = torch.empty(3 * N, device=dev)
+            ds = torch.empty(2, device=dev, dtype=torch.float64)
+            with ngf.Plan(desc) as pl:
+                for _ in range(max(3, args.warmup)):
+                    ngf.ngf_gradient_dev(pl.handle, R, T, u, grad, ds)
+                ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                      for _ in range(max(5, args.steps))]
+                for a, b in ev:
+                    a.record()
+                    ngf.ngf_gradient_dev(pl.handle, R, T, u, grad, ds)
+                    b.record()
+                torch.cuda.synchronize()
+            ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+            grad_rows.append({"m": M, "nodes": nn, "ms": ms, "gpixel_s": M * M / ms / 1e6,
+                              "paper_gtx980_ms": PAPER_2D_GRADIENT_MS.get((M, nn))})
+        nn = M // 4 + 1
+        desc = ngf.level_desc((M, M, 1), (1.0, 1.0, 1.0), (nn, nn, 1), 1.0, 0.05, 0.05)
+        opts = ngf.options(levels=3, gn_iters=20, method=ngf.NGF_METHOD_LBFGS, lbfgs_memory=5)
+        u = torch.zeros(3 * nn * nn, device=dev)
+        stream = torch.cuda.Stream(device=dev)
+        times, rep = [], None
+        with torch.cuda.stream(stream):
+            ngf.register_multilevel(desc, opts, R, T, u, stream)
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rep = ngf.register_multilevel(desc, opts, R, T, u, stream)
+                e1.record(stream)
+                stream.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+        reg_rows.append({"m": M, "nodes": nn, "seconds": statistics.median(times), "steps": rep.gn_done,
+                         "ls_trials": rep.ls_trials, "J": rep.J, "paper_gtx980_s": PAPER_2D_LBFGS_S.get(M)})
+        del R, T
+    line = {"workload": "plane_2d: 2-D method (one image plane, one node plane) on synthetic tissue-like m^2 pairs "
+                        "(unit spacing, alpha 1, tau = rho = 0.05)", "metric": "2-D objective gradient ms",
+            "unit": "ms", "gradient": grad_rows, "lbfgs_registration_3_levels_20_steps": reg_rows,
+            "gpu_launches": int(ngf.ngf_launch_count() - launches0),
+            "note": "paper numbers: GeForce GTX 980, histology pairs; context, not a like-for-like target",
+            "dtype": "f32", "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _meminfo_gb(key="MemAvailable"):
     try:
         with open("/proc/meminfo") as f:
@@ -907,7 +1015,7 @@ def main():
     ap.add_argument("--slab", type=int, default=0, help="--kernel-case: central z-slab of this many planes")
     ap.add_argument("--distance", default="ngf", choices=["ngf", "ssd"], help="distance of --kernel-case")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[*REG_WORKLOADS, "batch_64", "conv3d", "oracle_timing", "learned"],
+                    choices=[*REG_WORKLOADS, "batch_64", "conv3d", "oracle_timing", "learned", "plane_2d"],
                     help="thorax_abd (default) / lung_ct: full registrations; batch_64: the batched form on 64 "
                          "uneven pairs; conv3d: the tensor-core convolution layers; oracle_timing: the FP64 "
                          "oracle on the host cores (each of the last three prints its own JSON line)")
@@ -926,6 +1034,8 @@ def main():
         return run_oracle_timing(args)
     if args.workload == "learned":
         return run_learned(args)
+    if args.workload == "plane_2d":
+        return run_plane_2d(args)
     if args.workload == "conv3d":
         return run_conv3d(args)
     if args.impl == "reference":

@@ -417,6 +417,94 @@ def thorax_pair(m=(512, 512, 900), h=(0.8, 0.8, 1.0), seed=20, device="cpu", noi
     return R, T, U
 
 
+def tissue_pair_2d(m, h=(1.0, 1.0), seed=50, device="cpu", blobs=None, max_disp_px=None, noise=0.02):
+    """2-D pair (one image plane) standing in for the paper's histological
+    serial sections: a smooth background and many small Gaussian "nuclei"
+    (about one per 400 pixels, sigma 1.5-4 pixels, amplitude U[0.3, 1]),
+    evaluated at the pixel centres (R) and at x + u*(x) (T) with u* a sum of
+    6 low-frequency sines scaled to max_disp_px (default m0 / 64 pixels),
+    plus noise sd `noise`.  Each nucleus is evaluated on a window of pixels
+    (4 sigma around it for R; around its pre-image under u*, widened by the
+    change of u* across the window, for T) and added by a scatter.  Seeds:
+    seed (blobs), +1 (R noise), +2 (u*), +3 (T noise).  Returns R, T as
+    float32 of length m0 m1."""
+    r = _rng(seed)
+    ext = np.asarray(m[:2], float) * np.asarray(h[:2], float)
+    nb = blobs if blobs is not None else max(8, (m[0] * m[1]) // 400)
+    c = r.uniform(0.0, 1.0, size=(nb, 2)) * ext
+    sig = r.uniform(1.5, 4.0, size=nb) * min(h[:2])
+    amp = r.uniform(0.3, 1.0, size=nb)
+    rd = _rng(seed + 2)
+    freq = rd.integers(0, 3, size=(6, 2))
+    freq[np.all(freq == 0, axis=1), 0] = 1
+    famp = rd.normal(size=(6, 2))
+    phase = rd.uniform(0, 2 * math.pi, size=(6, 2))
+    md = (max_disp_px if max_disp_px is not None else m[0] / 64.0) * min(h[:2])
+    dtype = torch.float32
+
+    def field(X, Y):
+        out = []
+        for d in range(2):
+            acc = torch.zeros_like(X)
+            for k in range(6):
+                acc = acc + famp[k, d] * torch.sin(math.pi * (freq[k, 0] * X / ext[0] + freq[k, 1] * Y / ext[1])
+                                                   + phase[k, d])
+            out.append(acc)
+        return out
+
+    Xs = torch.linspace(0, ext[0], 65, dtype=torch.float64).view(1, -1).expand(65, 65)
+    Ys = torch.linspace(0, ext[1], 65, dtype=torch.float64).view(-1, 1).expand(65, 65)
+    fs = field(Xs, Ys)
+    scale = md / float(torch.sqrt(fs[0] ** 2 + fs[1] ** 2).max())
+    M = m[0] * m[1]
+    x = ((torch.arange(m[0], device=device, dtype=dtype) + 0.5) * h[0]).view(1, -1).expand(m[1], m[0])
+    y = ((torch.arange(m[1], device=device, dtype=dtype) + 0.5) * h[1]).view(-1, 1).expand(m[1], m[0])
+    ux, uy = (scale * f for f in field(x, y))
+    # bound of |grad u*| (pixels per pixel) from the frequencies
+    gmax = scale * float(np.abs(famp).sum(0).max()) * math.pi * 2.0 / float(min(ext)) * 2.0
+
+    def render(warped):
+        v = 0.2 + 0.1 * torch.sin(2 * math.pi * ((x + ux) if warped else x) / ext[0]) * \
+            torch.cos(2 * math.pi * ((y + uy) if warped else y) / ext[1])
+        v = v.reshape(-1).clone()
+        cb = torch.tensor(c, dtype=dtype, device=device)
+        if warped:  # pre-image of each centre under x -> x + u*(x)
+            cu = torch.stack(field(cb[:, 0:1].double().cpu(), cb[:, 1:2].double().cpu()), dim=1).view(-1, 2)
+            cb = cb - (scale * cu).to(device=device, dtype=dtype)
+        rad = 4.0 * float(sig.max())
+        half = int(math.ceil((rad + (gmax * rad + 1.0 if warped else 0.0)) / min(h[:2]))) + 1
+        off = torch.arange(-half, half + 1, device=device)
+        oy, ox = torch.meshgrid(off, off, indexing="ij")
+        ox, oy = ox.reshape(1, -1), oy.reshape(1, -1)
+        sb = torch.tensor(sig, dtype=dtype, device=device).view(-1, 1)
+        ab = torch.tensor(amp, dtype=dtype, device=device).view(-1, 1)
+        c0 = torch.tensor(c, dtype=dtype, device=device)
+        for k0 in range(0, nb, 2048):
+            sl = slice(k0, k0 + 2048)
+            px = torch.floor(cb[sl, 0:1] / h[0]).long() + ox
+            py = torch.floor(cb[sl, 1:2] / h[1]).long() + oy
+            ok = (px >= 0) & (px < m[0]) & (py >= 0) & (py < m[1])
+            pxc, pyc = px.clamp(0, m[0] - 1), py.clamp(0, m[1] - 1)
+            flat = pyc * m[0] + pxc
+            X = (pxc.to(dtype) + 0.5) * h[0]
+            Y = (pyc.to(dtype) + 0.5) * h[1]
+            if warped:
+                X = X + ux.reshape(-1)[flat]
+                Y = Y + uy.reshape(-1)[flat]
+            d2 = (X - c0[sl, 0:1]) ** 2 + (Y - c0[sl, 1:2]) ** 2
+            g = ab[sl] * torch.exp(-d2 / (2 * sb[sl] ** 2)) * ok
+            v.index_add_(0, flat.reshape(-1), g.reshape(-1))
+        return v
+
+    R = render(False)
+    T = render(True)
+    gR = torch.Generator(device="cpu").manual_seed(seed + 1)
+    gT = torch.Generator(device="cpu").manual_seed(seed + 3)
+    R += noise * torch.randn(M, generator=gR, dtype=dtype).to(device)
+    T += noise * torch.randn(M, generator=gT, dtype=dtype).to(device)
+    return R, T
+
+
 def make(workload, device="cpu"):
     """(R, T, u_true, desc) for a named workload; R, T are float32 of length
     m_x m_y m_z on `device`, u_true is 3 x M (image grid, mm)."""
