@@ -598,33 +598,35 @@ def run_batch(args):
     seq_ms = e0.elapsed_time(e1)
     same_u = all(torch.equal(a, b) for a, b in zip(U, U1))
     j_rel = max(abs(a.J - b.J) / abs(b.J) for a, b in zip(reps, reps1))
-    # at equal final NGF: one common z-chunk (the batch's default at the
-    # finest level) for both arms, so every pair takes identical decisions
+    # at equal final NGF: one common z-chunk for both arms on every level, so
+    # every pair takes identical decisions (bitwise equal u); several common
+    # chunk lengths are timed and the one that is best for the sequential
+    # arm is quoted (a long chunk starves a single small pair of CTAs)
     with ngf.Batch(descs, 0, stream) as b0:
-        zc_eq = ngf.ngf_batch_zc(b0.handle)
-    opts_eq = ngf.options(levels=2, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True, zc=zc_eq)
-    Ue = [torch.zeros(k, device=dev) for k in nn]
-    Us = [torch.zeros(k, device=dev) for k in nn]
-    with torch.cuda.stream(stream):
-        ngf.register_batch(descs, opts_eq, R, T, Ue, stream=stream)  # warm-up (plans, graphs)
-        ev_eq = []
-        for k in range(max(1, min(args.steps, 3))):
-            flush.fill_(float(k))
+        zc_batch = ngf.ngf_batch_zc(b0.handle)
+    eq_rows = []
+    for zc_c in sorted({8, 16, 32, zc_batch}):
+        opts_eq = ngf.options(levels=2, gn_iters=GN_ITERS, pcg_iters=PCG_ITERS, use_graph=True, zc=zc_c)
+        Ue = [torch.zeros(k, device=dev) for k in nn]
+        Us = [torch.zeros(k, device=dev) for k in nn]
+        with torch.cuda.stream(stream):
+            ngf.register_batch(descs, opts_eq, R, T, Ue, stream=stream)  # warm-up (plans, graphs)
+            flush.fill_(0.5)
             a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a_.record(stream)
             reps_e = ngf.register_batch(descs, opts_eq, R, T, Ue, stream=stream)
             b_.record(stream)
-            ev_eq.append((a_, b_))
-        flush.fill_(0.25)
-        es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        es0.record(stream)
-        reps_s = [ngf.register_multilevel(d, opts_eq, r, t, u, stream) for d, r, t, u in zip(descs, R, T, Us)]
-        es1.record(stream)
-    stream.synchronize()
-    batch_eq_ms = statistics.median(a_.elapsed_time(b_) for a_, b_ in ev_eq)
-    seq_eq_ms = es0.elapsed_time(es1)
-    eq_same_u = all(torch.equal(a_, b_) for a_, b_ in zip(Ue, Us))
-    eq_j_rel = max(abs(a_.J - b_.J) / abs(b_.J) for a_, b_ in zip(reps_e, reps_s))
+            flush.fill_(0.25)
+            es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            es0.record(stream)
+            reps_s = [ngf.register_multilevel(d, opts_eq, r, t, u, stream) for d, r, t, u in zip(descs, R, T, Us)]
+            es1.record(stream)
+        stream.synchronize()
+        eq_rows.append({"zc": zc_c, "batched_ms": a_.elapsed_time(b_), "sequential_ms": es0.elapsed_time(es1),
+                        "same_u_as_sequential": all(torch.equal(x_, y_) for x_, y_ in zip(Ue, Us)),
+                        "max_rel_J_diff_vs_sequential": max(abs(x_.J - y_.J) / abs(y_.J)
+                                                            for x_, y_ in zip(reps_e, reps_s))})
+    best = min(eq_rows, key=lambda r_: r_["sequential_ms"])
     # tile autotuner on the finest level, then per-pair parity with the oracle
     import oracle as O
     gen = torch.Generator(device="cpu").manual_seed(31)
@@ -652,9 +654,9 @@ def run_batch(args):
                         f"{GN_ITERS} GN x {PCG_ITERS} PCG", "metric": METRIC,
             "value": voxels / (batch_ms / 1e3) / 1e9, "unit": "Gvoxel/s", "steps": args.steps,
             "warmup": args.warmup,
-            "at_equal_NGF": {"zc": zc_eq, "batched_ms": batch_eq_ms, "sequential_ms": seq_eq_ms,
-                             "speedup_vs_sequential": seq_eq_ms / batch_eq_ms, "same_u_as_sequential": eq_same_u,
-                             "max_rel_J_diff_vs_sequential": eq_j_rel},
+            "at_equal_NGF": {**best, "speedup_vs_sequential": best["sequential_ms"] / best["batched_ms"],
+                             "note": "common z-chunk on both arms (the sequential arm's best of those timed)",
+                             "all_common_zc": eq_rows},
             "default_zc": {"batched_ms": batch_ms, "sequential_ms": seq_ms,
                            "speedup_vs_sequential": seq_ms / batch_ms, "same_u_as_sequential": same_u,
                            "max_rel_J_diff_vs_sequential": j_rel,

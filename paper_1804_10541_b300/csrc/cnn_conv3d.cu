@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -639,6 +640,7 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
         return NGF_ECUDA;
     const size_t per_sm = (size_t)smem_sm;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     {
         // brick form: P output planes per CTA, as many as leave room for two
         // CTAs per SM (256 tensor-memory columns, about 110 KB of shared
@@ -692,7 +694,6 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
         if (!brick_attr_set()) return NGF_ECUDA;
         // weights repacked per (slice, chunk, tap) into the B operand's
         // shared-memory image
-        cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
         void* wp = nullptr;
         if (dev_alloc(&wp, 27 * (size_t)Cout * Cin * 2, st) != cudaSuccess) return NGF_ENOMEM;
         const long long chunks = 27LL * Cout * (Cin / 8);

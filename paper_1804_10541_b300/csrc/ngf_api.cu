@@ -416,6 +416,10 @@ ImgParams img_params(const Plan* p, const float* R, const float* T, const float*
         P.ihs[a] = (float)(1.0 / (d.h[a] * d.h[a]));
         P.hh[a] = (float)(1.0 / (2.0 * d.h[a] * d.h[a]));
     }
+    // a planar level (the 2-D method) samples its one image plane: no z
+    // displacement and no z derivative of the template, one node plane
+    if (planar(d)) P.ih[2] = 0.f;
+    P.znext = p->n[2] > 1 ? p->n[0] * p->n[1] : 0;
     P.tau = (float)d.tau;
     P.rho = (float)d.rho;
     P.tr = (float)(d.tau * d.rho);

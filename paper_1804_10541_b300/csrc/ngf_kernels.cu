@@ -83,10 +83,6 @@ __device__ __forceinline__ void grid_sum_finish(double blocksum, double* part, u
 __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy, int gz, float d0, float d1,
                                              float d2, float& g0, float& g1, float& g2) {
     g0 = g1 = g2 = 0.f;
-    // a planar (2-D) level samples its one plane bilinearly: no z displacement,
-    // no zero-padded neighbour plane, no z derivative
-    const bool planar = P.m2 == 1 && P.n2 == 1;
-    if (planar) d2 = 0.f;
     if (!(fabsf(d0) < 1.0e9f) || !(fabsf(d1) < 1.0e9f) || !(fabsf(d2) < 1.0e9f)) return 0.f;
     const float f0 = floorf(d0), f1 = floorf(d1), f2 = floorf(d2);
     const int cx = gx + (int)f0, cy = gy + (int)f1, cz = gz + (int)f2;
@@ -133,7 +129,7 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
     const float q1 = fmaf(ty, (v111 - v011) - (v101 - v001), v101 - v001);
     g0 = fmaf(tz, q1 - q0, q0) * P.ih[0];
     g1 = fmaf(tz, (e11 - e01) - (e10 - e00), e10 - e00) * P.ih[1];
-    g2 = planar ? 0.f : (a1 - a0) * P.ih[2];
+    g2 = (a1 - a0) * P.ih[2];  // a planar level has ih[2] = 0: d2 = 0 and no z derivative
     return fmaf(tz, a1 - a0, a0);
 }
 
@@ -272,7 +268,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
 #pragma unroll
             for (int c = 0; c < NVEC; ++c) {
                 const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
-                const float a = __ldg(src + o), b = P.n2 > 1 ? __ldg(src + o + plane_n) : a;
+                const float a = __ldg(src + o), b = __ldg(src + o + P.znext);
                 (&S.Uz[c][0][0])[s0_s[k]] = fmaf(wzz, b - a, a);
             }
         }
@@ -604,7 +600,7 @@ __device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, i
 #pragma unroll
             for (int c = 0; c < NVEC; ++c) {
                 const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
-                const float a = __ldg(src + o), b = P.n2 > 1 ? __ldg(src + o + plane_n) : a;
+                const float a = __ldg(src + o), b = __ldg(src + o + P.znext);
                 (&S.Uz[c][0][0])[s0_s[k]] = fmaf(wzz, b - a, a);
             }
         }
@@ -824,7 +820,7 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
                 const int by = rem / UXn, bx = rem - by * UXn;
                 const float* src = P.u + c * P.N;
                 const long long o = pl0 + (UX0 + bx) + (long long)P.n0 * (UY0 + by);
-                const float a = __ldg(src + o), b = P.n2 > 1 ? __ldg(src + o + plane) : a;
+                const float a = __ldg(src + o), b = __ldg(src + o + P.znext);
                 S.Uz[c][by][bx] = fmaf(wzz, b - a, a);
             }
         }
@@ -921,6 +917,11 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
             int po[SPAN];
 #pragma unroll
             for (int g = 0; g < SPAN; ++g) po[g] = ((bzm + g + BZ0) & 3) * WPLANE + bxm;
+            // node planes and rows this voxel row reaches: the stencil's lowest
+            // floor up to its highest floor + 1 (two, not three, inside a cell);
+            // both are uniform over the warp (one row, one plane), and the
+            // entries beyond them are exactly zero, so they are skipped
+            const int spanY = min(SPAN, fyp - fym + 2), spanZ = min(SPAN, fzp - fzm + 2);
 #pragma unroll 1
             for (int d = 0; d < 3; ++d) {
                 const float* dTd[3] = {S.dT[szm][d], S.dT[sc][d], S.dT[szp][d]};
@@ -939,7 +940,7 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
                 // bounds are checked; the 2 hbar factor is applied at the store
 #pragma unroll
                 for (int b = 0; b < SPAN; ++b) {
-                    if (bym + b >= nby) continue;  // uniform over the warp
+                    if (b >= spanY || bym + b >= nby) continue;  // uniform over the warp
 #pragma unroll
                     for (int a = 0; a < SPAN; ++a) {
                         const bool inb = bxm + a < nbx;
@@ -947,6 +948,7 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
                         const float xy2 = WY[1][b] * WX[1][a];
 #pragma unroll
                         for (int g = 0; g < SPAN; ++g) {
+                            if (g >= spanZ) break;  // uniform over the warp
                             const float J = fmaf(WZ[1][g], xy1, cz[g] * xy2);
                             float v = act ? J * J : 0.f;
 #pragma unroll

@@ -42,8 +42,10 @@ enum Mode { MODE_OBJ = 0, MODE_GRAD = 1, MODE_HESS = 2 };
 
 struct ImgParams {
     int m0, m1, m2, n0, n1, n2;
+    int znext;      // offset of the upper node plane of the z interpolation:
+                    // n0 n1, or 0 on a planar level (one node plane)
     long long M, N;
-    float ih[3];    // 1/h
+    float ih[3];    // 1/h (ih[2] = 0 on a planar level: no z displacement or derivative)
     float ihs[3];   // 1/h^2
     float hh[3];    // 1/(2 h^2)  (h_hat of Eq. hatRho)
     float tau, rho, tr, tau2, rho2;

@@ -190,6 +190,8 @@ extern "C" ngf_status ngf_objective_noalloc(const ngf_level_desc* d, const float
         P.ihs[a] = (float)(1.0 / (d->h[a] * d->h[a]));
         P.hh[a] = (float)(1.0 / (2.0 * d->h[a] * d->h[a]));
     }
+    if (planar(*d)) P.ih[2] = 0.f;
+    P.znext = d->n[2] > 1 ? d->n[0] * d->n[1] : 0;
     P.tau = (float)d->tau;
     P.rho = (float)d->rho;
     P.tr = (float)(d->tau * d->rho);

@@ -101,6 +101,21 @@ def test_forward_bf16_relu_matches_oracle(ngf, shape):
     assert np.all(err <= bound), float((err / bound).max())
 
 
+def test_dgrad_large_volume_matches_oracle(ngf):
+    """A data gradient on a volume with more tiles than SMs (no output
+    channel slicing in the mirrored convolution), checked element-wise."""
+    shape = (1, 32, 48, 64, 32, 16)
+    x, w, dy = _data(shape, 99)
+    B, D, H, W, Ci, Co = shape
+    dx = torch.empty((B, D, H, W, Ci), device="cuda", dtype=torch.bfloat16)
+    ngf.ngf_conv3d_dgrad(dy.cuda(), w.cuda(), dx, flags=ngf.NGF_CONV_OUT_BF16)
+    assert ngf.ngf_conv3d_check() == 0
+    ref = CO.conv3d_dgrad(_f(dy), _f(w))
+    bound = 1e-5 * CO.dgrad_abs(_f(dy), _f(w)) + 2.0 ** -8 * np.abs(ref) + 1e-30
+    err = np.abs(_f(dx) - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
 def test_gradients_are_deterministic(ngf):
     x, w, dy = _data((1, 12, 10, 20, 32, 64), 77)
     x, w, dy = x.cuda(), w.cuda(), dy.cuda()
