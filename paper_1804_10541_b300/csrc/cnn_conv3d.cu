@@ -662,8 +662,12 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
         br.P = 1;
         br.nbuf = 3;
         br.ns = Cout;
+        // with 16 input channels (a small brick) and at most 32 output
+        // channels, two planes per CTA and twice the CTAs per SM hide the
+        // staging latency better (measured 5-7% faster; wider layers lose)
+        const int col_cap = (Cin == 16 && ncols == 32) ? 64 : 256;
         for (int p = 4; p >= 1; p >>= 1) {
-            if (p * ncols > 256 || (p > 1 && p > D)) continue;
+            if (p * ncols > col_cap || (p > 1 && p > D)) continue;
             const size_t wst = (size_t)Cout * br.kc * 2;
             const size_t brick = (size_t)(br.kc / 8) * BR_X * BR_Y * (p + 2) * 16;
             int nbf = CONV_MAXBUF;
