@@ -121,11 +121,11 @@ def image_pass_source_hash():
     csrc = os.path.join(ROOT, "paper_1804_10541_b300", "csrc")
     with open(os.path.join(csrc, "ngf_kernels.cu")) as f:
         cu = f.read()
-    end = cu.index("image_pass<MODE_HESS>(P, blockIdx.x, blockIdx.y, blockIdx.z);")
+    end = cu.index("image_pass<MODE_HESS, ImgSmemC>(P, blockIdx.x, blockIdx.y, blockIdx.z);")
     with open(os.path.join(csrc, "ngf_kernels.cuh")) as f:
         cuh = f.read()
     a = cuh.index("constexpr int TX")
-    b = cuh.index("};", cuh.index("struct ImgSmem")) + 2
+    b = cuh.index("constexpr int IMG_FILL")
     return hashlib.sha256((cu[:end] + cuh[a:b]).encode()).hexdigest()
 
 

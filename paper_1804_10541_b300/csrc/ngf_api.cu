@@ -286,9 +286,9 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     p->hbary = node_cell_volume(*d);
 
     // z-chunking: k chunks per column of tiles, chosen to minimise
-    // (rounds of 2 CTAs per SM) x (planes marched per chunk, 5 of them fill
-    // and drain); small levels get short chunks, since a CTA's march over
-    // its planes is sequential
+    // (rounds of 2 CTAs per SM) x (planes marched per chunk, 7 of them fill
+    // and drain the image pass's pipeline); small levels get short chunks,
+    // since a CTA's march over its planes is sequential
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -298,7 +298,7 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     for (long long k = 1; k <= std::min<long long>(p->m[2], 1024); ++k) {
         const long long zc = (p->m[2] + k - 1) / k;
         const long long chunks = (p->m[2] + zc - 1) / zc;
-        const long long cost = ((txy * chunks + slots - 1) / slots) * (zc + 5);
+        const long long cost = ((txy * chunks + slots - 1) / slots) * (zc + IMG_FILL);
         if (cost < best_cost) {
             best_cost = cost;
             best_k = k;
@@ -348,6 +348,22 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     NGF_CU(p, cudaMemcpyAsync(p->ftab, fh.data(), tl * sizeof(int), cudaMemcpyHostToDevice, p->stream), "copy tables");
     NGF_CU(p, cudaMemcpyAsync(p->wtab, wh.data(), tl * sizeof(float), cudaMemcpyHostToDevice, p->stream), "copy tables");
 
+    // image-pass layout: the compact one when every tile's front-end node box
+    // and owned node box fit it (two or more voxels per cell in x and y)
+    {
+        int ux = 0, uy = 0, bxm = 0, bym = 0;
+        for (int xs = 0; xs < p->m[0]; xs += TX) {
+            ux = std::max(ux, f[0][std::min(xs + TX + 1, p->m[0] - 1)] + 2 - f[0][std::max(xs - 2, 0)]);
+            bxm = std::max(bxm, f[0][std::min(xs + TX, p->m[0]) - 1] + 2 - f[0][xs]);
+        }
+        for (int ys = 0; ys < p->m[1]; ys += TY) {
+            uy = std::max(uy, f[1][std::min(ys + TY + 1, p->m[1] - 1)] + 2 - f[1][std::max(ys - 2, 0)]);
+            bym = std::max(bym, f[1][std::min(ys + TY, p->m[1]) - 1] + 2 - f[1][ys]);
+        }
+        p->img_wide = ux > ImgSmemC::kUBX || uy > ImgSmemC::kUBY || bxm > ImgSmemC::kNBX || bym > ImgSmemC::kNBY;
+        if (ux > UBX || uy > UBY || bxm > NBX || bym > NBY)
+            return set_error(p, NGF_EBOUNDS, "internal: tile node box exceeds the image pass's shared-memory box");
+    }
     NGF_TRY(build_geometry(p, 0, f, p->g0));
     NGF_TRY(build_geometry(p, 1, f, p->g1));
     if (p->g0.pbx > NBX || p->g0.pby > NBY || p->g1.pbx > DBX || p->g1.pby > DBY)
@@ -375,11 +391,14 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     NGF_CU(p, dev_alloc((void**)&p->dcount, 4 * sizeof(unsigned int), p->stream), "allocate counter");
     NGF_CU(p, cudaMemsetAsync(p->dcount, 0, 4 * sizeof(unsigned int), p->stream), "clear counter");
 
-    NGF_CU(p, cudaFuncSetAttribute(k_image_obj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
-    NGF_CU(p, cudaFuncSetAttribute(k_image_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
-    NGF_CU(p, cudaFuncSetAttribute(k_image_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)), "smem attr");
+    for (auto kern : {k_image_obj, k_image_grad, k_image_hess})
+        NGF_CU(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmemC)),
+               "smem attr");
+    for (auto kern : {k_image_obj_w, k_image_grad_w, k_image_hess_w})
+        NGF_CU(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmemW)),
+               "smem attr");
     for (auto kern : {k_ssd_obj, k_ssd_grad, k_ssd_hess, k_ssd_diag})
-        NGF_CU(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem)),
+        NGF_CU(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsdSmem)),
                "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmem)), "smem attr");
@@ -485,10 +504,23 @@ static dim3 img_grid(const Geometry& g) { return dim3(g.ntx, g.nty, g.ntz); }
 
 static bool ssd(const Plan* p) { return p->desc.distance == NGF_DIST_SSD; }
 
+// the image-pass kernel of a mode for this plan's distance and layout, and
+// its shared memory
+using ImgKernel = void (*)(const ImgParams);
+static ImgKernel img_kernel(const Plan* p, int mode) {
+    static const ImgKernel tab[3][3] = {{k_image_obj, k_image_grad, k_image_hess},
+                                        {k_image_obj_w, k_image_grad_w, k_image_hess_w},
+                                        {k_ssd_obj, k_ssd_grad, k_ssd_hess}};
+    return tab[ssd(p) ? 2 : (p->img_wide ? 1 : 0)][mode];
+}
+static size_t img_smem(const Plan* p) {
+    return ssd(p) ? sizeof(SsdSmem) : (p->img_wide ? sizeof(ImgSmemW) : sizeof(ImgSmemC));
+}
+
 ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* u, double* dD, double* dS) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_OBJ, p->g0, dD);
     NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
-    NGF_CU(p, launch(ssd(p) ? k_ssd_obj : k_image_obj, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P),
+    NGF_CU(p, launch(img_kernel(p, MODE_OBJ), img_grid(p->g0), dim3(NT), img_smem(p), p->stream, P),
            "k_image_obj");
     NGF_CU(p, prof_mark(p, NGF_K_OBJECTIVE), "cudaEventRecord");
     NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
@@ -501,7 +533,7 @@ ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u
                          double* dS) {
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_GRAD, p->g0, dD);
     NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
-    NGF_CU(p, launch(ssd(p) ? k_ssd_grad : k_image_grad, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P),
+    NGF_CU(p, launch(img_kernel(p, MODE_GRAD), img_grid(p->g0), dim3(NT), img_smem(p), p->stream, P),
            "k_image_grad");
     NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
     NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
@@ -519,7 +551,7 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
            "k_lap");
     ImgParams P = img_params(p, R, T, u, pv, MODE_HESS, p->g0, nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
-    NGF_CU(p, launch(ssd(p) ? k_ssd_hess : k_image_hess, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P),
+    NGF_CU(p, launch(img_kernel(p, MODE_HESS), img_grid(p->g0), dim3(NT), img_smem(p), p->stream, P),
            "k_image_hess");
     NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
     CombineParams C = combine_params(p, p->g0, q, p->L, nullptr, dotw, dout);
@@ -531,7 +563,7 @@ ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u
     if (ssd(p)) {  // no neighbour coupling: the halo-0 geometry
         ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g0, nullptr);
         NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
-        NGF_CU(p, launch(k_ssd_diag, img_grid(p->g0), dim3(NT), sizeof(ImgSmem), p->stream, P), "k_ssd_diag");
+        NGF_CU(p, launch(k_ssd_diag, img_grid(p->g0), dim3(NT), sizeof(SsdSmem), p->stream, P), "k_ssd_diag");
         NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
         CombineParams C = combine_params(p, p->g0, diag, nullptr, p->ctab, nullptr, nullptr);
         NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");

@@ -122,7 +122,7 @@ static void tile_items(const Batch& b, int p0, int p1, bool halo1, int want_span
             for (int y = 0; y < g.nty; ++y)
                 for (int x = 0; x < g.ntx; ++x) {
                     const long long vx = std::min(TX, p->m[0] - x * TX), vy = std::min(TY, p->m[1] - y * TY);
-                    const long long vz = std::min(p->zc, p->m[2] - z * p->zc) + 5;  // plus the march's fill planes
+                    const long long vz = std::min(p->zc, p->m[2] - z * p->zc) + IMG_FILL;  // plus the march's fill planes
                     it.push_back({vx * vy * vz, make_int4(k, x, y, z)});
                 }
     }
@@ -133,7 +133,7 @@ static void tile_items(const Batch& b, int p0, int p1, bool halo1, int want_span
 
 // One z-chunk length for all pairs (capped by each pair's depth), chosen to
 // minimise the persistent queue's time: the larger of (all items' marched
-// planes / slots of 2 CTAs per SM) and the longest item (zc + 5 planes).
+// planes / slots of 2 CTAs per SM) and the longest item (zc + IMG_FILL planes).
 static int batch_zc(const ngf_level_desc* descs, int np, int sms) {
     int best = 1;
     double best_cost = 1e300;
@@ -143,8 +143,8 @@ static int batch_zc(const ngf_level_desc* descs, int np, int sms) {
         for (int k = 0; k < np; ++k) {
             const int m2 = descs[k].m[2], z = std::min(zc, m2);
             const long long tiles = (long long)((descs[k].m[0] + TX - 1) / TX) * ((descs[k].m[1] + TY - 1) / TY);
-            work += (double)tiles * ((m2 + z - 1) / z) * (z + 5);
-            longest = std::max(longest, z + 5);
+            work += (double)tiles * ((m2 + z - 1) / z) * (z + IMG_FILL);
+            longest = std::max(longest, z + IMG_FILL);
         }
         const double cost = std::max(work / (2.0 * sms), (double)longest);
         if (cost < best_cost) {
@@ -153,6 +153,12 @@ static int batch_zc(const ngf_level_desc* descs, int np, int sms) {
         }
     }
     return best;
+}
+
+// shared memory of a batched image pass: NGF pairs in the compact or wide
+// layout and SSD pairs share one launch
+static size_t batch_img_smem(bool wide) {
+    return std::max(sizeof(SsdSmem), wide ? sizeof(ImgSmemW) : sizeof(ImgSmemC));
 }
 
 static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int zc, cudaStream_t stream) {
@@ -203,13 +209,15 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     b->t_img.assign(np, ImgParams{});
     B_CU(b->t_lap.alloc(np, stream), "allocate batch tables");
     B_CU(b->t_comb.alloc(np, stream), "allocate batch tables");
-    const int ismem = (int)sizeof(ImgSmem), dsmem = (int)sizeof(DiagSmem);
-    B_CU(cudaFuncSetAttribute(k_batch_image_obj, cudaFuncAttributeMaxDynamicSharedMemorySize, ismem), "smem attr");
-    B_CU(cudaFuncSetAttribute(k_batch_image_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, ismem), "smem attr");
-    B_CU(cudaFuncSetAttribute(k_batch_image_hess, cudaFuncAttributeMaxDynamicSharedMemorySize, ismem), "smem attr");
+    const int csmem = (int)batch_img_smem(false), wsmem = (int)batch_img_smem(true), dsmem = (int)sizeof(DiagSmem);
+    for (auto kern : {k_batch_image_obj, k_batch_image_grad, k_batch_image_hess})
+        B_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, csmem), "smem attr");
+    for (auto kern : {k_batch_image_obj_w, k_batch_image_grad_w, k_batch_image_hess_w})
+        B_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem), "smem attr");
-    B_CU(cudaFuncSetAttribute(k_batch_ssd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, ismem), "smem attr");
+    B_CU(cudaFuncSetAttribute(k_batch_ssd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsdSmem)),
+         "smem attr");
     B_CU(cudaStreamSynchronize(stream), "cudaStreamSynchronize");
     return NGF_OK;
 }
@@ -249,11 +257,13 @@ static ngf_status launch_image(const Batch& b, int mode, const std::vector<ImgPa
         fill_table(b, r, tab, *T);
         const BatchQueue Q = queue(b, r, r.items0, active);
         const dim3 grid(std::min((int)r.items0.h.size(), 2 * b.sms));
-        if (mode == MODE_OBJ)
-            B_CU(launch(k_batch_image_obj, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_image_obj");
-        else if (mode == MODE_GRAD)
-            B_CU(launch(k_batch_image_grad, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_image_grad");
-        else B_CU(launch(k_batch_image_hess, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_image_hess");
+        bool wide = false;  // the wide layout when any NGF pair of the range needs it
+        for (int k = r.p0; k < r.p1; ++k) wide = wide || (!is_ssd(b.plan(k)) && b.plan(k)->img_wide);
+        using BK = void (*)(const BatchQueue, const BatchImgTable);
+        static const BK tab2[2][3] = {{k_batch_image_obj, k_batch_image_grad, k_batch_image_hess},
+                                      {k_batch_image_obj_w, k_batch_image_grad_w, k_batch_image_hess_w}};
+        B_CU(launch(tab2[wide ? 1 : 0][mode], grid, dim3(NT), batch_img_smem(wide), b.stream, Q, *T),
+             "k_batch_image");
     }
     return NGF_OK;
 }
@@ -276,7 +286,7 @@ static ngf_status launch_diag(const Batch& b, const std::vector<ImgParams>& tab,
         if (!r.itemsS.h.empty()) {
             const BatchQueue Q = queue(b, r, r.itemsS, active);
             const dim3 grid(std::min((int)r.itemsS.h.size(), 2 * b.sms));
-            B_CU(launch(k_batch_ssd_diag, grid, dim3(NT), sizeof(ImgSmem), b.stream, Q, *T), "k_batch_ssd_diag");
+            B_CU(launch(k_batch_ssd_diag, grid, dim3(NT), sizeof(SsdSmem), b.stream, Q, *T), "k_batch_ssd_diag");
         }
     }
     return NGF_OK;

@@ -140,26 +140,35 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
 //   MODE_HESS: tile partials of P^T[2 hbar dT dr^T dr (dT . P p)]       (Eq. hessMult)
 // The transposed grid conversion is completed by k_node_combine.
 //
-// Stages (plane indices relative to the march variable zf):
-//   S0(zf+1): node values of u (and p) interpolated in z to the next plane;
-//   S1(zf)  : warp T and dT (and s = dT . P p) on the front-end region;
-//   S2(zf-1): residual Jacobian row rho_hat (Eqs. rho, hatRho) on the halo-1
+// One barrier per plane.  Every stage of a plane interval reads only what
+// earlier intervals wrote, so the buffer between two stages is a ring one
+// plane deeper than their distance (plane indices relative to the march
+// variable zf):
+//   S0(zf+1): node values of u (and p) interpolated in z to plane zf+1;
+//   S1(zf)  : warp T and dT (and s = dT . P p) on the front-end region
+//             (first in the interval, or last for the Hessian, whose template
+//             gathers then overlap the other warps' stencil work: 2% faster
+//             there, 3-5% slower for the objective and gradient);
+//   S2(zf-2): residual Jacobian row rho_hat (Eqs. rho, hatRho) on the halo-1
 //             region and the products pi_i(k) = rho_hat_i(k) w_i with w = r
 //             (gradient) or w = dr s (Hessian): in-plane ones to shared
 //             memory, pi(0) and pi(+-z) of the owned column in registers;
-//   S3(zf-2): t_j = sum_k pi_{j+k}(-k) over true neighbours (column j of
-//             dr^T), q_hat = qscale dT_j t_j to shared memory;
-//   A(zf-3) : x-reduction of q_hat onto node columns (separable P^T);
-//   B(zf-3) : y-reduction and accumulation into two live node planes; a
+//   S3(zf-3): t_j = sum_k pi_{j+k}(-k) over true neighbours (column j of
+//             dr^T), q_hat = qscale dT_j t_j to shared memory; pi(-z) of
+//             plane zf-2 comes from this interval's S2 of the same column;
+//   A(zf-4) : x-reduction of q_hat onto node columns (separable P^T);
+//   B(zf-5) : y-reduction and accumulation into two live node planes; a
 //             completed node plane is stored as this tile's partial.
-// Two barriers per plane: {S1, A} | {S2, S3, S0, B}.  S3 needs pi(-z) of
-// the next plane from S2 of the same owned column, which the same thread has
-// just computed, so it shares S2's interval.
+// Besides its own column every thread may carry optional work: the
+// front-end ring sits on the last threads, the Jacobian ring on the first,
+// and the A, B and S0 items follow one another from the first thread past
+// the Jacobian ring, so that the threads' loads stay close to one another.
 // ---------------------------------------------------------------------------
-template <int MODE>
+template <int MODE, class SM>
 __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, int bz) {
     NGF_DYNAMIC_SMEM(smraw);
-    ImgSmem& S = *reinterpret_cast<ImgSmem*>(smraw);
+    SM& S = *reinterpret_cast<SM*>(smraw);
+    constexpr int SUBX = SM::kUBX, SUBY = SM::kUBY, SNBX = SM::kNBX, SNBY = SM::kNBY;
     constexpr bool OBJ = (MODE == MODE_OBJ), HESS = (MODE == MODE_HESS);
     constexpr int FH = OBJ ? 1 : 2;  // front-end halo
     constexpr int NVEC = HESS ? 6 : 3;
@@ -209,58 +218,55 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
             S.yr_lo[b] = lo;
             S.yr_hi[b] = hi;
         }
-        for (int i = tid; i < 2 * 3 * NBY * NBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
+        for (int i = tid; i < 2 * 3 * SNBY * SNBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
     }
 
     // ---- per-thread work descriptors, fixed for the whole march
     const int lx0 = tid % TX, ly0 = tid / TX;  // owned column
     const int gx0 = xs + lx0, gy0 = ys + ly0;
     const bool own_ok = (lx0 < txe) && (ly0 < tye);
-    const int box = UXn * UYn;  // S0 items: node columns of the front-end box (<= 2 per thread)
-    int s0_g[2], s0_s[2];
+    constexpr int RING1 = ring_size(FH), RING2 = OBJ ? 0 : ring_size(1);
+    const int box = UXn * UYn;  // S0 items: node columns of the front-end box
+    const int nA = OBJ ? 0 : TY * nbx, nB = OBJ ? 0 : nby * nbx;
+    const int offA = RING2 % NT, offB = (RING2 + nA) % NT, offS = (RING2 + nA + nB) % NT;
+    // S0 items (<= 2 per thread) as (global node column, Uz offset); A items
+    // (ly, bx) and B items (by, bx) packed as row*64 + col
+    int s0_g[2], s0_s[2], a_it[2], b_it[2];
     for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * NT;
+        const int i = (tid + NT - offS) % NT + k * NT;
         if (i < box) {
-            const int by = i / UXn, bx = i - by * UXn;
-            s0_g[k] = (UX0 + bx) + P.n0 * (UY0 + by);
-            s0_s[k] = by * UBX + bx;
+            const int yy = i / UXn, xx = i - yy * UXn;
+            s0_g[k] = (UX0 + xx) + P.n0 * (UY0 + yy);
+            s0_s[k] = yy * SUBX + xx;
         } else {
             s0_g[k] = 0;
             s0_s[k] = -1;
         }
+        const int ia = (tid + NT - offA) % NT + k * NT, ib = (tid + NT - offB) % NT + k * NT;
+        a_it[k] = (ia < nA) ? ((ia / nbx) << 6) + (ia % nbx) : -1;
+        b_it[k] = (ib < nB) ? ((ib / nbx) << 6) + (ib % nbx) : -1;
     }
-    // A items (ly, bx) and B items (by, bx), packed as row*64 + col.  Optional
-    // work is spread over disjoint thread ranges so that both barrier intervals
-    // stay balanced: A from thread 0 while the front-end ring sits on the last
-    // threads; B right after the S0 items while the Jacobian ring sits on the
-    // last threads.
-    int a_it[2], b_it[2];
-    const int b_rot = (tid + NT - (box % NT)) % NT;
-    for (int k = 0; k < 2; ++k) {
-        const int i = tid + k * NT, j = b_rot + k * NT;
-        a_it[k] = (!OBJ && i < TY * nbx) ? ((i / nbx) << 6) + (i % nbx) : -1;
-        b_it[k] = (!OBJ && j < nby * nbx) ? ((j / nbx) << 6) + (j % nbx) : -1;
-    }
-    constexpr int RING1 = ring_size(FH), RING2 = ring_size(1);
     const int plane_n = P.n0 * P.n1;
     __syncthreads();
 
     // register queues of the owned column
-    float dq0[3] = {0.f, 0.f, 0.f}, dq1[3] = {0.f, 0.f, 0.f}, dq2[3] = {0.f, 0.f, 0.f};  // dT at zf, zf-1, zf-2
-    float pm_c = 0.f, p0_c = 0.f, pp_c = 0.f;        // pi(-z), pi(0), pi(+z) of plane zf-1
+    float dq0[3] = {0.f, 0.f, 0.f}, dq1[3] = {0.f, 0.f, 0.f}, dq2[3] = {0.f, 0.f, 0.f},
+          dq3[3] = {0.f, 0.f, 0.f};  // dT of the last four front-end planes
+    float pm_c = 0.f, p0_c = 0.f, pp_c = 0.f;        // pi(-z), pi(0), pi(+z) of plane zf-2
     float p0_prev = 0.f, pp_prev = 0.f, pp_prev2 = 0.f;
     double dacc = 0.0;
     int cur = BZ0;  // lower live node plane of the P^T accumulators
 
     const int zbeg = z0 - FH;
     const int fe_last = OBJ ? z1 : z1 + 1;   // last front-end plane needed
-    const int zend = OBJ ? z1 : z1 + 2;      // B of the last owned plane runs at zf = z1 + 2
+    const int zend = OBJ ? z1 + 1 : z1 + 4;  // S2 (objective) or B of the last owned plane
 
-    // S0: node values of plane zf interpolated in z into Uz
+    // S0: node values of plane zf interpolated in z into Uz[zf & 1]
     auto stage0 = [&](int zf) {
         const int fzz = P.fz[zf];
         const float wzz = P.wz[zf];
         const int pl0 = fzz * plane_n;
+        float* uz = &S.Uz[zf & 1][0][0][0];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (s0_s[k] < 0) continue;
@@ -269,7 +275,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
             for (int c = 0; c < NVEC; ++c) {
                 const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
                 const float a = __ldg(src + o), b = __ldg(src + o + P.znext);
-                (&S.Uz[c][0][0])[s0_s[k]] = fmaf(wzz, b - a, a);
+                uz[c * (SUBY * SUBX) + s0_s[k]] = fmaf(wzz, b - a, a);
             }
         }
     };
@@ -279,16 +285,17 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
         const int li = (ly + 2) * SX2 + (lx + 2);
         const int ax = S.fx2[lx + 2], ay = S.fy2[ly + 2];
         const float wxv = S.wx2[lx + 2], wyv = S.wy2[ly + 2];
+        const int uzs = zf & 1;
         float uh[NVEC];
 #pragma unroll
         for (int c = 0; c < NVEC; ++c) {
-            const float v00 = S.Uz[c][ay][ax], v10 = S.Uz[c][ay][ax + 1];
-            const float v01 = S.Uz[c][ay + 1][ax], v11 = S.Uz[c][ay + 1][ax + 1];
+            const float v00 = S.Uz[uzs][c][ay][ax], v10 = S.Uz[uzs][c][ay][ax + 1];
+            const float v01 = S.Uz[uzs][c][ay + 1][ax], v11 = S.Uz[uzs][c][ay + 1][ax + 1];
             const float a0 = fmaf(wxv, v10 - v00, v00), a1 = fmaf(wxv, v11 - v01, v01);
             uh[c] = fmaf(wyv, a1 - a0, a0);
         }
         const float tw = warp_sample(P, gx, gy, zf, uh[0] * P.ih[0], uh[1] * P.ih[1], uh[2] * P.ih[2], g0, g1, g2);
-        const int slot = zf % 3;
+        const int slot = zf & 3;
         S.R[slot][li] = __ldg(P.R + (gx + P.m0 * (gy + P.m1 * zf)));
         S.Tw[slot][li] = tw;
         if (HESS) S.S[slot][li] = fmaf(g0, uh[NVEC - 3], fmaf(g1, uh[NVEC - 2], g2 * uh[NVEC - 1]));
@@ -297,8 +304,8 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
     auto stage2 = [&](int lx, int ly, int zq, bool owned) {
         const int gx = xs + lx, gy = ys + ly;
         const int li = (ly + 2) * SX2 + (lx + 2);
-        const int sc = zq % 3;
-        const int szm = (zq > 0 ? zq - 1 : zq) % 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) % 3;
+        const int sc = zq & 3;
+        const int szm = (zq > 0 ? zq - 1 : zq) & 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) & 3;
         // clamped neighbours (Eq. boundary_conditions), K order -z,-y,-x,+x,+y,+z
         const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
         const int ym = (gy > 0) ? li - SX2 : li, yp = (gy < P.m1 - 1) ? li + SX2 : li;
@@ -372,69 +379,62 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (b_it[k] < 0) continue;
-            const int by = b_it[k] >> 6, bx = b_it[k] & 63;
+            const int yy = b_it[k] >> 6, xx = b_it[k] & 63;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float& a = S.Acc[pl & 1][c][by][bx];
-                P.partial[((tile * 3 + c) * P.pbz + (pl - BZ0)) * (long long)(P.pby * P.pbx) + by * P.pbx + bx] = a;
+                float& a = S.Acc[pl & 1][c][yy][xx];
+                P.partial[((tile * 3 + c) * P.pbz + (pl - BZ0)) * (long long)(P.pby * P.pbx) + yy * P.pbx + xx] = a;
                 a = 0.f;
             }
         }
     };
 
+    constexpr bool S1_LAST = HESS;
+
     if (zbeg >= 0 && zbeg < P.m2) stage0(zbeg);
     __syncthreads();
 
     for (int zf = zbeg; zf <= zend; ++zf) {
-        // ================= interval 1: S1(zf), A(zf-3)
-        dq2[0] = dq1[0]; dq2[1] = dq1[1]; dq2[2] = dq1[2];
-        dq1[0] = dq0[0]; dq1[1] = dq0[1]; dq1[2] = dq0[2];
-        dq0[0] = dq0[1] = dq0[2] = 0.f;
-        if (zf >= 0 && zf < P.m2 && zf <= fe_last) {
-            if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
-            if (tid >= NT - RING1) {
-                int lx, ly;
-                ring_coord(tid - (NT - RING1), FH, lx, ly);
-                const int gx = xs + lx, gy = ys + ly;
-                float g0, g1, g2;
-                if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage1(lx, ly, zf, g0, g1, g2);
-            }
-        }
-        const int za = zf - 3;
-        if (!OBJ && za >= z0 && za < z1) {  // A: x-reduction of q_hat(za)
+        if (zf + 1 >= 0 && zf + 1 < P.m2 && zf + 1 <= fe_last) stage0(zf + 1);
+        if constexpr (!S1_LAST) {  // ---- S1(zf)
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (a_it[k] < 0) continue;
-                const int ly = a_it[k] >> 6, bx = a_it[k] & 63;
-                float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int lx = S.xr_lo[bx]; lx <= S.xr_hi[bx]; ++lx) {
-                    const float wxl = S.wx2[lx + 2];
-                    const float wx = (S.fxb[lx] == bx) ? 1.f - wxl : wxl;
-                    const float4 q = *reinterpret_cast<const float4*>(S.Q4[ly * TX + lx]);
-                    r.x = fmaf(wx, q.x, r.x);
-                    r.y = fmaf(wx, q.y, r.y);
-                    r.z = fmaf(wx, q.z, r.z);
+            for (int c = 0; c < 3; ++c) {
+                dq3[c] = dq2[c];
+                dq2[c] = dq1[c];
+                dq1[c] = dq0[c];
+                dq0[c] = 0.f;
+            }
+            if (zf >= 0 && zf < P.m2 && zf <= fe_last) {
+                if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
+                if (tid >= NT - RING1) {
+                    int lx, ly;
+                    ring_coord(tid - (NT - RING1), FH, lx, ly);
+                    const int gx = xs + lx, gy = ys + ly;
+                    float g0, g1, g2;
+                    if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage1(lx, ly, zf, g0, g1, g2);
                 }
-                *reinterpret_cast<float4*>(S.Qx4[ly][bx]) = r;
             }
         }
-        __syncthreads();
-        // ================= interval 2: S2(zf-1), S3(zf-2), S0(zf+1), B(zf-3)
-        const int zq = zf - 1;
+        // ---- S2(zf-2)
+        const int zq = zf - 2;
         pm_c = p0_c = pp_c = 0.f;
         if (zq >= 0 && zq < P.m2 && (OBJ ? (zq >= z0 && zq < z1) : (zq >= z0 - 1 && zq <= z1))) {
             if (gx0 < P.m0 && gy0 < P.m1) stage2(lx0, ly0, zq, true);
-            if (!OBJ && tid >= NT - RING2) {
+            if (!OBJ && tid < RING2) {
                 int lx, ly;
-                ring_coord(tid - (NT - RING2), 1, lx, ly);
+                ring_coord(tid, 1, lx, ly);
                 const int gx = xs + lx, gy = ys + ly;
                 if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage2(lx, ly, zq, false);
             }
         }
         if (!OBJ) {
-            const int zo = zf - 2;
-            if (zo >= z0 && zo < z1) {  // S3: column sums of dr^T over true neighbours
+            // ---- S3(zf-3): column sums of dr^T over true neighbours
+            const int zo = zf - 3;
+            if (zo >= z0 && zo < z1) {
                 float t = 0.f;
+                // dT(zo): three planes back before this interval's S1, four after it
+                const float dqo0 = S1_LAST ? dq2[0] : dq3[0], dqo1 = S1_LAST ? dq2[1] : dq3[1],
+                            dqo2 = S1_LAST ? dq2[2] : dq3[2];
                 if (own_ok) {
                     const int l1 = (ly0 + 1) * SX1 + (lx0 + 1);
                     const int pb = zo & 1;
@@ -447,41 +447,81 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
                     if (zo < P.m2 - 1) t += pm_c;
                     t *= P.qscale;
                 }
-                *reinterpret_cast<float4*>(S.Q4[tid]) =
-                    own_ok ? make_float4(dq2[0] * t, dq2[1] * t, dq2[2] * t, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+                *reinterpret_cast<float4*>(S.Q4[zo & 1][tid]) =
+                    own_ok ? make_float4(dqo0 * t, dqo1 * t, dqo2 * t, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
             pp_prev2 = pp_prev;
             pp_prev = pp_c;
             p0_prev = p0_c;
-        }
-        if (zf + 1 >= 0 && zf + 1 < P.m2 && zf + 1 <= fe_last) stage0(zf + 1);
-        if (!OBJ && za >= z0 && za < z1) {  // B: y-reduction and z accumulation of plane za
-            const int fzo = P.fz[za];
-            const float wzo = P.wz[za];
-            if (fzo > cur) {  // node plane `cur` is complete
-                store_plane(cur);
-                cur = fzo;
-            }
+            // ---- A(zf-4): x-reduction of q_hat
+            const int za = zf - 4;
+            if (za >= z0 && za < z1) {
+                const int qs = za & 1;
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                if (b_it[k] < 0) continue;
-                const int by = b_it[k] >> 6, bx = b_it[k] & 63;
-                float q0 = 0.f, q1 = 0.f, q2 = 0.f;
-                for (int ly = S.yr_lo[by]; ly <= S.yr_hi[by]; ++ly) {
-                    const float wyl = S.wy2[ly + 2];
-                    const float wy = (S.fyb[ly] == by) ? 1.f - wyl : wyl;
-                    const float4 q = *reinterpret_cast<const float4*>(S.Qx4[ly][bx]);
-                    q0 = fmaf(wy, q.x, q0);
-                    q1 = fmaf(wy, q.y, q1);
-                    q2 = fmaf(wy, q.z, q2);
+                for (int k = 0; k < 2; ++k) {
+                    if (a_it[k] < 0) continue;
+                    const int ly = a_it[k] >> 6, xx = a_it[k] & 63;
+                    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (int lx = S.xr_lo[xx]; lx <= S.xr_hi[xx]; ++lx) {
+                        const float wxl = S.wx2[lx + 2];
+                        const float wx = (S.fxb[lx] == xx) ? 1.f - wxl : wxl;
+                        const float4 q = *reinterpret_cast<const float4*>(S.Q4[qs][ly * TX + lx]);
+                        r.x = fmaf(wx, q.x, r.x);
+                        r.y = fmaf(wx, q.y, r.y);
+                        r.z = fmaf(wx, q.z, r.z);
+                    }
+                    *reinterpret_cast<float4*>(S.Qx4[qs][ly][xx]) = r;
                 }
-                const int lo = cur & 1, hi = (cur + 1) & 1;
-                S.Acc[lo][0][by][bx] = fmaf(1.f - wzo, q0, S.Acc[lo][0][by][bx]);
-                S.Acc[lo][1][by][bx] = fmaf(1.f - wzo, q1, S.Acc[lo][1][by][bx]);
-                S.Acc[lo][2][by][bx] = fmaf(1.f - wzo, q2, S.Acc[lo][2][by][bx]);
-                S.Acc[hi][0][by][bx] = fmaf(wzo, q0, S.Acc[hi][0][by][bx]);
-                S.Acc[hi][1][by][bx] = fmaf(wzo, q1, S.Acc[hi][1][by][bx]);
-                S.Acc[hi][2][by][bx] = fmaf(wzo, q2, S.Acc[hi][2][by][bx]);
+            }
+            // ---- B(zf-5): y-reduction and z accumulation
+            const int zb = zf - 5;
+            if (zb >= z0 && zb < z1) {
+                const int fzo = P.fz[zb];
+                const float wzo = P.wz[zb];
+                if (fzo > cur) {  // node plane `cur` is complete
+                    store_plane(cur);
+                    cur = fzo;
+                }
+                const int qs = zb & 1;
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    if (b_it[k] < 0) continue;
+                    const int yy = b_it[k] >> 6, xx = b_it[k] & 63;
+                    float q0 = 0.f, q1 = 0.f, q2 = 0.f;
+                    for (int ly = S.yr_lo[yy]; ly <= S.yr_hi[yy]; ++ly) {
+                        const float wyl = S.wy2[ly + 2];
+                        const float wy = (S.fyb[ly] == yy) ? 1.f - wyl : wyl;
+                        const float4 q = *reinterpret_cast<const float4*>(S.Qx4[qs][ly][xx]);
+                        q0 = fmaf(wy, q.x, q0);
+                        q1 = fmaf(wy, q.y, q1);
+                        q2 = fmaf(wy, q.z, q2);
+                    }
+                    const int lo = cur & 1, hi = (cur + 1) & 1;
+                    S.Acc[lo][0][yy][xx] = fmaf(1.f - wzo, q0, S.Acc[lo][0][yy][xx]);
+                    S.Acc[lo][1][yy][xx] = fmaf(1.f - wzo, q1, S.Acc[lo][1][yy][xx]);
+                    S.Acc[lo][2][yy][xx] = fmaf(1.f - wzo, q2, S.Acc[lo][2][yy][xx]);
+                    S.Acc[hi][0][yy][xx] = fmaf(wzo, q0, S.Acc[hi][0][yy][xx]);
+                    S.Acc[hi][1][yy][xx] = fmaf(wzo, q1, S.Acc[hi][1][yy][xx]);
+                    S.Acc[hi][2][yy][xx] = fmaf(wzo, q2, S.Acc[hi][2][yy][xx]);
+                }
+            }
+        }
+        if constexpr (S1_LAST) {  // ---- S1(zf), the same as above
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                dq2[c] = dq1[c];
+                dq1[c] = dq0[c];
+                dq0[c] = 0.f;
+            }
+            if (zf >= 0 && zf < P.m2 && zf <= fe_last) {
+                if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
+                if (tid >= NT - RING1) {
+                    int lx, ly;
+                    ring_coord(tid - (NT - RING1), FH, lx, ly);
+                    const int gx = xs + lx, gy = ys + ly;
+                    float g0, g1, g2;
+                    if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage1(lx, ly, zf, g0, g1, g2);
+                }
             }
         }
         __syncthreads();
@@ -499,13 +539,22 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
 }
 
 __global__ void __launch_bounds__(NT, 2) k_image_obj(const ImgParams P) {
-    image_pass<MODE_OBJ>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+    image_pass<MODE_OBJ, ImgSmemC>(P, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 __global__ void __launch_bounds__(NT, 2) k_image_grad(const ImgParams P) {
-    image_pass<MODE_GRAD>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+    image_pass<MODE_GRAD, ImgSmemC>(P, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 __global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) {
-    image_pass<MODE_HESS>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+    image_pass<MODE_HESS, ImgSmemC>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_image_obj_w(const ImgParams P) {
+    image_pass<MODE_OBJ, ImgSmemW>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_image_grad_w(const ImgParams P) {
+    image_pass<MODE_GRAD, ImgSmemW>(P, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+__global__ void __launch_bounds__(NT, 2) k_image_hess_w(const ImgParams P) {
+    image_pass<MODE_HESS, ImgSmemW>(P, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -521,7 +570,7 @@ __global__ void __launch_bounds__(NT, 2) k_image_hess(const ImgParams P) {
 template <int MODE>
 __device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, int bz_) {
     NGF_DYNAMIC_SMEM(smraw);
-    ImgSmem& S = *reinterpret_cast<ImgSmem*>(smraw);
+    SsdSmem& S = *reinterpret_cast<SsdSmem*>(smraw);
     constexpr bool OBJ = (MODE == MODE_OBJ), HESS = (MODE == MODE_HESS), DIAG = (MODE == MODE_SSD_DIAG);
     constexpr bool WANT_D = (MODE == MODE_OBJ || MODE == MODE_GRAD);  // the gradient pass also returns D
     constexpr int NVEC = HESS ? 6 : 3;
@@ -1472,7 +1521,9 @@ __device__ __forceinline__ void queue_release(const BatchQueue& Q) {
     }
 }
 
-template <int KIND>  // 0..2: image pass mode (NGF or SSD per pair), 3/4: NGF diagonal (span 3/4), 5: SSD diagonal
+// KIND 0..2: image pass mode (NGF or SSD per pair), 3/4: NGF diagonal (span 3/4), 5: SSD diagonal;
+// SM: shared-memory layout of the NGF image pass
+template <int KIND, class SM = ImgSmemC>
 __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q, const BatchImgTable& T) {
     __shared__ int4 item;
     for (;;) {
@@ -1489,7 +1540,7 @@ __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q, const Batc
             else if (KIND == 4) diag_pass<4>(Ps, it.y, it.z, it.w);
             else if (KIND == 5) ssd_pass<MODE_SSD_DIAG>(Ps, it.y, it.z, it.w);
             else if (T.ssd[it.x - Q.pair0]) ssd_pass<KIND>(Ps, it.y, it.z, it.w);
-            else image_pass<KIND>(Ps, it.y, it.z, it.w);
+            else image_pass<KIND, SM>(Ps, it.y, it.z, it.w);
         }
         __syncthreads();
     }
@@ -1504,6 +1555,15 @@ __global__ void __launch_bounds__(NT, 2) k_batch_image_grad(const BatchQueue Q, 
 }
 __global__ void __launch_bounds__(NT, 2) k_batch_image_hess(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
     batch_image_loop<MODE_HESS>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 2) k_batch_image_obj_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<MODE_OBJ, ImgSmemW>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 2) k_batch_image_grad_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<MODE_GRAD, ImgSmemW>(Q, T);
+}
+__global__ void __launch_bounds__(NT, 2) k_batch_image_hess_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
+    batch_image_loop<MODE_HESS, ImgSmemW>(Q, T);
 }
 __global__ void __launch_bounds__(NT, 1) k_batch_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
     batch_image_loop<3>(Q, T);

@@ -72,11 +72,8 @@ struct ImgParams {
     double* dout;               // D (hbar * sum(1 - r^2))
 };
 
-struct ImgSmem {
-    float R[3][R2N];
-    float Tw[3][R2N];
-    float S[3][R2N];
-    float Pi[2][4][R1N];        // pi(-x), pi(+x), pi(-y), pi(+y) of the halo-1 region
+// Shared memory of the SSD pass (no halo, no neighbour stencil)
+struct SsdSmem {
     float Uz[6][UBY][UBX];      // u (and p) interpolated to the current plane in z
     alignas(16) float Q4[R0N][4];       // q_hat of the owned columns (3 components + pad)
     alignas(16) float Qx4[TY][NBX][4];  // q_hat reduced onto node columns in x
@@ -87,6 +84,38 @@ struct ImgSmem {
     int xr_lo[NBX], xr_hi[NBX], yr_lo[NBY], yr_hi[NBY];
     double red[NT];
 };
+
+// Shared memory of the NGF image pass (one barrier per plane, so every ring
+// is one plane deeper than the stages' distance): R, Tw, s in four plane
+// slots, the in-plane products and the node-plane buffers in two.  The node
+// boxes are compile-time sizes: the compact layout holds grids with two or
+// more voxels per cell in x and y (two CTAs per SM), the wide one any ratio.
+template <int UBX_, int UBY_, int NBX_, int NBY_>
+struct ImgSmemT {
+    static constexpr int kUBX = UBX_, kUBY = UBY_, kNBX = NBX_, kNBY = NBY_;
+    float R[4][R2N];
+    float Tw[4][R2N];
+    float S[4][R2N];
+    union {
+        float Pi[2][4][R1N];    // pi(-x), pi(+x), pi(-y), pi(+y) of the halo-1 region
+        double red[NT];         // reductions after the march
+    };
+    float Uz[2][6][UBY_][UBX_];           // u (and p) interpolated to a plane in z
+    alignas(16) float Q4[2][R0N][4];      // q_hat of the owned columns (3 components + pad)
+    alignas(16) float Qx4[2][TY][NBX_][4];  // q_hat reduced onto node columns in x
+    float Acc[2][3][NBY_][NBX_];          // node-plane accumulators of P^T (two live planes)
+    float wx2[SX2], wy2[SY2];
+    int fx2[SX2], fy2[SY2];     // node floor relative to the Uz box
+    int fxb[TX], fyb[TY];       // node floor relative to the partial box
+    int xr_lo[NBX_], xr_hi[NBX_], yr_lo[NBY_], yr_hi[NBY_];
+};
+// >= 2 voxels per cell: the 36 x 20 front-end region spans <= 20 x 12 nodes,
+// the 32 x 16 owned columns <= 18 x 10 (checked per plan on the host)
+using ImgSmemC = ImgSmemT<20, 12, 18, 10>;
+using ImgSmemW = ImgSmemT<UBX, UBY, NBX, NBY>;
+// planes a CTA marches beyond its z-chunk: two front-end halo planes and the
+// pipeline's drain from S1 to B
+constexpr int IMG_FILL = 7;
 
 struct DiagSmem {
     float R[3][R1N];
@@ -222,6 +251,10 @@ __host__ __device__ constexpr int ring_size(int halo) { return 2 * halo * (TX + 
 __global__ void k_image_obj(const ImgParams P);   // D only
 __global__ void k_image_grad(const ImgParams P);  // D and gradient tile partials
 __global__ void k_image_hess(const ImgParams P);  // Hessian-vector tile partials
+// the same passes with the wide shared-memory layout (< 2 voxels per cell)
+__global__ void k_image_obj_w(const ImgParams P);
+__global__ void k_image_grad_w(const ImgParams P);
+__global__ void k_image_hess_w(const ImgParams P);
 __global__ void k_diag(const ImgParams P);        // Jacobi-diagonal tile partials (>= 2 voxels per cell)
 __global__ void k_diag4(const ImgParams P);       // same, any voxels-per-cell ratio
 // SSD distance (identity residual Jacobian): D, gradient, Hessian-vector and
@@ -291,6 +324,9 @@ struct BatchSegs {
 __global__ void k_batch_image_obj(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_image_grad(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_image_hess(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_image_obj_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_image_grad_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
+__global__ void k_batch_image_hess_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag4(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_ssd_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T);

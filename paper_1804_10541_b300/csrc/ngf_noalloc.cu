@@ -114,8 +114,10 @@ ngf_status scratch_on_device(unsigned char** out) {
         unsigned char* ptr = nullptr;
         e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_check(nullptr, e, "cudaGetSymbolAddress(no-allocation scratch)");
-        e = cudaFuncSetAttribute(k_image_obj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmem));
+        e = cudaFuncSetAttribute(k_image_obj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmemC));
         if (e != cudaSuccess) return cuda_check(nullptr, e, "cudaFuncSetAttribute(k_image_obj)");
+        e = cudaFuncSetAttribute(k_image_obj_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ImgSmemW));
+        if (e != cudaSuccess) return cuda_check(nullptr, e, "cudaFuncSetAttribute(k_image_obj_w)");
         g_na_addr[dev] = ptr;
     }
     *out = g_na_addr[dev];
@@ -217,7 +219,11 @@ extern "C" ngf_status ngf_objective_noalloc(const ngf_level_desc* d, const float
     P.dpart = part;
     P.dcount = count;
     P.dout = dev_DS;
-    e = launch(k_image_obj, grid, dim3(NT), sizeof(ImgSmem), stream, P);
+    // two or more voxels per cell in x and y bound the front-end node box by
+    // the compact layout's (the objective pass uses no owned node box)
+    const bool compact = 2 * (d->n[0] - 1) <= d->m[0] && 2 * (d->n[1] - 1) <= d->m[1];
+    e = compact ? launch(k_image_obj, grid, dim3(NT), sizeof(ImgSmemC), stream, P)
+                : launch(k_image_obj_w, grid, dim3(NT), sizeof(ImgSmemW), stream, P);
     if (e != cudaSuccess) return cuda_check(nullptr, e, "k_image_obj");
 
     NodeGeom G;

@@ -41,6 +41,7 @@ struct Plan {
     double hbar = 0, hbary = 0, hy[3]{};
     int zc = 0;
     bool diag_span3 = false;    // diagonal: three-node span (>= 2 voxels per cell on every axis)
+    bool img_wide = false;      // image pass: wide shared-memory layout (< 2 voxels per cell in x or y)
     int dsteps[2] = {0, 0};     // diagonal: shuffle steps covering the longest run of equal x
                                 // floors in the first x tile and in the others
     int img_blocks = 0, diag_blocks = 0, node_blocks = 0, node1_blocks = 0;
