@@ -209,12 +209,12 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     b->t_img.assign(np, ImgParams{});
     B_CU(b->t_lap.alloc(np, stream), "allocate batch tables");
     B_CU(b->t_comb.alloc(np, stream), "allocate batch tables");
-    const int csmem = (int)batch_img_smem(false), wsmem = (int)batch_img_smem(true), dsmem = (int)sizeof(DiagSmem);
+    const int csmem = (int)batch_img_smem(false), wsmem = (int)batch_img_smem(true), dsmem = (int)sizeof(DiagSmemT<4>), dsmem3 = (int)sizeof(DiagSmemT<3>);
     for (auto kern : {k_batch_image_obj, k_batch_image_grad, k_batch_image_hess})
         B_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, csmem), "smem attr");
     for (auto kern : {k_batch_image_obj_w, k_batch_image_grad_w, k_batch_image_hess_w})
         B_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem), "smem attr");
-    B_CU(cudaFuncSetAttribute(k_batch_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem), "smem attr");
+    B_CU(cudaFuncSetAttribute(k_batch_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem3), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_ssd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsdSmem)),
          "smem attr");
@@ -275,13 +275,13 @@ static ngf_status launch_diag(const Batch& b, const std::vector<ImgParams>& tab,
         fill_table(b, r, tab, *T);
         if (!r.items3.h.empty()) {
             const BatchQueue Q = queue(b, r, r.items3, active);
-            const dim3 grid(std::min((int)r.items3.h.size(), b.sms));
-            B_CU(launch(k_batch_diag, grid, dim3(NT), sizeof(DiagSmem), b.stream, Q, *T), "k_batch_diag");
+            const dim3 grid(std::min((int)r.items3.h.size(), 2 * b.sms));
+            B_CU(launch(k_batch_diag, grid, dim3(NT), sizeof(DiagSmemT<3>), b.stream, Q, *T), "k_batch_diag");
         }
         if (!r.items4.h.empty()) {
             const BatchQueue Q = queue(b, r, r.items4, active);
             const dim3 grid(std::min((int)r.items4.h.size(), b.sms));
-            B_CU(launch(k_batch_diag4, grid, dim3(NT), sizeof(DiagSmem), b.stream, Q, *T), "k_batch_diag4");
+            B_CU(launch(k_batch_diag4, grid, dim3(NT), sizeof(DiagSmemT<4>), b.stream, Q, *T), "k_batch_diag4");
         }
         if (!r.itemsS.h.empty()) {
             const BatchQueue Q = queue(b, r, r.itemsS, active);

@@ -36,7 +36,6 @@ constexpr int DBX = TX + 3, DBY = TY + 3;       // node box of the halo-1 region
 __host__ __device__ constexpr int diag_pxw(int span) { return span == 3 ? 20 : 36; }
 // four live node planes x 3 components x span y-nodes x window, per row
 __host__ __device__ constexpr int diag_window(int span) { return 4 * 3 * span * diag_pxw(span); }
-constexpr int DIAG_ACC = TY * diag_window(4);
 
 enum Mode { MODE_OBJ = 0, MODE_GRAD = 1, MODE_HESS = 2 };
 
@@ -117,12 +116,15 @@ using ImgSmemW = ImgSmemT<UBX, UBY, NBX, NBY>;
 // pipeline's drain from S1 to B
 constexpr int IMG_FILL = 7;
 
-struct DiagSmem {
+// Shared memory of the diagonal pass; the windows are sized for the span, so
+// the three-node form (92.7 KB) runs two CTAs per SM
+template <int SPAN>
+struct DiagSmemT {
     float R[3][R1N];
     float Tw[3][R1N];
     float dT[3][3][R1N];        // [plane slot][component][column]
     float Uz[3][UBY][UBX];
-    float Acc[DIAG_ACC];        // one private node window per warp row (see diag_pass)
+    float Acc[TY * diag_window(SPAN)];  // one private node window per warp row (see diag_pass)
     float wx1[SX1], wy1[SY1];
     int fx1[SX1], fy1[SY1];     // node floor relative to the Uz (= partial) box
 };
