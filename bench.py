@@ -115,8 +115,9 @@ class ClockSampler:
 
 def image_pass_source_hash():
     """sha256 of the Hessian image pass's source (kernel body, its helpers and
-    the parameter and shared-memory layouts), to tell whether a stored DRAM
-    traffic figure still describes the kernel that runs."""
+    the tile, parameter and shared-memory layouts; not the diagonal pass's),
+    to tell whether a stored DRAM traffic figure still describes the kernel
+    that runs."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1804_10541_b300", "csrc")
     with open(os.path.join(csrc, "ngf_kernels.cu")) as f:
@@ -124,9 +125,9 @@ def image_pass_source_hash():
     end = cu.index("image_pass<MODE_HESS, ImgSmemC>(P, blockIdx.x, blockIdx.y, blockIdx.z);")
     with open(os.path.join(csrc, "ngf_kernels.cuh")) as f:
         cuh = f.read()
-    a = cuh.index("constexpr int TX")
-    b = cuh.index("constexpr int IMG_FILL")
-    return hashlib.sha256((cu[:end] + cuh[a:b]).encode()).hexdigest()
+    tiles = cuh[cuh.index("constexpr int TX"):cuh.index("// x-node window of one warp row in the diagonal kernel")]
+    layouts = cuh[cuh.index("enum Mode"):cuh.index("constexpr int IMG_FILL")]
+    return hashlib.sha256((cu[:end] + tiles + layouts).encode()).hexdigest()
 
 
 def stored_traffic(workload):
