@@ -244,6 +244,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
                               (size_t)blockIdx.y * a.nch * 27 * b_bytes;  // this slice's stages
     uint32_t tmem = 0;
     bool failed = false;
+    __syncthreads();  // barriers and flags initialised before the producer's first copy
 
     for (int c = 0; c < a.nch; ++c) {
         if (c > 0) {
@@ -251,6 +252,28 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
             const bool ok = mbar_wait(smem_addr(chunk_bar), (uint32_t)((c - 1) & 1));
             if (__syncthreads_or(!ok || flags[0] != 0)) { failed = true; break; }
         }
+        // weight producer, first part: when all of the chunk's stages fit the
+        // buffers, they go out before the brick is staged (they depend on
+        // nothing and their buffers are free: the previous chunk's MMAs have
+        // all completed), so their copies overlap the staging (5-10% faster
+        // on the small layers; with more stages than buffers, issuing the
+        // first ones early measured 10% slower); the rest follow the barrier,
+        // paced by the MMA thread's releases
+        const int pre_end = spc * c + (spc <= nbuf ? spc : 0);
+        auto produce = [&](int s0, int s1) {
+            for (int s = s0; s < s1; ++s) {
+                const int buf = s % nbuf;
+                if (s >= nbuf && !mbar_wait(smem_addr(&empty[buf]), (uint32_t)(((s - nbuf) / nbuf) & 1))) {
+                    atomicExch(&flags[0], 1);
+                    break;
+                }
+                if (*(volatile int*)&flags[0]) break;
+                mbar_expect_tx(smem_addr(&full[buf]), st_bytes);
+                bulk_copy(sB + buf * st_bytes, wp + (size_t)s * st_bytes, st_bytes, smem_addr(&full[buf]));
+                flags[1] = s + 1;
+            }
+        };
+        if (tid == 32) produce(spc * c, pre_end);
         // the brick of chunk c: one 16-byte copy per (voxel, channel group),
         // channel group fastest across lanes (contiguous global reads), zero
         // outside
@@ -271,18 +294,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         tmem = *tmem_slot;
 
         if (tid == 32) {
-            // weight producer: stages s = 27c .. 27c + 26
-            for (int s = spc * c; s < spc * c + spc; ++s) {
-                const int buf = s % nbuf;
-                if (s >= nbuf && !mbar_wait(smem_addr(&empty[buf]), (uint32_t)(((s - nbuf) / nbuf) & 1))) {
-                    atomicExch(&flags[0], 1);
-                    break;
-                }
-                if (*(volatile int*)&flags[0]) break;
-                mbar_expect_tx(smem_addr(&full[buf]), st_bytes);
-                bulk_copy(sB + buf * st_bytes, wp + (size_t)s * st_bytes, st_bytes, smem_addr(&full[buf]));
-                flags[1] = s + 1;
-            }
+            produce(pre_end, spc * c + spc);  // weight producer, second part
         } else if (tid == 0) {
             // MMA issuer
             const uint32_t idesc = instr_desc(CONV_M, ns);
