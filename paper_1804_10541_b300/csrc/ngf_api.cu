@@ -348,26 +348,13 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     NGF_CU(p, cudaMemcpyAsync(p->ftab, fh.data(), tl * sizeof(int), cudaMemcpyHostToDevice, p->stream), "copy tables");
     NGF_CU(p, cudaMemcpyAsync(p->wtab, wh.data(), tl * sizeof(float), cudaMemcpyHostToDevice, p->stream), "copy tables");
 
-    // image-pass layout: the compact one when every tile's front-end node box
-    // and owned node box fit it (two or more voxels per cell in x and y)
-    {
-        int ux = 0, uy = 0, bxm = 0, bym = 0;
-        for (int xs = 0; xs < p->m[0]; xs += TX) {
-            ux = std::max(ux, f[0][std::min(xs + TX + 1, p->m[0] - 1)] + 2 - f[0][std::max(xs - 2, 0)]);
-            bxm = std::max(bxm, f[0][std::min(xs + TX, p->m[0]) - 1] + 2 - f[0][xs]);
-        }
-        for (int ys = 0; ys < p->m[1]; ys += TY) {
-            uy = std::max(uy, f[1][std::min(ys + TY + 1, p->m[1] - 1)] + 2 - f[1][std::max(ys - 2, 0)]);
-            bym = std::max(bym, f[1][std::min(ys + TY, p->m[1]) - 1] + 2 - f[1][ys]);
-        }
-        p->img_wide = ux > ImgSmemC::kUBX || uy > ImgSmemC::kUBY || bxm > ImgSmemC::kNBX || bym > ImgSmemC::kNBY;
-        if (ux > UBX || uy > UBY || bxm > NBX || bym > NBY)
-            return set_error(p, NGF_EBOUNDS, "internal: tile node box exceeds the image pass's shared-memory box");
-    }
     NGF_TRY(build_geometry(p, 0, f, p->g0));
     NGF_TRY(build_geometry(p, 1, f, p->g1));
     if (p->g0.pbx > NBX || p->g0.pby > NBY || p->g1.pbx > DBX || p->g1.pby > DBY)
         return set_error(p, NGF_EBOUNDS, "internal: tile node box exceeds the kernel's shared-memory box");
+    // image-pass layout: the compact one when every tile's halo-1 node box
+    // fits it (always with two or more voxels per cell in x and y)
+    p->img_wide = p->g1.pbx > ImgSmemC::kNBX || p->g1.pby > ImgSmemC::kNBY;
     const long long pf = std::max(p->g0.partial_floats(), p->g1.partial_floats());
     NGF_CU(p, dev_alloc((void**)&p->partial, pf * sizeof(float), p->stream), "allocate partials");
     NGF_CU(p, dev_alloc((void**)&p->L, 3 * p->N * sizeof(float), p->stream), "allocate L");
@@ -531,7 +518,7 @@ ngf_status objective_impl(Plan* p, const float* R, const float* T, const float* 
 
 ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u, float* g, double* dD,
                          double* dS) {
-    ImgParams P = img_params(p, R, T, u, nullptr, MODE_GRAD, p->g0, dD);
+    ImgParams P = img_params(p, R, T, u, nullptr, MODE_GRAD, img_geom(p), dD);
     NGF_CU(p, prof_mark(p, NGF_K_GRADIENT), "cudaEventRecord");
     NGF_CU(p, launch(img_kernel(p, MODE_GRAD), img_grid(p->g0), dim3(NT), img_smem(p), p->stream, P),
            "k_image_grad");
@@ -539,7 +526,7 @@ ngf_status gradient_impl(Plan* p, const float* R, const float* T, const float* u
     NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), u, p->L, p->dpart,
                      p->dcount, dS, p->hbary),
            "k_lap");
-    CombineParams C = combine_params(p, p->g0, g, p->L, nullptr, nullptr, nullptr);
+    CombineParams C = combine_params(p, img_geom(p), g, p->L, nullptr, nullptr, nullptr);
     NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
 }
@@ -549,12 +536,12 @@ ngf_status hessvec_impl(Plan* p, const float* R, const float* T, const float* u,
     NGF_CU(p, launch(k_lap, dim3(p->node1_blocks), dim3(NT), 0, p->stream, node_geom(p), pv, p->L, p->dpart,
                      p->dcount, (double*)nullptr, 0.0),
            "k_lap");
-    ImgParams P = img_params(p, R, T, u, pv, MODE_HESS, p->g0, nullptr);
+    ImgParams P = img_params(p, R, T, u, pv, MODE_HESS, img_geom(p), nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
     NGF_CU(p, launch(img_kernel(p, MODE_HESS), img_grid(p->g0), dim3(NT), img_smem(p), p->stream, P),
            "k_image_hess");
     NGF_CU(p, prof_mark(p, NGF_K_HESSVEC), "cudaEventRecord");
-    CombineParams C = combine_params(p, p->g0, q, p->L, nullptr, dotw, dout);
+    CombineParams C = combine_params(p, img_geom(p), q, p->L, nullptr, dotw, dout);
     NGF_CU(p, launch(k_node_combine, dim3(p->node1_blocks), dim3(NT), 0, p->stream, C), "k_node_combine");
     return NGF_OK;
 }

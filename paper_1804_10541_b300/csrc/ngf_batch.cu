@@ -326,8 +326,8 @@ static ngf_status batch_hessvec(Batch& b, const float* const* R, const float* co
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
         b.t_lap.h[k] = lap_args(p, pv[k], nullptr);
-        b.t_img[k] = img_params(p, R[k], T[k], u[k], pv[k], MODE_HESS, p->g0, nullptr);
-        b.t_comb.h[k] = combine_params(p, p->g0, q[k], p->L, nullptr, nullptr, nullptr);
+        b.t_img[k] = img_params(p, R[k], T[k], u[k], pv[k], MODE_HESS, img_geom(p), nullptr);
+        b.t_comb.h[k] = combine_params(p, img_geom(p), q[k], p->L, nullptr, nullptr, nullptr);
     }
     B_CU(b.t_lap.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
@@ -458,9 +458,9 @@ ngf_status ngf_batch_gradient(ngf_batch* batch, const float* const* R, const flo
                          {(const void* const*)grad, "grad"}}));
     for (int k = 0; k < b.np; ++k) {
         const Plan* p = b.plan(k);
-        b.t_img[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_GRAD, p->g0, p->dsc);
+        b.t_img[k] = img_params(p, R[k], T[k], u[k], nullptr, MODE_GRAD, img_geom(p), p->dsc);
         b.t_lap.h[k] = lap_args(p, u[k], p->dsc + 1);
-        b.t_comb.h[k] = combine_params(p, p->g0, grad[k], p->L, nullptr, nullptr, nullptr);
+        b.t_comb.h[k] = combine_params(p, img_geom(p), grad[k], p->L, nullptr, nullptr, nullptr);
     }
     B_CU(b.t_lap.upload(), "upload tables");
     B_CU(b.t_comb.upload(), "upload tables");
@@ -702,16 +702,16 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             const float *Rk = Rl[l][k], *Tk = Tl[l][k];
             tb.obj_u[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_OBJ, p->g0, sk);
             tb.obj_ut[k] = img_params(p, Rk, Tk, seg(ut, k), nullptr, MODE_OBJ, p->g0, sk);
-            tb.grad[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_GRAD, p->g0, sk);
+            tb.grad[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_GRAD, img_geom(p), sk);
             const Geometry& gd = is_ssd(p) ? p->g0 : p->g1;
             tb.diag[k] = img_params(p, Rk, Tk, seg(u, k), nullptr, MODE_HESS, gd, nullptr);
-            tb.hess[k] = img_params(p, Rk, Tk, seg(u, k), seg(d, k), MODE_HESS, p->g0, nullptr);
+            tb.hess[k] = img_params(p, Rk, Tk, seg(u, k), seg(d, k), MODE_HESS, img_geom(p), nullptr);
             tb.lap_u.h[k] = lap_args(p, seg(u, k), sk + 1);
             tb.lap_ut.h[k] = lap_args(p, seg(ut, k), sk + 1);
             tb.lap_d.h[k] = lap_args(p, seg(d, k), nullptr);
-            tb.comb_grad.h[k] = combine_params(p, p->g0, seg(g, k), p->L, nullptr, nullptr, nullptr);
+            tb.comb_grad.h[k] = combine_params(p, img_geom(p), seg(g, k), p->L, nullptr, nullptr, nullptr);
             tb.comb_diag.h[k] = combine_params(p, gd, seg(dg, k), nullptr, p->ctab, nullptr, nullptr);
-            tb.comb_hess.h[k] = combine_params(p, p->g0, seg(q, k), p->L, nullptr, seg(d, k), sk + 8 + PS_DQ);
+            tb.comb_hess.h[k] = combine_params(p, img_geom(p), seg(q, k), p->L, nullptr, seg(d, k), sk + 8 + PS_DQ);
             PcgParams& P = tb.pcg.h[k];
             P.n = n;
             P.x = seg(x, k);

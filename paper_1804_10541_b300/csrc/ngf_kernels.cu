@@ -140,104 +140,125 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
 //   MODE_HESS: tile partials of P^T[2 hbar dT dr^T dr (dT . P p)]       (Eq. hessMult)
 // The transposed grid conversion is completed by k_node_combine.
 //
+// A CTA owns the residual rows i of its TX x TY column tile and z-chunk: it
+// forms rho_hat_i and w_i = r_i (gradient) or (dr s)_i (Hessian) for those
+// rows only, and scatters each row's products pi_i(k) = rho_hat_i(k) w_i to
+// the columns j = i + k of dr^T, which lie in the tile or on the face ring
+// just outside it (and on the planes just below and above the chunk).  The
+// tile's partial holds q_hat_j = qscale dT_j t_j for all those columns, with
+// t_j the sum over the tile's own rows; the neighbouring tiles add the rest
+// of t_j through their own partials, since P^T is linear.  So the front end
+// (warp, dT, s) runs on the halo-1 region only (own columns and face ring,
+// no corners) and no residual Jacobian row is evaluated twice.
+//
 // One barrier per plane.  Every stage of a plane interval reads only what
 // earlier intervals wrote, so the buffer between two stages is a ring one
 // plane deeper than their distance (plane indices relative to the march
 // variable zf):
 //   S0(zf+1): node values of u (and p) interpolated in z to plane zf+1;
-//   S1(zf)  : warp T and dT (and s = dT . P p) on the front-end region
-//             (first in the interval, or last for the Hessian, whose template
-//             gathers then overlap the other warps' stencil work: 2% faster
-//             there, 3-5% slower for the objective and gradient);
-//   S2(zf-2): residual Jacobian row rho_hat (Eqs. rho, hatRho) on the halo-1
-//             region and the products pi_i(k) = rho_hat_i(k) w_i with w = r
-//             (gradient) or w = dr s (Hessian): in-plane ones to shared
-//             memory, pi(0) and pi(+-z) of the owned column in registers;
-//   S3(zf-3): t_j = sum_k pi_{j+k}(-k) over true neighbours (column j of
-//             dr^T), q_hat = qscale dT_j t_j to shared memory; pi(-z) of
-//             plane zf-2 comes from this interval's S2 of the same column;
+//   S1(zf)  : warp T and dT (and s = dT . P p) on the own columns and the
+//             face ring (first in the interval, or last for the Hessian,
+//             whose template gathers then overlap the other warps' stencil
+//             work);
+//   S2(zf-2): residual Jacobian row rho_hat (Eqs. rho, hatRho) of the own
+//             rows and the products pi_i(k): in-plane ones to shared memory,
+//             pi(0) and pi(+-z) in registers;
+//   S3(zf-3): t_j = sum_k pi_{j+k}(-k) over the tile's own rows that are
+//             true neighbours of j (column j of dr^T), q_hat = qscale dT_j t_j
+//             on the halo-1 region; pi(-z) of plane zf-2 comes from this
+//             interval's S2 of the same column;
 //   A(zf-4) : x-reduction of q_hat onto node columns (separable P^T);
 //   B(zf-5) : y-reduction and accumulation into two live node planes; a
 //             completed node plane is stored as this tile's partial.
-// Besides its own column every thread may carry optional work: the
-// front-end ring sits on the last threads, the Jacobian ring on the first,
-// and the A, B and S0 items follow one another from the first thread past
-// the Jacobian ring, so that the threads' loads stay close to one another.
+// Besides its own column a thread may carry optional work: the front end of
+// the face ring sits on the last RINGF threads, the ring's S3 on the first
+// RINGF, and the A, B and S0 items follow one another from thread RINGF on.
 // ---------------------------------------------------------------------------
+// position of face-ring column k of the halo-1 region: the row below and
+// above the tile, then the column left and right of it
+__device__ __forceinline__ void ring_face(int k, int& lx, int& ly) {
+    if (k < 2 * TX) {
+        lx = k & (TX - 1);
+        ly = (k < TX) ? -1 : TY;
+    } else {
+        k -= 2 * TX;
+        ly = k % TY;
+        lx = (k < TY) ? -1 : TX;
+    }
+}
+
 template <int MODE, class SM>
 __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, int bz) {
     NGF_DYNAMIC_SMEM(smraw);
     SM& S = *reinterpret_cast<SM*>(smraw);
-    constexpr int SUBX = SM::kUBX, SUBY = SM::kUBY, SNBX = SM::kNBX, SNBY = SM::kNBY;
+    constexpr int SNBX = SM::kNBX, SNBY = SM::kNBY;
     constexpr bool OBJ = (MODE == MODE_OBJ), HESS = (MODE == MODE_HESS);
-    constexpr int FH = OBJ ? 1 : 2;  // front-end halo
     constexpr int NVEC = HESS ? 6 : 3;
     const int tid = threadIdx.x;
     const int xs = bx * TX, ys = by * TY;
     const int z0 = bz * P.zc, z1 = min(P.m2, z0 + P.zc);
     const int txe = min(TX, P.m0 - xs), tye = min(TY, P.m1 - ys);
 
-    // node box of the front-end region (z-interpolated node planes)
-    const int UX0 = P.fx[max(xs - 2, 0)], UY0 = P.fy[max(ys - 2, 0)];
-    const int UXn = P.fx[min(xs + TX + 1, P.m0 - 1)] + 1 - UX0 + 1;
-    const int UYn = P.fy[min(ys + TY + 1, P.m1 - 1)] + 1 - UY0 + 1;
-    // node box of the owned columns (tile partials)
-    const int BX0 = P.fx[xs], BY0 = P.fy[ys], BZ0 = P.fz[z0];
-    const int nbx = P.fx[xs + txe - 1] + 1 - BX0 + 1;
-    const int nby = P.fy[ys + tye - 1] + 1 - BY0 + 1;
+    // node box of the halo-1 region: z-interpolated node planes and partials
+    const int BX0 = P.fx[max(xs - 1, 0)], BY0 = P.fy[max(ys - 1, 0)], BZ0 = P.fz[max(z0 - 1, 0)];
+    const int nbx = P.fx[min(xs + TX, P.m0 - 1)] + 1 - BX0 + 1;
+    const int nby = P.fy[min(ys + TY, P.m1 - 1)] + 1 - BY0 + 1;
     const long long tile = ((long long)bz * P.nty + by) * P.ntx + bx;
 
-    for (int i = tid; i < SX2; i += NT) {
-        const int gx = min(max(xs - 2 + i, 0), P.m0 - 1);
-        S.fx2[i] = P.fx[gx] - UX0;
-        S.wx2[i] = P.wx[gx];
+    for (int i = tid; i < SX1; i += NT) {
+        const int gx = min(max(xs - 1 + i, 0), P.m0 - 1);
+        S.fx1[i] = P.fx[gx] - BX0;
+        S.wx1[i] = P.wx[gx];
     }
-    for (int i = tid; i < SY2; i += NT) {
-        const int gy = min(max(ys - 2 + i, 0), P.m1 - 1);
-        S.fy2[i] = P.fy[gy] - UY0;
-        S.wy2[i] = P.wy[gy];
+    for (int i = tid; i < SY1; i += NT) {
+        const int gy = min(max(ys - 1 + i, 0), P.m1 - 1);
+        S.fy1[i] = P.fy[gy] - BY0;
+        S.wy1[i] = P.wy[gy];
     }
     if (!OBJ) {
-        for (int i = tid; i < TX; i += NT) S.fxb[i] = P.fx[min(xs + i, P.m0 - 1)] - BX0;
-        for (int i = tid; i < TY; i += NT) S.fyb[i] = P.fy[min(ys + i, P.m1 - 1)] - BY0;
+        // halo-1 columns (in the image) reduced onto each node column / row
         for (int b = tid; b < nbx; b += NT) {
-            int lo = TX, hi = -1;
-            for (int lx = 0; lx < txe; ++lx) {
-                const int f = P.fx[xs + lx] - BX0;
-                if (f == b || f == b - 1) { lo = min(lo, lx); hi = max(hi, lx); }
+            int lo = SX1, hi = -1;
+            for (int l = 0; l < SX1; ++l) {
+                const int gx = xs - 1 + l;
+                if (gx < 0 || gx >= P.m0) continue;
+                const int f = P.fx[gx] - BX0;
+                if (f == b || f == b - 1) { lo = min(lo, l); hi = max(hi, l); }
             }
             S.xr_lo[b] = lo;
             S.xr_hi[b] = hi;
         }
         for (int b = tid; b < nby; b += NT) {
-            int lo = TY, hi = -1;
-            for (int ly = 0; ly < tye; ++ly) {
-                const int f = P.fy[ys + ly] - BY0;
-                if (f == b || f == b - 1) { lo = min(lo, ly); hi = max(hi, ly); }
+            int lo = SY1, hi = -1;
+            for (int l = 0; l < SY1; ++l) {
+                const int gy = ys - 1 + l;
+                if (gy < 0 || gy >= P.m1) continue;
+                const int f = P.fy[gy] - BY0;
+                if (f == b || f == b - 1) { lo = min(lo, l); hi = max(hi, l); }
             }
             S.yr_lo[b] = lo;
             S.yr_hi[b] = hi;
         }
         for (int i = tid; i < 2 * 3 * SNBY * SNBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
+        for (int i = tid; i < 2 * R1N * 4; i += NT) (&S.Q4[0][0][0])[i] = 0.f;  // the corners stay zero
     }
 
     // ---- per-thread work descriptors, fixed for the whole march
     const int lx0 = tid % TX, ly0 = tid / TX;  // owned column
     const int gx0 = xs + lx0, gy0 = ys + ly0;
     const bool own_ok = (lx0 < txe) && (ly0 < tye);
-    constexpr int RING1 = ring_size(FH), RING2 = OBJ ? 0 : ring_size(1);
-    const int box = UXn * UYn;  // S0 items: node columns of the front-end box
-    const int nA = OBJ ? 0 : TY * nbx, nB = OBJ ? 0 : nby * nbx;
-    const int offA = RING2 % NT, offB = (RING2 + nA) % NT, offS = (RING2 + nA + nB) % NT;
+    const int box = nbx * nby;  // S0 items: node columns of the box
+    const int nA = OBJ ? 0 : SY1 * nbx, nB = OBJ ? 0 : nby * nbx;
+    const int offA = RINGF % NT, offB = (RINGF + nA) % NT, offS = (RINGF + nA + nB) % NT;
     // S0 items (<= 2 per thread) as (global node column, Uz offset); A items
-    // (ly, bx) and B items (by, bx) packed as row*64 + col
+    // (row of the halo-1 region, bx) and B items (by, bx) packed as row*64 + col
     int s0_g[2], s0_s[2], a_it[2], b_it[2];
     for (int k = 0; k < 2; ++k) {
         const int i = (tid + NT - offS) % NT + k * NT;
         if (i < box) {
-            const int yy = i / UXn, xx = i - yy * UXn;
-            s0_g[k] = (UX0 + xx) + P.n0 * (UY0 + yy);
-            s0_s[k] = yy * SUBX + xx;
+            const int yy = i / nbx, xx = i - yy * nbx;
+            s0_g[k] = (BX0 + xx) + P.n0 * (BY0 + yy);
+            s0_s[k] = yy * SNBX + xx;
         } else {
             s0_g[k] = 0;
             s0_s[k] = -1;
@@ -257,9 +278,9 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
     double dacc = 0.0;
     int cur = BZ0;  // lower live node plane of the P^T accumulators
 
-    const int zbeg = z0 - FH;
-    const int fe_last = OBJ ? z1 : z1 + 1;   // last front-end plane needed
-    const int zend = OBJ ? z1 + 1 : z1 + 4;  // S2 (objective) or B of the last owned plane
+    const int zbeg = z0 - 1;
+    const int fe_last = z1;                   // last front-end plane needed
+    const int zend = OBJ ? z1 + 1 : z1 + 5;   // S2 (objective) or B of the plane above the chunk
 
     // S0: node values of plane zf interpolated in z into Uz[zf & 1]
     auto stage0 = [&](int zf) {
@@ -275,16 +296,16 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
             for (int c = 0; c < NVEC; ++c) {
                 const float* src = (c < 3) ? (P.u + c * P.N) : (P.p + (c - 3) * P.N);
                 const float a = __ldg(src + o), b = __ldg(src + o + P.znext);
-                uz[c * (SUBY * SUBX) + s0_s[k]] = fmaf(wzz, b - a, a);
+                uz[c * (SNBY * SNBX) + s0_s[k]] = fmaf(wzz, b - a, a);
             }
         }
     };
     // S1 on one column of plane zf; returns dT
     auto stage1 = [&](int lx, int ly, int zf, float& g0, float& g1, float& g2) {
         const int gx = xs + lx, gy = ys + ly;
-        const int li = (ly + 2) * SX2 + (lx + 2);
-        const int ax = S.fx2[lx + 2], ay = S.fy2[ly + 2];
-        const float wxv = S.wx2[lx + 2], wyv = S.wy2[ly + 2];
+        const int li = (ly + 1) * SX1 + (lx + 1);
+        const int ax = S.fx1[lx + 1], ay = S.fy1[ly + 1];
+        const float wxv = S.wx1[lx + 1], wyv = S.wy1[ly + 1];
         const int uzs = zf & 1;
         float uh[NVEC];
 #pragma unroll
@@ -300,15 +321,33 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
         S.Tw[slot][li] = tw;
         if (HESS) S.S[slot][li] = fmaf(g0, uh[NVEC - 3], fmaf(g1, uh[NVEC - 2], g2 * uh[NVEC - 1]));
     };
-    // S2 on one column of plane zq; owned columns also return pi(-z, 0, +z)
-    auto stage2 = [&](int lx, int ly, int zq, bool owned) {
-        const int gx = xs + lx, gy = ys + ly;
-        const int li = (ly + 2) * SX2 + (lx + 2);
+    // S1 of plane zf: the own column, then (last threads) a face-ring column
+    auto front_end = [&](int zf) {
+        if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
+        if (tid >= NT - RINGF) {
+            const int k = tid - (NT - RINGF);
+            int lx, ly;
+            ring_face(k, lx, ly);
+            const int gx = xs + lx, gy = ys + ly;
+            if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) {
+                float g0, g1, g2;
+                stage1(lx, ly, zf, g0, g1, g2);
+                if (!OBJ) {
+                    S.DTr[zf & 3][0][k] = g0;
+                    S.DTr[zf & 3][1][k] = g1;
+                    S.DTr[zf & 3][2][k] = g2;
+                }
+            }
+        }
+    };
+    // S2 on the own column of plane zq: pi of the own row
+    auto stage2 = [&](int zq) {
+        const int li = (ly0 + 1) * SX1 + (lx0 + 1);
         const int sc = zq & 3;
         const int szm = (zq > 0 ? zq - 1 : zq) & 3, szp = (zq < P.m2 - 1 ? zq + 1 : zq) & 3;
         // clamped neighbours (Eq. boundary_conditions), K order -z,-y,-x,+x,+y,+z
-        const int xm = (gx > 0) ? li - 1 : li, xp = (gx < P.m0 - 1) ? li + 1 : li;
-        const int ym = (gy > 0) ? li - SX2 : li, yp = (gy < P.m1 - 1) ? li + SX2 : li;
+        const int xm = (gx0 > 0) ? li - 1 : li, xp = (gx0 < P.m0 - 1) ? li + 1 : li;
+        const int ym = (gy0 > 0) ? li - SX1 : li, yp = (gy0 < P.m1 - 1) ? li + SX1 : li;
         const float r0 = S.R[sc][li], t0 = S.Tw[sc][li];
         const float dR[6] = {S.R[szm][li] - r0, S.R[sc][ym] - r0, S.R[sc][xm] - r0,
                              S.R[sc][xp] - r0, S.R[sc][yp] - r0, S.R[szp][li] - r0};
@@ -326,7 +365,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
         a2 = fmaf(0.5f, a2, P.tau2); // A^2 = ||grad T||_tau^2
         b2 = fmaf(0.5f, b2, P.rho2); // B^2 = ||grad R||_rho^2
         const float c1 = rsqrtf(a2 * b2);  // 1/(A B)
-        if (!HESS && owned && zq >= z0 && zq < z1) {
+        if (!HESS) {
             // 1 - r^2 = (A^2 B^2 - N^2)/(A^2 B^2), numerator by the Lagrange identity
             float a[6], b[6];
             const float ih6[6] = {P.ih[2], P.ih[1], P.ih[0], P.ih[0], P.ih[1], P.ih[2]};
@@ -367,13 +406,15 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
             w = fmaf(rh[4], S.S[sc][yp], w);
             w = fmaf(rh[5], S.S[szp][li], w);
         }
-        const int l1 = (ly + 1) * SX1 + (lx + 1);
+        const int l0 = ly0 * TX + lx0;
         const int pb = zq & 1;
-        S.Pi[pb][0][l1] = rh[2] * w;  // pi(-x)
-        S.Pi[pb][1][l1] = rh[3] * w;  // pi(+x)
-        S.Pi[pb][2][l1] = rh[1] * w;  // pi(-y)
-        S.Pi[pb][3][l1] = rh[4] * w;  // pi(+y)
-        if (owned) { pm_c = rh[0] * w; p0_c = rh0 * w; pp_c = rh[5] * w; }
+        S.Pi[pb][0][l0] = rh[2] * w;  // pi(-x)
+        S.Pi[pb][1][l0] = rh[3] * w;  // pi(+x)
+        S.Pi[pb][2][l0] = rh[1] * w;  // pi(-y)
+        S.Pi[pb][3][l0] = rh[4] * w;  // pi(+y)
+        pm_c = rh[0] * w;
+        p0_c = rh0 * w;
+        pp_c = rh[5] * w;
     };
     auto store_plane = [&](int pl) {  // node plane `pl` of this tile -> partials
 #pragma unroll
@@ -404,68 +445,78 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
                 dq1[c] = dq0[c];
                 dq0[c] = 0.f;
             }
-            if (zf >= 0 && zf < P.m2 && zf <= fe_last) {
-                if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
-                if (tid >= NT - RING1) {
-                    int lx, ly;
-                    ring_coord(tid - (NT - RING1), FH, lx, ly);
-                    const int gx = xs + lx, gy = ys + ly;
-                    float g0, g1, g2;
-                    if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage1(lx, ly, zf, g0, g1, g2);
-                }
-            }
+            if (zf >= 0 && zf < P.m2 && zf <= fe_last) front_end(zf);
         }
-        // ---- S2(zf-2)
+        // ---- S2(zf-2): the own rows of the chunk
         const int zq = zf - 2;
         pm_c = p0_c = pp_c = 0.f;
-        if (zq >= 0 && zq < P.m2 && (OBJ ? (zq >= z0 && zq < z1) : (zq >= z0 - 1 && zq <= z1))) {
-            if (gx0 < P.m0 && gy0 < P.m1) stage2(lx0, ly0, zq, true);
-            if (!OBJ && tid < RING2) {
-                int lx, ly;
-                ring_coord(tid, 1, lx, ly);
-                const int gx = xs + lx, gy = ys + ly;
-                if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage2(lx, ly, zq, false);
-            }
-        }
+        if (zq >= z0 && zq < z1 && own_ok) stage2(zq);
         if (!OBJ) {
-            // ---- S3(zf-3): column sums of dr^T over true neighbours
+            // ---- S3(zf-3): column sums of dr^T over the tile's own rows
             const int zo = zf - 3;
-            if (zo >= z0 && zo < z1) {
-                float t = 0.f;
+            if (zo >= z0 - 1 && zo <= z1 && zo >= 0 && zo < P.m2) {
+                const bool in_chunk = (zo >= z0 && zo < z1);
+                const int pb = zo & 1;
                 // dT(zo): three planes back before this interval's S1, four after it
                 const float dqo0 = S1_LAST ? dq2[0] : dq3[0], dqo1 = S1_LAST ? dq2[1] : dq3[1],
                             dqo2 = S1_LAST ? dq2[2] : dq3[2];
+                float t = 0.f;
                 if (own_ok) {
-                    const int l1 = (ly0 + 1) * SX1 + (lx0 + 1);
-                    const int pb = zo & 1;
-                    t = p0_prev;
-                    if (gx0 > 0) t += S.Pi[pb][1][l1 - 1];
-                    if (gx0 < P.m0 - 1) t += S.Pi[pb][0][l1 + 1];
-                    if (gy0 > 0) t += S.Pi[pb][3][l1 - SX1];
-                    if (gy0 < P.m1 - 1) t += S.Pi[pb][2][l1 + SX1];
-                    if (zo > 0) t += pp_prev2;
-                    if (zo < P.m2 - 1) t += pm_c;
+                    const int l0 = ly0 * TX + lx0;
+                    if (in_chunk) {
+                        t = p0_prev;
+                        if (lx0 > 0) t += S.Pi[pb][1][l0 - 1];
+                        if (lx0 + 1 < txe) t += S.Pi[pb][0][l0 + 1];
+                        if (ly0 > 0) t += S.Pi[pb][3][l0 - TX];
+                        if (ly0 + 1 < tye) t += S.Pi[pb][2][l0 + TX];
+                    }
+                    if (zo > 0 && zo - 1 >= z0) t += pp_prev2;    // row zo-1 of the chunk, its +z
+                    if (zo < P.m2 - 1 && zo + 1 < z1) t += pm_c;  // row zo+1 of the chunk, its -z
                     t *= P.qscale;
                 }
-                *reinterpret_cast<float4*>(S.Q4[zo & 1][tid]) =
+                *reinterpret_cast<float4*>(S.Q4[pb][(ly0 + 1) * SX1 + (lx0 + 1)]) =
                     own_ok ? make_float4(dqo0 * t, dqo1 * t, dqo2 * t, 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tid < RINGF) {
+                    // face-ring column: the one in-plane own row next to it
+                    int lx, ly;
+                    ring_face(tid, lx, ly);
+                    const int gx = xs + lx, gy = ys + ly;
+                    float tr = 0.f;
+                    if (in_chunk && gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) {
+                        if (ly < 0) {
+                            if (lx < txe) tr = S.Pi[pb][2][lx];                      // pi(-y) of row (lx, 0)
+                        } else if (ly == TY) {
+                            if (lx < txe) tr = S.Pi[pb][3][(TY - 1) * TX + lx];      // pi(+y) of row (lx, TY-1)
+                        } else if (lx < 0) {
+                            if (ly < tye) tr = S.Pi[pb][0][ly * TX];                 // pi(-x) of row (0, ly)
+                        } else {
+                            if (ly < tye) tr = S.Pi[pb][1][ly * TX + TX - 1];        // pi(+x) of row (TX-1, ly)
+                        }
+                        tr *= P.qscale;
+                    }
+                    const int dslot = zo & 3;
+                    *reinterpret_cast<float4*>(S.Q4[pb][(ly + 1) * SX1 + (lx + 1)]) =
+                        tr != 0.f ? make_float4(S.DTr[dslot][0][tid] * tr, S.DTr[dslot][1][tid] * tr,
+                                                S.DTr[dslot][2][tid] * tr, 0.f)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
             pp_prev2 = pp_prev;
             pp_prev = pp_c;
             p0_prev = p0_c;
             // ---- A(zf-4): x-reduction of q_hat
             const int za = zf - 4;
-            if (za >= z0 && za < z1) {
+            if (za >= z0 - 1 && za <= z1 && za >= 0 && za < P.m2) {
                 const int qs = za & 1;
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
                     if (a_it[k] < 0) continue;
-                    const int ly = a_it[k] >> 6, xx = a_it[k] & 63;
+                    const int ly = a_it[k] >> 6, xx = a_it[k] & 63;  // ly: row of the halo-1 region
                     float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-                    for (int lx = S.xr_lo[xx]; lx <= S.xr_hi[xx]; ++lx) {
-                        const float wxl = S.wx2[lx + 2];
-                        const float wx = (S.fxb[lx] == xx) ? 1.f - wxl : wxl;
-                        const float4 q = *reinterpret_cast<const float4*>(S.Q4[qs][ly * TX + lx]);
+                    for (int l = S.xr_lo[xx]; l <= S.xr_hi[xx]; ++l) {
+                        const float wxl = S.wx1[l];
+                        const float wx = (S.fx1[l] == xx) ? 1.f - wxl : wxl;
+                        const float4 q = *reinterpret_cast<const float4*>(S.Q4[qs][ly * SX1 + l]);
                         r.x = fmaf(wx, q.x, r.x);
                         r.y = fmaf(wx, q.y, r.y);
                         r.z = fmaf(wx, q.z, r.z);
@@ -475,7 +526,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
             }
             // ---- B(zf-5): y-reduction and z accumulation
             const int zb = zf - 5;
-            if (zb >= z0 && zb < z1) {
+            if (zb >= z0 - 1 && zb <= z1 && zb >= 0 && zb < P.m2) {
                 const int fzo = P.fz[zb];
                 const float wzo = P.wz[zb];
                 if (fzo > cur) {  // node plane `cur` is complete
@@ -488,10 +539,10 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
                     if (b_it[k] < 0) continue;
                     const int yy = b_it[k] >> 6, xx = b_it[k] & 63;
                     float q0 = 0.f, q1 = 0.f, q2 = 0.f;
-                    for (int ly = S.yr_lo[yy]; ly <= S.yr_hi[yy]; ++ly) {
-                        const float wyl = S.wy2[ly + 2];
-                        const float wy = (S.fyb[ly] == yy) ? 1.f - wyl : wyl;
-                        const float4 q = *reinterpret_cast<const float4*>(S.Qx4[qs][ly][xx]);
+                    for (int l = S.yr_lo[yy]; l <= S.yr_hi[yy]; ++l) {
+                        const float wyl = S.wy1[l];
+                        const float wy = (S.fy1[l] == yy) ? 1.f - wyl : wyl;
+                        const float4 q = *reinterpret_cast<const float4*>(S.Qx4[qs][l][xx]);
                         q0 = fmaf(wy, q.x, q0);
                         q1 = fmaf(wy, q.y, q1);
                         q2 = fmaf(wy, q.z, q2);
@@ -513,16 +564,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
                 dq1[c] = dq0[c];
                 dq0[c] = 0.f;
             }
-            if (zf >= 0 && zf < P.m2 && zf <= fe_last) {
-                if (gx0 < P.m0 && gy0 < P.m1) stage1(lx0, ly0, zf, dq0[0], dq0[1], dq0[2]);
-                if (tid >= NT - RING1) {
-                    int lx, ly;
-                    ring_coord(tid - (NT - RING1), FH, lx, ly);
-                    const int gx = xs + lx, gy = ys + ly;
-                    float g0, g1, g2;
-                    if (gx >= 0 && gx < P.m0 && gy >= 0 && gy < P.m1) stage1(lx, ly, zf, g0, g1, g2);
-                }
-            }
+            if (zf >= 0 && zf < P.m2 && zf <= fe_last) front_end(zf);
         }
         __syncthreads();
     }

@@ -85,35 +85,40 @@ struct SsdSmem {
 };
 
 // Shared memory of the NGF image pass (one barrier per plane, so every ring
-// is one plane deeper than the stages' distance): R, Tw, s in four plane
-// slots, the in-plane products and the node-plane buffers in two.  The node
-// boxes are compile-time sizes: the compact layout holds grids with two or
-// more voxels per cell in x and y (two CTAs per SM), the wide one any ratio.
-template <int UBX_, int UBY_, int NBX_, int NBY_>
+// is one plane deeper than the stages' distance).  The pass works on the
+// halo-1 region of its tile: R, Tw, s of the owned columns and the face ring
+// in four plane slots, the in-plane products of the owned rows and q_hat of
+// the whole region in two.  The tile's node box covers the halo-1 region
+// (the z-interpolated node planes and the P^T accumulators use the same
+// box); its size is a compile-time bound: the compact layout holds grids
+// with two or more voxels per cell in x and y (two CTAs per SM), the wide
+// one any ratio.
+constexpr int RINGF = 2 * TX + 2 * TY;  // face ring of the halo-1 region (no corners)
+template <int NBX_, int NBY_>
 struct ImgSmemT {
-    static constexpr int kUBX = UBX_, kUBY = UBY_, kNBX = NBX_, kNBY = NBY_;
-    float R[4][R2N];
-    float Tw[4][R2N];
-    float S[4][R2N];
+    static constexpr int kNBX = NBX_, kNBY = NBY_;
+    float R[4][R1N];
+    float Tw[4][R1N];
+    float S[4][R1N];
     union {
-        float Pi[2][4][R1N];    // pi(-x), pi(+x), pi(-y), pi(+y) of the halo-1 region
+        float Pi[2][4][R0N];    // pi(-x), pi(+x), pi(-y), pi(+y) of the owned rows
         double red[NT];         // reductions after the march
     };
-    float Uz[2][6][UBY_][UBX_];           // u (and p) interpolated to a plane in z
-    alignas(16) float Q4[2][R0N][4];      // q_hat of the owned columns (3 components + pad)
-    alignas(16) float Qx4[2][TY][NBX_][4];  // q_hat reduced onto node columns in x
+    float DTr[4][3][RINGF];     // dT of the face-ring columns
+    float Uz[2][6][NBY_][NBX_];           // u (and p) interpolated to a plane in z
+    alignas(16) float Q4[2][R1N][4];      // q_hat of the halo-1 region (corners stay zero)
+    alignas(16) float Qx4[2][SY1][NBX_][4];  // q_hat reduced onto node columns in x
     float Acc[2][3][NBY_][NBX_];          // node-plane accumulators of P^T (two live planes)
-    float wx2[SX2], wy2[SY2];
-    int fx2[SX2], fy2[SY2];     // node floor relative to the Uz box
-    int fxb[TX], fyb[TY];       // node floor relative to the partial box
+    float wx1[SX1], wy1[SY1];
+    int fx1[SX1], fy1[SY1];     // node floor relative to the tile's node box
     int xr_lo[NBX_], xr_hi[NBX_], yr_lo[NBY_], yr_hi[NBY_];
 };
-// >= 2 voxels per cell: the 36 x 20 front-end region spans <= 20 x 12 nodes,
-// the 32 x 16 owned columns <= 18 x 10 (checked per plan on the host)
-using ImgSmemC = ImgSmemT<20, 12, 18, 10>;
-using ImgSmemW = ImgSmemT<UBX, UBY, NBX, NBY>;
-// planes a CTA marches beyond its z-chunk: two front-end halo planes and the
-// pipeline's drain from S1 to B
+// >= 2 voxels per cell: the 34 x 18 halo-1 region spans <= 19 x 11 nodes
+// (checked per plan on the host); any ratio: <= 35 x 19
+using ImgSmemC = ImgSmemT<19, 11>;
+using ImgSmemW = ImgSmemT<DBX, DBY>;
+// planes a CTA marches beyond its z-chunk: the halo plane on each side and
+// the pipeline's drain from S1 to B
 constexpr int IMG_FILL = 7;
 
 // Shared memory of the diagonal pass; the windows are sized for the span, so

@@ -76,6 +76,13 @@ struct Plan {
 cudaError_t dev_alloc(void** ptr, size_t bytes, cudaStream_t stream);
 void dev_free(void* ptr, cudaStream_t stream);
 
+// tile-partial geometry of the image pass: the NGF pass writes q_hat on the
+// halo-1 region of its tile (the face ring carries its rows' transposed
+// stencil), the SSD pass on the tile alone
+inline const Geometry& img_geom(const Plan* p) {
+    return p->desc.distance == NGF_DIST_SSD ? p->g0 : p->g1;
+}
+
 // helpers implemented in ngf_api.cu
 ngf_status set_error(Plan* p, ngf_status s, const std::string& msg);
 ngf_status cuda_check(Plan* p, cudaError_t e, const char* what);

@@ -177,8 +177,10 @@ def test_thorax_full_size_properties(ngf):
 
 
 def test_pcg_matches_oracle_and_graph(ngf):
-    """PCG iterates equal the oracle's; the captured-graph solve reproduces
-    the direct launches bitwise (same diagonal, same inputs)."""
+    """PCG iterates equal the oracle's.  pcg_solve (two launches per
+    iteration: the image pass and the cooperative nodal kernel), directly and
+    as a captured graph, reproduces pcg_step (five launches per iteration)
+    bitwise in every state vector and float64 scalar."""
     import oracle as O
     c, _ = G.workload_case("blobs_32")
     iters = 8
@@ -190,17 +192,24 @@ def test_pcg_matches_oracle_and_graph(ngf):
         dg = c.empty()
         ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, dg)
         rhs = (-g).contiguous()
-        for use_graph in (False, True):
+        for arm in ("steps", "direct", "graph"):
             vec = [c.empty() for _ in range(5)]
             sc = torch.zeros(8, device="cuda", dtype=torch.float64)
             st = ngf.pcg_state(*vec, dg, sc)
             ngf.pcg_init(pl.handle, st, rhs)
-            ngf.pcg_solve(pl.handle, st, c.R, c.T, c.u, iters, use_graph=use_graph)
+            if arm == "steps":
+                for _ in range(iters):
+                    ngf.pcg_step(pl.handle, st, c.R, c.T, c.u)
+            else:
+                ngf.pcg_solve(pl.handle, st, c.R, c.T, c.u, iters, use_graph=(arm == "graph"))
             info = ngf.pcg_read(pl.handle, st)
             stream.synchronize()
-            res[use_graph] = (vec[0].clone(), info)
-    assert torch.equal(res[False][0], res[True][0])
-    x, info = res[True]
+            res[arm] = ([v.clone() for v in vec[:4]], sc.clone(), info)
+    for arm in ("direct", "graph"):
+        for a, b in zip(res[arm][0], res["steps"][0]):
+            assert torch.equal(a, b), arm
+        assert torch.equal(res[arm][1], res["steps"][1]), arm
+    x, info = res["graph"][0][0], res["graph"][2]
     assert info.iters_done == iters and info.status == 0
     xo, _ = O.pcg(c.L, c.Rh, c.Th, c.uh, G.f64(rhs), G.f64(dg), iters)
     assert G.rel(G.f64(x), xo) < G.TOL_PCG
