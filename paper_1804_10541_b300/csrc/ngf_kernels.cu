@@ -2,6 +2,8 @@
 // ngf_kernels.cuh).
 #include "ngf_kernels.cuh"
 
+#include <climits>
+
 namespace ngf {
 
 // position of ring element k of the (TX+2h) x (TY+2h) region minus the TX x TY core
@@ -157,9 +159,7 @@ __device__ __forceinline__ float warp_sample(const ImgParams& P, int gx, int gy,
 // variable zf):
 //   S0(zf+1): node values of u (and p) interpolated in z to plane zf+1;
 //   S1(zf)  : warp T and dT (and s = dT . P p) on the own columns and the
-//             face ring (first in the interval, or last for the Hessian,
-//             whose template gathers then overlap the other warps' stencil
-//             work);
+//             face ring, first in the interval;
 //   S2(zf-2): residual Jacobian row rho_hat (Eqs. rho, hatRho) of the own
 //             rows and the products pi_i(k): in-plane ones to shared memory,
 //             pi(0) and pi(+-z) in registers;
@@ -249,12 +249,19 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
     const bool own_ok = (lx0 < txe) && (ly0 < tye);
     const int box = nbx * nby;  // S0 items: node columns of the box
     const int nA = OBJ ? 0 : SY1 * nbx, nB = OBJ ? 0 : nby * nbx;
-    const int offA = RINGF % NT, offB = (RINGF + nA) % NT, offS = (RINGF + nA + nB) % NT;
+    // The A, B and S0 items form one sequence dealt out to thread positions:
+    // first the threads without ring work, then those with the ring's cheap
+    // S3; the threads with a second front-end column (the ring's S1) take
+    // items only when the layout's items exceed two per other thread.
+    constexpr bool FEW_ITEMS = SY1 * SNBX + 2 * SNBY * SNBX <= 2 * (NT - RINGF);
+    constexpr int W = FEW_ITEMS ? NT - RINGF : NT;
+    const int pos = !FEW_ITEMS ? tid : (tid >= NT - RINGF ? -1 : (tid >= RINGF ? tid - RINGF : tid + NT - 2 * RINGF));
+    const int offA = 0, offB = nA % W, offS = (nA + nB) % W;
     // S0 items (<= 2 per thread) as (global node column, Uz offset); A items
     // (row of the halo-1 region, bx) and B items (by, bx) packed as row*64 + col
     int s0_g[2], s0_s[2], a_it[2], b_it[2];
     for (int k = 0; k < 2; ++k) {
-        const int i = (tid + NT - offS) % NT + k * NT;
+        const int i = pos < 0 ? INT_MAX : (pos + W - offS) % W + k * W;
         if (i < box) {
             const int yy = i / nbx, xx = i - yy * nbx;
             s0_g[k] = (BX0 + xx) + P.n0 * (BY0 + yy);
@@ -263,7 +270,8 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
             s0_g[k] = 0;
             s0_s[k] = -1;
         }
-        const int ia = (tid + NT - offA) % NT + k * NT, ib = (tid + NT - offB) % NT + k * NT;
+        const int ia = pos < 0 ? INT_MAX : (pos + W - offA) % W + k * W;
+        const int ib = pos < 0 ? INT_MAX : (pos + W - offB) % W + k * W;
         a_it[k] = (ia < nA) ? ((ia / nbx) << 6) + (ia % nbx) : -1;
         b_it[k] = (ib < nB) ? ((ib / nbx) << 6) + (ib % nbx) : -1;
     }
@@ -430,23 +438,20 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
         }
     };
 
-    constexpr bool S1_LAST = HESS;
-
     if (zbeg >= 0 && zbeg < P.m2) stage0(zbeg);
     __syncthreads();
 
     for (int zf = zbeg; zf <= zend; ++zf) {
         if (zf + 1 >= 0 && zf + 1 < P.m2 && zf + 1 <= fe_last) stage0(zf + 1);
-        if constexpr (!S1_LAST) {  // ---- S1(zf)
+        // ---- S1(zf)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dq3[c] = dq2[c];
-                dq2[c] = dq1[c];
-                dq1[c] = dq0[c];
-                dq0[c] = 0.f;
-            }
-            if (zf >= 0 && zf < P.m2 && zf <= fe_last) front_end(zf);
+        for (int c = 0; c < 3; ++c) {
+            dq3[c] = dq2[c];
+            dq2[c] = dq1[c];
+            dq1[c] = dq0[c];
+            dq0[c] = 0.f;
         }
+        if (zf >= 0 && zf < P.m2 && zf <= fe_last) front_end(zf);
         // ---- S2(zf-2): the own rows of the chunk
         const int zq = zf - 2;
         pm_c = p0_c = pp_c = 0.f;
@@ -457,9 +462,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
             if (zo >= z0 - 1 && zo <= z1 && zo >= 0 && zo < P.m2) {
                 const bool in_chunk = (zo >= z0 && zo < z1);
                 const int pb = zo & 1;
-                // dT(zo): three planes back before this interval's S1, four after it
-                const float dqo0 = S1_LAST ? dq2[0] : dq3[0], dqo1 = S1_LAST ? dq2[1] : dq3[1],
-                            dqo2 = S1_LAST ? dq2[2] : dq3[2];
+                const float dqo0 = dq3[0], dqo1 = dq3[1], dqo2 = dq3[2];  // dT(zo)
                 float t = 0.f;
                 if (own_ok) {
                     const int l0 = ly0 * TX + lx0;
@@ -556,15 +559,6 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
                     S.Acc[hi][2][yy][xx] = fmaf(wzo, q2, S.Acc[hi][2][yy][xx]);
                 }
             }
-        }
-        if constexpr (S1_LAST) {  // ---- S1(zf), the same as above
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                dq2[c] = dq1[c];
-                dq1[c] = dq0[c];
-                dq0[c] = 0.f;
-            }
-            if (zf >= 0 && zf < P.m2 && zf <= fe_last) front_end(zf);
         }
         __syncthreads();
     }
