@@ -403,8 +403,9 @@ def run_ours(args):
                         "frac": (bytes_per_voxel * M / t_launch / 1e9) / peaks["hbm_gbs"] if "hbm_gbs" in peaks else None},
                 "kernel_gvoxel_s": M / t_launch / 1e9,
                 "measured_limiter": "instruction issue and latency, not the FP32 pipes or HBM: ncu shows issue "
-                                    "active 57%, FMA pipe 27%, DRAM 3% of peak, top stalls barrier and "
-                                    "long scoreboard (profiles/k_image_hess_<workload>.md)"}
+                                    "active 61-63%, FMA pipe 28%, DRAM 3-4% of peak, top stalls long "
+                                    "scoreboard (template gathers) and barrier "
+                                    "(profiles/k_image_hess_<workload>.md)"}
 
     if rank == 0:
         cpu = None if (args.no_cpu_baseline or ws > 1) else cpu_baseline_leg(workload, R, T, w)
