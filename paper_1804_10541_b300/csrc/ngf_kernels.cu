@@ -216,13 +216,19 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
         S.wy1[i] = P.wy[gy];
     }
     if (!OBJ) {
+        for (int i = tid; i < 2 * 3 * SNBY * SNBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
+        // S3 writes every q_hat entry of the region but its four corners
+        if (tid < 2 * 4) {
+            const int c = tid & 3;
+            const int l = ((c >> 1) ? (SY1 - 1) * SX1 : 0) + ((c & 1) ? SX1 - 1 : 0);
+            *reinterpret_cast<float4*>(S.Q4[tid >> 2][l]) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();  // node floors of the region in shared memory
         // halo-1 columns (in the image) reduced onto each node column / row
         for (int b = tid; b < nbx; b += NT) {
             int lo = SX1, hi = -1;
-            for (int l = 0; l < SX1; ++l) {
-                const int gx = xs - 1 + l;
-                if (gx < 0 || gx >= P.m0) continue;
-                const int f = P.fx[gx] - BX0;
+            for (int l = max(0, 1 - xs); l < min(SX1, P.m0 - xs + 1); ++l) {
+                const int f = S.fx1[l];
                 if (f == b || f == b - 1) { lo = min(lo, l); hi = max(hi, l); }
             }
             S.xr_lo[b] = lo;
@@ -230,17 +236,13 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
         }
         for (int b = tid; b < nby; b += NT) {
             int lo = SY1, hi = -1;
-            for (int l = 0; l < SY1; ++l) {
-                const int gy = ys - 1 + l;
-                if (gy < 0 || gy >= P.m1) continue;
-                const int f = P.fy[gy] - BY0;
+            for (int l = max(0, 1 - ys); l < min(SY1, P.m1 - ys + 1); ++l) {
+                const int f = S.fy1[l];
                 if (f == b || f == b - 1) { lo = min(lo, l); hi = max(hi, l); }
             }
             S.yr_lo[b] = lo;
             S.yr_hi[b] = hi;
         }
-        for (int i = tid; i < 2 * 3 * SNBY * SNBX; i += NT) (&S.Acc[0][0][0][0])[i] = 0.f;
-        for (int i = tid; i < 2 * R1N * 4; i += NT) (&S.Q4[0][0][0])[i] = 0.f;  // the corners stay zero
     }
 
     // ---- per-thread work descriptors, fixed for the whole march
@@ -425,6 +427,7 @@ __device__ __forceinline__ void image_pass(const ImgParams& P, int bx, int by, i
         pp_c = rh[5] * w;
     };
     auto store_plane = [&](int pl) {  // node plane `pl` of this tile -> partials
+        if (pl >= P.n2) return;  // the empty second plane of a planar level's box: never read
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (b_it[k] < 0) continue;
@@ -691,6 +694,7 @@ __device__ __forceinline__ void ssd_pass(const ImgParams& P, int bx_, int by_, i
         }
     };
     auto store_plane = [&](int pl) {
+        if (pl >= P.n2) return;  // the empty second plane of a planar level's box: never read
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             if (b_it[k] < 0) continue;
