@@ -11,6 +11,8 @@
 // Shared-memory operand layout (K-major, no swizzle): 8x8 core matrices of
 // 16-byte rows; the leading byte offset steps between the two 8-channel
 // halves of a K=16 slab, the stride byte offset between 8-row groups.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -196,25 +198,52 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_
                  : "memory");
 }
 
-// Per chunk, after all threads staged its brick: thread 32 (warp 1) streams
+// Tiled tensor copy of one 5-D box (TMA) from global to shared memory,
+// completing on mbarrier `bar` with its byte count; coordinates in elements,
+// innermost first (channel, x, y, z, batch); boxes reaching outside the
+// tensor are filled with zeros.
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            int c4, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory bytes of one channel-group plane of the brick (16 bytes per
+// voxel), rounded up to 128 so that every plane starts a tensor copy on a
+// 128-byte boundary.
+__host__ __device__ constexpr uint32_t brick_plane_bytes(int P) {
+    return ((uint32_t)BR_X * BR_Y * (P + 2) * 16 + 127u) & ~127u;
+}
+
+// Per chunk: thread 0 copies the chunk's input brick by one tensor copy per
+// channel group (zeros outside the volume) and the CTA waits for it; thread
+// 32 (warp 1) streams
 // the chunk's packed weights, one bulk copy per tap, into nbuf buffers (a
 // "full" mbarrier per buffer counts the bytes); thread 0 issues the MMAs of
 // each tap once its buffer is full and commits to the buffer's "empty"
 // mbarrier, and after the chunk's last tap to the "chunk" mbarrier that the
 // whole CTA waits on before restaging the brick (or draining the result).
-__global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a) {
-    NGF_DYNAMIC_SMEM(smem);
+__global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a,
+                                                               const __grid_constant__ CUtensorMap xmap) {
+    NGF_DYNAMIC_SMEM(smem_raw);
+    // the brick starts on a 128-byte boundary (tensor-copy destination)
+    unsigned char* smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nbuf = a.nbuf, P = a.P, cg = a.kc / 8, ns = a.ns, n0 = blockIdx.y * a.ns;
     const int nb = BR_X * BR_Y * (P + 2);           // brick voxels
-    const uint32_t brick_bytes = (uint32_t)cg * nb * 16, b_bytes = (uint32_t)ns * a.kc * 2;
+    const uint32_t gplane = brick_plane_bytes(P);   // one channel group of the brick
+    const uint32_t brick_bytes = (uint32_t)cg * gplane, b_bytes = (uint32_t)ns * a.kc * 2;
     const uint32_t st_bytes = a.tps * b_bytes;     // one weight stage
     const int spc = 27 / a.tps;                    // stages per chunk
     const uint32_t sBr = smem_addr(smem), sB = sBr + brick_bytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + brick_bytes + nbuf * st_bytes);
     uint64_t* empty = full + CONV_MAXBUF;
     uint64_t* chunk_bar = empty + CONV_MAXBUF;
-    int* flags = reinterpret_cast<int*>(chunk_bar + 1);  // [0] failed, [1] copies issued, [2] stages consumed
+    uint64_t* brick_bar = chunk_bar + 1;                 // the brick's tensor copies
+    int* flags = reinterpret_cast<int*>(brick_bar + 1);  // [0] failed, [1] copies issued, [2] stages consumed
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags + 3);
     const uint32_t tcols = (uint32_t)(P * a.ncols);
 
@@ -230,6 +259,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
             mbar_init(smem_addr(&empty[i]), 1);
         }
         mbar_init(smem_addr(chunk_bar), 1);
+        mbar_init(smem_addr(brick_bar), 1);
         flags[0] = 0; flags[1] = 0; flags[2] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -244,6 +274,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
                               (size_t)blockIdx.y * a.nch * 27 * b_bytes;  // this slice's stages
     uint32_t tmem = 0;
     bool failed = false;
+    int brick_pending = -1;  // chunk whose brick copy is issued and not seen complete
     __syncthreads();  // barriers and flags initialised before the producer's first copy
 
     for (int c = 0; c < a.nch; ++c) {
@@ -274,22 +305,24 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
             }
         };
         if (tid == 32) produce(spc * c, pre_end);
-        // the brick of chunk c: one 16-byte copy per (voxel, channel group),
-        // channel group fastest across lanes (contiguous global reads), zero
-        // outside
-        for (int idx = tid; idx < cg * nb; idx += CONV_THREADS) {
-            const int g = idx % cg, v = idx / cg;
-            const int bx = v % BR_X, by = (v / BR_X) % BR_Y, bz = v / (BR_X * BR_Y);
-            const int gx = x0 - 1 + bx, gy = y0 - 1 + by, gz = z0 - 1 + bz;
-            const bool in = gx >= 0 && gx < a.W && gy >= 0 && gy < a.H && gz >= 0 && gz < a.D;
-            const uint4* src = a.x;
-            if (in) src += ((((long long)b * a.D + gz) * a.H + gy) * a.W + gx) * (a.cin / 8) + c * cg + g;
-            cp16_ca(sBr + (uint32_t)(g * nb + v) * 16, src, in ? 16u : 0u);
+        // the brick of chunk c: one tensor copy per channel group, the box
+        // (8 channels, 10 x, 18 y, P+2 z) from (x0-1, y0-1, z0-1) of batch b,
+        // zeros outside the volume; every thread waits for its bytes
+        if (tid == 0) {
+            mbar_expect_tx(smem_addr(brick_bar), (uint32_t)cg * nb * 16);
+            for (int g = 0; g < cg; ++g)
+                tma_load_5d(sBr + g * gplane, &xmap, c * a.kc + 8 * g, x0 - 1, y0 - 1, z0 - 1, b,
+                            smem_addr(brick_bar));
         }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        brick_pending = c;
+        const bool brick_ok = mbar_wait(smem_addr(brick_bar), (uint32_t)(c & 1));
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        if (__syncthreads_or(!brick_ok)) {
+            if (tid == 0) atomicExch(&flags[0], 1);
+            failed = true;
+            break;
+        }
+        brick_pending = -1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         tmem = *tmem_slot;
 
@@ -298,7 +331,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         } else if (tid == 0) {
             // MMA issuer
             const uint32_t idesc = instr_desc(CONV_M, ns);
-            const uint32_t lbo = (uint32_t)nb * 16;  // one channel group plane
+            const uint32_t lbo = gplane;  // one channel group plane
             for (int s = spc * c; s < spc * c + spc; ++s) {
                 const int buf = s % nbuf;
                 if (!mbar_wait(smem_addr(&full[buf]), (uint32_t)((s / nbuf) & 1))) {
@@ -374,6 +407,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         atomicAdd(&g_conv_timeouts, 1u);
         // bounded waits for bulk copies still in flight (issued, not consumed)
         for (int s = flags[2]; s < flags[1]; ++s) mbar_wait(smem_addr(&full[s % nbuf]), (uint32_t)((s / nbuf) & 1));
+        if (brick_pending >= 0) mbar_wait(smem_addr(brick_bar), (uint32_t)(brick_pending & 1));
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -381,6 +415,39 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
     }
+}
+
+// cuTensorMapEncodeTiled of the installed driver, looked up once through the
+// runtime (the library does not link the driver library itself).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+// Tensor map of the brick kernel's input x[B][D][H][W][C] (bf16, channels
+// fastest): 5-D (C, W, H, D, B), boxes of 8 channels x 10 x 18 x (P+2) x 1,
+// zeros outside.  The strides are multiples of 16 bytes because C is a
+// multiple of 16, and x is 16-byte aligned (both checked by the caller).
+bool brick_map(CUtensorMap* map, const void* x, int B, int D, int H, int W, int C, int P) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dim[5] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)D, (cuuint64_t)B};
+    const cuuint64_t stride[4] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2,
+                                  (cuuint64_t)D * H * W * C * 2};
+    const cuuint32_t box[5] = {8, BR_X, BR_Y, (cuuint32_t)(P + 2), 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dim, stride, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // The brick kernel's dynamic shared-memory limit is raised once per device
@@ -681,7 +748,7 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
         for (int p = 4; p >= 1; p >>= 1) {
             if (p * ncols > col_cap || (p > 1 && p > D)) continue;
             const size_t wst = (size_t)Cout * br.kc * 2;
-            const size_t brick = (size_t)(br.kc / 8) * BR_X * BR_Y * (p + 2) * 16;
+            const size_t brick = (size_t)(br.kc / 8) * brick_plane_bytes(p);
             int nbf = CONV_MAXBUF;
             while (nbf > 3 && brick + nbf * wst > 110 * 1024) --nbf;
             if (brick + nbf * wst <= 110 * 1024 || p == 1) { br.P = p; br.nbuf = nbf; break; }
@@ -692,7 +759,7 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
         br.ncols = 32;
         while (br.ncols < br.ns) br.ncols <<= 1;
         const size_t wst = (size_t)br.ns * br.kc * 2;
-        const size_t brick = (size_t)(br.kc / 8) * BR_X * BR_Y * (br.P + 2) * 16;
+        const size_t brick = (size_t)(br.kc / 8) * brick_plane_bytes(br.P);
         // taps per weight stage: small weight images are moved several taps
         // per bulk copy (fewer waits in the MMA thread's chain)
         br.tps = 1;
@@ -701,7 +768,8 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
         const int stages = br.nch * (27 / br.tps);
         br.nbuf = stages < CONV_MAXBUF ? stages : CONV_MAXBUF;
         while (br.nbuf > 1 && brick + br.nbuf * br.tps * wst > 110 * 1024) --br.nbuf;
-        size_t smem = brick + br.nbuf * br.tps * wst + (2 * CONV_MAXBUF + 1) * sizeof(uint64_t) + 32;
+        // + 128: the brick is aligned to 128 bytes inside the dynamic block
+        size_t smem = 128 + brick + br.nbuf * br.tps * wst + (2 * CONV_MAXBUF + 2) * sizeof(uint64_t) + 32;
         // every resident CTA's tensor-memory allocation must fit at once
         const size_t ctas = 512 / (br.P * br.ncols);
         const size_t smem_min = per_sm / (ctas + 1) - 1024 + 16;
@@ -719,10 +787,12 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
                               static_cast<uint4*>(wp), (int)Cin, (int)Cout, br.ns, br.kc)
                      : launch(k_conv3d_pack_w, pg, dim3(256), 0, st, static_cast<const uint4*>(w),
                               static_cast<uint4*>(wp), (int)Cout, (int)Cin, br.ns, br.kc);
-        const bool ok = pe == cudaSuccess &&
+        CUtensorMap xmap;
+        const bool mapped = brick_map(&xmap, x, B, D, H, W, Cin, br.P);
+        const bool ok = pe == cudaSuccess && mapped &&
                         (br.w = static_cast<const uint4*>(wp),
                          launch(k_conv3d_brick, dim3((unsigned)tiles, (unsigned)(Cout / br.ns)), dim3(CONV_THREADS),
-                                smem, st, br) == cudaSuccess);
+                                smem, st, br, xmap) == cudaSuccess);
         dev_free(wp, st);
         return ok ? NGF_OK : NGF_ECUDA;
     }
