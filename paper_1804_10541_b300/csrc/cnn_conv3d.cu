@@ -332,6 +332,13 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
             // MMA issuer
             const uint32_t idesc = instr_desc(CONV_M, ns);
             const uint32_t lbo = gplane;  // one channel group plane
+            // Descriptors of the brick's and the weight buffers' starts: an
+            // operand at byte offset o (a multiple of 16) is the start's
+            // descriptor plus o / 16, since the start-address field holds
+            // address / 16 in 14 bits and shared addresses stay below 256 KB
+            // (no carry out of the field).
+            const uint64_t ad0 = smem_desc(sBr, lbo, BR_X * 16), bd0 = smem_desc(sB, 128, 256);
+            const uint32_t ja = 2 * lbo / 16, jb = (uint32_t)(ns / 8) * 256 / 16, nkj = (uint32_t)(a.kc / 16);
             for (int s = spc * c; s < spc * c + spc; ++s) {
                 const int buf = s % nbuf;
                 if (!mbar_wait(smem_addr(&full[buf]), (uint32_t)((s / nbuf) & 1))) {
@@ -342,16 +349,12 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
                 for (int i = 0; i < a.tps; ++i) {
                     const int tap = (s - spc * c) * a.tps + i;
                     const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // brick offsets 0..2
-                    const uint32_t bbase = sB + buf * st_bytes + i * b_bytes;
-                    for (int p = 0; p < P; ++p) {
-                        const uint32_t abase = sBr + (uint32_t)(((p + dz) * BR_Y + dy) * BR_X + dx) * 16;
-                        for (int j = 0; j < a.kc / 16; ++j) {
-                            const uint64_t ad = smem_desc(abase + 2 * j * lbo, lbo, BR_X * 16);
-                            const uint64_t bd = smem_desc(bbase + j * (ns / 8) * 256, 128, 256);
-                            mma_bf16(tmem + (uint32_t)(p * a.ncols), ad, bd, idesc,
-                                     (s > 0 || i > 0 || j > 0) ? 1u : 0u);
-                        }
-                    }
+                    const uint64_t bd = bd0 + (buf * st_bytes + i * b_bytes) / 16;
+                    uint64_t ad = ad0 + (uint32_t)((dz * BR_Y + dy) * BR_X + dx);  // 16 bytes per brick voxel
+                    uint32_t d = tmem;
+                    for (int p = 0; p < P; ++p, ad += BR_X * BR_Y, d += (uint32_t)a.ncols)
+                        for (uint32_t j = 0; j < nkj; ++j)
+                            mma_bf16(d, ad + j * ja, bd + j * jb, idesc, (s > 0 || i > 0 || j > 0) ? 1u : 0u);
                 }
                 mma_commit(smem_addr(&empty[buf]));
                 flags[2] = s + 1;
