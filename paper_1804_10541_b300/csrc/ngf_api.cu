@@ -387,7 +387,7 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     for (auto kern : {k_ssd_obj, k_ssd_grad, k_ssd_hess, k_ssd_diag})
         NGF_CU(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsdSmem)),
                "smem attr");
-    for (auto kern : {k_diag, k_diag_s1, k_diag_s2, k_diag_s3})
+    for (auto kern : {k_diag, k_diag_s2, k_diag_s3})
         NGF_CU(p, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmemT<3>)),
                "smem attr");
     NGF_CU(p, cudaFuncSetAttribute(k_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(DiagSmemT<4>)), "smem attr");
@@ -561,11 +561,11 @@ ngf_status diagonal_impl(Plan* p, const float* R, const float* T, const float* u
     ImgParams P = img_params(p, R, T, u, nullptr, MODE_HESS, p->g1, nullptr);
     NGF_CU(p, prof_mark(p, NGF_K_DIAGONAL), "cudaEventRecord");
     // three-node span: the kernel with the plan's largest shuffle-step count
-    // fixed at compile time when it is 1 to 3
+    // fixed at compile time when it is 2 or 3
     using DiagKernel = void (*)(const ImgParams);
     const int ds = std::max(p->dsteps[0], p->dsteps[1]);
     DiagKernel dk = k_diag4;
-    if (p->diag_span3) dk = ds == 1 ? k_diag_s1 : ds == 2 ? k_diag_s2 : ds == 3 ? k_diag_s3 : k_diag;
+    if (p->diag_span3) dk = ds == 2 ? k_diag_s2 : ds == 3 ? k_diag_s3 : k_diag;
     NGF_CU(p, launch(dk, img_grid(p->g1), dim3(NT), p->diag_span3 ? sizeof(DiagSmemT<3>) : sizeof(DiagSmemT<4>),
                      p->stream, P),
            "k_diag");

@@ -214,7 +214,7 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
         B_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, csmem), "smem attr");
     for (auto kern : {k_batch_image_obj_w, k_batch_image_grad_w, k_batch_image_hess_w})
         B_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, wsmem), "smem attr");
-    for (auto kern : {k_batch_diag, k_batch_diag_s1, k_batch_diag_s2, k_batch_diag_s3})
+    for (auto kern : {k_batch_diag, k_batch_diag_s2, k_batch_diag_s3})
         B_CU(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem3), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_diag4, cudaFuncAttributeMaxDynamicSharedMemorySize, dsmem), "smem attr");
     B_CU(cudaFuncSetAttribute(k_batch_ssd_diag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsdSmem)),
@@ -283,8 +283,7 @@ static ngf_status launch_diag(const Batch& b, const std::vector<ImgParams>& tab,
                 if (!is_ssd(p) && p->diag_span3) ds = std::max({ds, p->dsteps[0], p->dsteps[1]});
             }
             using BatchKernel = void (*)(const BatchQueue, const BatchImgTable);
-            const BatchKernel dk = ds == 1 ? k_batch_diag_s1 : ds == 2 ? k_batch_diag_s2 : ds == 3 ? k_batch_diag_s3
-                                                                                                    : k_batch_diag;
+            const BatchKernel dk = ds == 2 ? k_batch_diag_s2 : ds == 3 ? k_batch_diag_s3 : k_batch_diag;
             const BatchQueue Q = queue(b, r, r.items3, active);
             const dim3 grid(std::min((int)r.items3.h.size(), 2 * b.sms));
             B_CU(launch(dk, grid, dim3(NT), sizeof(DiagSmemT<3>), b.stream, Q, *T), "k_batch_diag");

@@ -846,6 +846,8 @@ __device__ __forceinline__ float pw_weight(int f, float w1, int node) {
 // DS > 0: the shuffle steps of the run sums as a compile-time count (the
 // largest any tile of the plan needs; extra steps add nothing to a run's
 // head, so the sums are the same); DS = 0: per tile from the parameters.
+// With two or more voxels per cell the first x tile's clamped lane 0 makes
+// a run of at least three, so a three-node span needs two steps or more.
 template <int SPAN, int DS = 0>
 __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, int bz) {
     NGF_DYNAMIC_SMEM(smraw);
@@ -1097,9 +1099,6 @@ __device__ __forceinline__ void diag_pass(const ImgParams& P, int bx, int by, in
 // 64 registers and its shared memory twice per SM: two CTAs per SM, 27%
 // faster on the thorax grid than one CTA of 111 registers.
 __global__ void __launch_bounds__(NT, 2) k_diag(const ImgParams P) { diag_pass<3>(P, blockIdx.x, blockIdx.y, blockIdx.z); }
-__global__ void __launch_bounds__(NT, 2) k_diag_s1(const ImgParams P) {
-    diag_pass<3, 1>(P, blockIdx.x, blockIdx.y, blockIdx.z);
-}
 __global__ void __launch_bounds__(NT, 2) k_diag_s2(const ImgParams P) {
     diag_pass<3, 2>(P, blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -1586,7 +1585,7 @@ __device__ __forceinline__ void queue_release(const BatchQueue& Q) {
 }
 
 // KIND 0..2: image pass mode (NGF or SSD per pair), 3/4: NGF diagonal (span 3/4), 5: SSD diagonal,
-// 6..8: NGF diagonal of span 3 with 1..3 shuffle steps fixed at compile time;
+// 7, 8: NGF diagonal of span 3 with 2 or 3 shuffle steps fixed at compile time;
 // SM: shared-memory layout of the NGF image pass
 template <int KIND, class SM = ImgSmemC>
 __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q, const BatchImgTable& T) {
@@ -1602,7 +1601,7 @@ __device__ __forceinline__ void batch_image_loop(const BatchQueue& Q, const Batc
         if (!Q.active || Q.active[it.x]) {
             const ImgParams& Ps = T.p[it.x - Q.pair0];
             if (KIND == 3) diag_pass<3>(Ps, it.y, it.z, it.w);
-            else if (KIND >= 6 && KIND <= 8) diag_pass<3, (KIND >= 6 && KIND <= 8) ? KIND - 5 : 0>(Ps, it.y, it.z, it.w);
+            else if (KIND == 7 || KIND == 8) diag_pass<3, (KIND == 7 || KIND == 8) ? KIND - 5 : 0>(Ps, it.y, it.z, it.w);
             else if (KIND == 4) diag_pass<4>(Ps, it.y, it.z, it.w);
             else if (KIND == 5) ssd_pass<MODE_SSD_DIAG>(Ps, it.y, it.z, it.w);
             else if (T.ssd[it.x - Q.pair0]) ssd_pass<KIND>(Ps, it.y, it.z, it.w);
@@ -1633,9 +1632,6 @@ __global__ void __launch_bounds__(NT, 2) k_batch_image_hess_w(const BatchQueue Q
 }
 __global__ void __launch_bounds__(NT, 2) k_batch_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
     batch_image_loop<3>(Q, T);
-}
-__global__ void __launch_bounds__(NT, 2) k_batch_diag_s1(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
-    batch_image_loop<6>(Q, T);
 }
 __global__ void __launch_bounds__(NT, 2) k_batch_diag_s2(const BatchQueue Q, const __grid_constant__ BatchImgTable T) {
     batch_image_loop<7>(Q, T);

@@ -265,8 +265,7 @@ __global__ void k_image_obj_w(const ImgParams P);
 __global__ void k_image_grad_w(const ImgParams P);
 __global__ void k_image_hess_w(const ImgParams P);
 __global__ void k_diag(const ImgParams P);        // Jacobi-diagonal tile partials (>= 2 voxels per cell)
-// the same with 1, 2 or 3 shuffle steps per run sum fixed at compile time
-__global__ void k_diag_s1(const ImgParams P);
+// the same with 2 or 3 shuffle steps per run sum fixed at compile time
 __global__ void k_diag_s2(const ImgParams P);
 __global__ void k_diag_s3(const ImgParams P);
 __global__ void k_diag4(const ImgParams P);       // same, any voxels-per-cell ratio
@@ -341,7 +340,6 @@ __global__ void k_batch_image_obj_w(const BatchQueue Q, const __grid_constant__ 
 __global__ void k_batch_image_grad_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_image_hess_w(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
-__global__ void k_batch_diag_s1(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag_s2(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag_s3(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
 __global__ void k_batch_diag4(const BatchQueue Q, const __grid_constant__ BatchImgTable T);
