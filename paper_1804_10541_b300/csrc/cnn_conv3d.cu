@@ -84,6 +84,15 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
+// 16 columns of zeros into this warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_load16(uint32_t taddr, float (&v)[16]) {
     uint32_t r[16];
     asm volatile(
@@ -142,22 +151,38 @@ struct BrickArgs {
     int tps;          // taps per weight stage: 1, 3, 9 or 27
     int nbuf;         // weight buffers (1 .. CONV_MAXBUF)
     int tiles_x, tiles_y, tiles_z;
+    int zs;           // z-stacked taps: one MMA per (dy, dx, input plane) with N = 3 ns
+    int tcols;        // tensor-memory columns allocated
 };
 
 // Weights of (slice, chunk, tap) repacked into the exact shared-memory image
 // of the B operand (K-major core matrices), so that one bulk copy moves a
-// whole stage.
+// whole stage.  z-stacked (zs): one image per (slice, chunk, dy, dx) of
+// 3 ns rows, row b ns + o holding tap (2 - b, dy, dx) of output channel o.
+__device__ __forceinline__ void pack_index(long long idx, int ns, int qk, int nch, int zs, long long& dst, int& slice,
+                                           int& chunk, int& tap, int& n, int& q) {
+    const int rows = zs ? 3 * ns : ns, per_stage = rows * qk, nimg = zs ? 9 : 27;
+    const long long st = idx / per_stage;  // (slice * nch + chunk) * nimg + image
+    const int r = (int)(idx - st * per_stage), nr = r / qk;
+    q = r - nr * qk;
+    const int img = (int)(st % nimg);
+    chunk = (int)((st / nimg) % nch);
+    slice = (int)(st / ((long long)nimg * nch));
+    n = zs ? nr % ns : nr;
+    tap = zs ? (2 - nr / ns) * 9 + img : img;
+    dst = st * per_stage + operand_off(nr, q, rows) / 16;
+}
+
 __global__ void k_conv3d_pack_w(const uint4* __restrict__ w, uint4* __restrict__ wp, int cout, int cin, int ns,
-                                int kc) {
-    const int qk = kc / 8, per_stage = ns * qk, nch = cin / kc;
-    const long long total = (long long)(cout / ns) * nch * 27 * per_stage;
+                                int kc, int zs) {
+    const int qk = kc / 8, nch = cin / kc;
+    const long long total = (long long)(cout / ns) * nch * 27 * ns * qk;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const long long st = idx / per_stage;  // (slice * nch + chunk) * 27 + tap
-        const int r = (int)(idx - st * per_stage), n = r / qk, q = r - n * qk;
-        const int tap = (int)(st % 27), chunk = (int)((st / 27) % nch), slice = (int)(st / (27LL * nch));
-        wp[st * per_stage + operand_off(n, q, ns) / 16] =
-            w[((long long)(slice * ns + n) * 27 + tap) * (cin / 8) + chunk * qk + q];
+        long long dst;
+        int slice, chunk, tap, n, q;
+        pack_index(idx, ns, qk, nch, zs, dst, slice, chunk, tap, n, q);
+        wp[dst] = w[((long long)(slice * ns + n) * 27 + tap) * (cin / 8) + chunk * qk + q];
     }
 }
 
@@ -167,15 +192,15 @@ __global__ void k_conv3d_pack_w(const uint4* __restrict__ w, uint4* __restrict__
 // from the forward layout w[cout][27][cin]) into the same shared-memory image
 // as k_conv3d_pack_w, for a convolution with cin' = cout and cout' = cin.
 __global__ void k_conv3d_pack_wT(const __nv_bfloat16* __restrict__ w, uint4* __restrict__ wp, int cout_f,
-                                 int cin_f, int ns, int kc) {
+                                 int cin_f, int ns, int kc, int zs) {
     const int cinp = cout_f, coutp = cin_f;  // channels of the mirrored convolution
-    const int qk = kc / 8, per_stage = ns * qk, nch = cinp / kc;
-    const long long total = (long long)(coutp / ns) * nch * 27 * per_stage;
+    const int qk = kc / 8, nch = cinp / kc;
+    const long long total = (long long)(coutp / ns) * nch * 27 * ns * qk;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
          idx += (long long)gridDim.x * blockDim.x) {
-        const long long st = idx / per_stage;
-        const int r = (int)(idx - st * per_stage), n = r / qk, q = r - n * qk;
-        const int tap = (int)(st % 27), chunk = (int)((st / 27) % nch), slice = (int)(st / (27LL * nch));
+        long long dst;
+        int slice, chunk, tap, n, q;
+        pack_index(idx, ns, qk, nch, zs, dst, slice, chunk, tap, n, q);
         const int oc = slice * ns + n;  // output channel of the mirrored convolution = forward input channel
         uint32_t pk[4];
         for (int e = 0; e < 8; e += 2) {
@@ -184,7 +209,7 @@ __global__ void k_conv3d_pack_wT(const __nv_bfloat16* __restrict__ w, uint4* __r
             const __nv_bfloat16 hi = w[((long long)(ic0 + 1) * 27 + (26 - tap)) * cin_f + oc];
             pk[e / 2] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
         }
-        wp[st * per_stage + operand_off(n, q, ns) / 16] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        wp[dst] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
 }
 
@@ -235,9 +260,11 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
     const int nbuf = a.nbuf, P = a.P, cg = a.kc / 8, ns = a.ns, n0 = blockIdx.y * a.ns;
     const int nb = BR_X * BR_Y * (P + 2);           // brick voxels
     const uint32_t gplane = brick_plane_bytes(P);   // one channel group of the brick
-    const uint32_t brick_bytes = (uint32_t)cg * gplane, b_bytes = (uint32_t)ns * a.kc * 2;
+    // one B image: ns rows (a tap) or, z-stacked, 3 ns rows (the three dz of one (dy, dx))
+    const int nimg = a.zs ? 9 : 27;  // B images per chunk
+    const uint32_t brick_bytes = (uint32_t)cg * gplane, b_bytes = (uint32_t)(a.zs ? 3 : 1) * ns * a.kc * 2;
     const uint32_t st_bytes = a.tps * b_bytes;     // one weight stage
-    const int spc = 27 / a.tps;                    // stages per chunk
+    const int spc = nimg / a.tps;                  // stages per chunk
     const uint32_t sBr = smem_addr(smem), sB = sBr + brick_bytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + brick_bytes + nbuf * st_bytes);
     uint64_t* empty = full + CONV_MAXBUF;
@@ -245,7 +272,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
     uint64_t* brick_bar = chunk_bar + 1;                 // the brick's tensor copies
     int* flags = reinterpret_cast<int*>(brick_bar + 1);  // [0] failed, [1] copies issued, [2] stages consumed
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags + 3);
-    const uint32_t tcols = (uint32_t)(P * a.ncols);
+    const uint32_t tcols = (uint32_t)a.tcols;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
@@ -271,11 +298,19 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
     const int b = t / a.tiles_z;
     const int x0 = tx * 8, y0 = ty * 16, z0 = tz * P;
     const unsigned char* wp = reinterpret_cast<const unsigned char*>(a.w) +
-                              (size_t)blockIdx.y * a.nch * 27 * b_bytes;  // this slice's stages
+                              (size_t)blockIdx.y * a.nch * nimg * b_bytes;  // this slice's stages
     uint32_t tmem = 0;
     bool failed = false;
     int brick_pending = -1;  // chunk whose brick copy is issued and not seen complete
     __syncthreads();  // barriers and flags initialised before the producer's first copy
+    if (a.zs) {  // z-stacked accumulators start at zero: every MMA accumulates
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t t0 = *tmem_slot + ((uint32_t)(warp * 32) << 16);
+        for (uint32_t col = 0; col < tcols; col += 16) tmem_zero16(t0 + col);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+    }
 
     for (int c = 0; c < a.nch; ++c) {
         if (c > 0) {
@@ -330,7 +365,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
             produce(pre_end, spc * c + spc);  // weight producer, second part
         } else if (tid == 0) {
             // MMA issuer
-            const uint32_t idesc = instr_desc(CONV_M, ns);
+            const uint32_t idesc = instr_desc(CONV_M, a.zs ? 3 * ns : ns);
             const uint32_t lbo = gplane;  // one channel group plane
             // Descriptors of the brick's and the weight buffers' starts: an
             // operand at byte offset o (a multiple of 16) is the start's
@@ -338,7 +373,8 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
             // address / 16 in 14 bits and shared addresses stay below 256 KB
             // (no carry out of the field).
             const uint64_t ad0 = smem_desc(sBr, lbo, BR_X * 16), bd0 = smem_desc(sB, 128, 256);
-            const uint32_t ja = 2 * lbo / 16, jb = (uint32_t)(ns / 8) * 256 / 16, nkj = (uint32_t)(a.kc / 16);
+            const uint32_t ja = 2 * lbo / 16, jb = (uint32_t)((a.zs ? 3 : 1) * ns / 8) * 256 / 16,
+                           nkj = (uint32_t)(a.kc / 16);
             for (int s = spc * c; s < spc * c + spc; ++s) {
                 const int buf = s % nbuf;
                 if (!mbar_wait(smem_addr(&full[buf]), (uint32_t)((s / nbuf) & 1))) {
@@ -347,14 +383,25 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 for (int i = 0; i < a.tps; ++i) {
-                    const int tap = (s - spc * c) * a.tps + i;
-                    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;  // brick offsets 0..2
+                    const int img = (s - spc * c) * a.tps + i;
                     const uint64_t bd = bd0 + (buf * st_bytes + i * b_bytes) / 16;
-                    uint64_t ad = ad0 + (uint32_t)((dz * BR_Y + dy) * BR_X + dx);  // 16 bytes per brick voxel
-                    uint32_t d = tmem;
-                    for (int p = 0; p < P; ++p, ad += BR_X * BR_Y, d += (uint32_t)a.ncols)
-                        for (uint32_t j = 0; j < nkj; ++j)
-                            mma_bf16(d, ad + j * ja, bd + j * jb, idesc, (s > 0 || i > 0 || j > 0) ? 1u : 0u);
+                    if (a.zs) {
+                        // (dy, dx) = img: input plane pi meets dz = 2, 1, 0 (image rows
+                        // 0, ns, 2 ns) for output planes pi - 2, pi - 1, pi, whose
+                        // accumulators sit at columns (q + 2) ns: one MMA at pi ns
+                        const int dy = img / 3, dx = img % 3;
+                        uint64_t ad = ad0 + (uint32_t)(dy * BR_X + dx);  // 16 bytes per brick voxel
+                        uint32_t d = tmem;
+                        for (int pi = 0; pi < P + 2; ++pi, ad += BR_X * BR_Y, d += (uint32_t)ns)
+                            for (uint32_t j = 0; j < nkj; ++j) mma_bf16(d, ad + j * ja, bd + j * jb, idesc, 1u);
+                    } else {
+                        const int dz = img / 9, dy = (img / 3) % 3, dx = img % 3;  // brick offsets 0..2
+                        uint64_t ad = ad0 + (uint32_t)((dz * BR_Y + dy) * BR_X + dx);
+                        uint32_t d = tmem;
+                        for (int p = 0; p < P; ++p, ad += BR_X * BR_Y, d += (uint32_t)a.ncols)
+                            for (uint32_t j = 0; j < nkj; ++j)
+                                mma_bf16(d, ad + j * ja, bd + j * jb, idesc, (s > 0 || i > 0 || j > 0) ? 1u : 0u);
+                    }
                 }
                 mma_commit(smem_addr(&empty[buf]));
                 flags[2] = s + 1;
@@ -380,7 +427,7 @@ __global__ void __launch_bounds__(CONV_THREADS) k_conv3d_brick(const BrickArgs a
             const long long obase = row_ok ? ((((long long)b * a.D + vz) * a.H + vy) * a.W + vx) * a.cout + n0 : 0;
             for (int cc = 0; cc < ns; cc += 16) {
                 float r[16];
-                tmem_load16(tmem + lane_base + (uint32_t)(p * a.ncols + cc), r);
+                tmem_load16(tmem + lane_base + (uint32_t)((a.zs ? (p + 2) * ns : p * a.ncols) + cc), r);
                 if (row_ok) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
@@ -757,24 +804,51 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
             if (brick + nbf * wst <= 110 * 1024 || p == 1) { br.P = p; br.nbuf = nbf; break; }
         }
         br.tiles_z = (D + br.P - 1) / br.P;
-        const long long tiles = (long long)br.tiles_x * br.tiles_y * br.tiles_z * B;
+        long long tiles = (long long)br.tiles_x * br.tiles_y * br.tiles_z * B;
         while (br.ns % 32 == 0 && tiles * (Cout / br.ns) < sm_count) br.ns /= 2;
         br.ncols = 32;
         while (br.ncols < br.ns) br.ncols <<= 1;
-        const size_t wst = (size_t)br.ns * br.kc * 2;
+        br.zs = 0;
+        br.tcols = br.P * br.ncols;
+        // z-stacked taps for slices of at most 64 output channels: an MMA of
+        // N = 16..64 reads its 128 x 16 A operand for little work, so the
+        // three dz taps of one (dy, dx) go into one MMA of N = 3 ns over each
+        // brick plane, (P + 2) / (3 P) of the MMAs and A reads.  Four planes
+        // per CTA (or two) whose (P + 4) ns accumulator columns fit 256 (two
+        // CTAs per SM), whose brick and one weight image fit, and that still
+        // give every SM a CTA; eight planes (fewer CTAs per SM) measured
+        // slower on the 128^3 16->16 layer (0.122 vs 0.097 ms).
+        if (br.ns <= 64) {
+            for (int pz : {4, 2}) {
+                if (pz > 2 && pz > D) continue;
+                int tc = 32;
+                while (tc < (pz + 4) * br.ns) tc <<= 1;
+                const long long tz = (long long)br.tiles_x * br.tiles_y * ((D + pz - 1) / pz) * B;
+                if (tc > 256 || (pz > 2 && tz * (Cout / br.ns) < sm_count)) continue;
+                if ((size_t)(br.kc / 8) * brick_plane_bytes(pz) + (size_t)3 * br.ns * br.kc * 2 > 110 * 1024) continue;
+                br.zs = 1;
+                br.P = pz;
+                br.tcols = tc;
+                br.tiles_z = (D + pz - 1) / pz;
+                tiles = tz;
+                break;
+            }
+        }
+        const int nimg = br.zs ? 9 : 27;  // B images per chunk
+        const size_t wst = (size_t)(br.zs ? 3 : 1) * br.ns * br.kc * 2;
         const size_t brick = (size_t)(br.kc / 8) * brick_plane_bytes(br.P);
-        // taps per weight stage: small weight images are moved several taps
-        // per bulk copy (fewer waits in the MMA thread's chain)
+        // images per weight stage: small weight images are moved several per
+        // bulk copy (fewer waits in the MMA thread's chain)
         br.tps = 1;
         for (int tp : {27, 9, 3})
-            if (tp * wst <= 24 * 1024 && brick + tp * wst <= 110 * 1024) { br.tps = tp; break; }
-        const int stages = br.nch * (27 / br.tps);
+            if (tp <= nimg && tp * wst <= 24 * 1024 && brick + tp * wst <= 110 * 1024) { br.tps = tp; break; }
+        const int stages = br.nch * (nimg / br.tps);
         br.nbuf = stages < CONV_MAXBUF ? stages : CONV_MAXBUF;
         while (br.nbuf > 1 && brick + br.nbuf * br.tps * wst > 110 * 1024) --br.nbuf;
         // + 128: the brick is aligned to 128 bytes inside the dynamic block
         size_t smem = 128 + brick + br.nbuf * br.tps * wst + (2 * CONV_MAXBUF + 2) * sizeof(uint64_t) + 32;
         // every resident CTA's tensor-memory allocation must fit at once
-        const size_t ctas = 512 / (br.P * br.ncols);
+        const size_t ctas = 512 / br.tcols;
         const size_t smem_min = per_sm / (ctas + 1) - 1024 + 16;
         if (smem < smem_min) smem = smem_min;
         if (tiles >= (1LL << 31) || smem > 200 * 1024) return NGF_EBOUNDS;
@@ -787,9 +861,9 @@ ngf_status conv_run(const void* x, const void* w, bool mirrored, const float* bi
         const dim3 pg((unsigned)((chunks + 255) / 256));
         const cudaError_t pe =
             mirrored ? launch(k_conv3d_pack_wT, pg, dim3(256), 0, st, static_cast<const __nv_bfloat16*>(w),
-                              static_cast<uint4*>(wp), (int)Cin, (int)Cout, br.ns, br.kc)
+                              static_cast<uint4*>(wp), (int)Cin, (int)Cout, br.ns, br.kc, br.zs)
                      : launch(k_conv3d_pack_w, pg, dim3(256), 0, st, static_cast<const uint4*>(w),
-                              static_cast<uint4*>(wp), (int)Cout, (int)Cin, br.ns, br.kc);
+                              static_cast<uint4*>(wp), (int)Cout, (int)Cin, br.ns, br.kc, br.zs);
         CUtensorMap xmap;
         const bool mapped = brick_map(&xmap, x, B, D, H, W, Cin, br.P);
         const bool ok = pe == cudaSuccess && mapped &&
