@@ -40,9 +40,10 @@ extern "C" {
  * stream-ordered pool (NGF_ENOMEM if that fails; released on the stream
  * after the launch); then one CTA computes an 8 x 16 x P block of output
  * voxels (P = 1, 2 or 4) for a slice of the output channels from an input
- * brick staged in shared memory once per 64 input channels.  Repeated calls
- * with the same arguments give identical results (no atomics; each output
- * accumulates (channel chunk, tap) in a fixed order). */
+ * brick copied to shared memory (TMA) once per 64 input channels; slices of
+ * at most 64 output channels multiply the three z taps of a (dy, dx) in one
+ * MMA.  Repeated calls with the same arguments give identical results (no
+ * atomics; each output accumulates its products in a fixed order). */
 ngf_status ngf_conv3d_fwd(const void* x, const void* w, const float* bias, float* y,
                           int32_t B, int32_t D, int32_t H, int32_t W,
                           int32_t Cin, int32_t Cout, int32_t relu, void* cuda_stream);
