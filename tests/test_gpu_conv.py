@@ -107,12 +107,14 @@ def test_conv3d_empty_and_bad_arguments(ngf):
 # Volumes with at least as many output tiles (8 x 16 x P voxels) as the GPU
 # has SMs, so that no output-channel slicing happens and every CTA computes
 # all output channels of its tile (the path the 64^3 and 128^3 layers take),
-# with 16 to 64 input channels, a batch of two and ragged tiles.
+# with 16 to 128 input channels, a batch of two and ragged tiles; the ones
+# with at most 64 output channels take the z-stacked taps.
 LARGE_CASES = [
     (1, 32, 48, 64, 32, 64),
     (1, 40, 64, 64, 16, 16),
     (2, 24, 48, 40, 16, 32),
     (1, 32, 64, 64, 64, 64),
+    (1, 32, 64, 64, 128, 32),  # z-stacked taps, 4 planes per CTA, two 64-channel chunks
 ]
 
 
