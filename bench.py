@@ -416,6 +416,8 @@ def run_ours(args):
                 "config": {"workload": f"{workload} {m[0]}x{m[1]}x{m[2]} at {h[0]}x{h[1]}x{h[2]} mm, nodes "
                                        f"{n[0]}x{n[1]}x{n[2]}, {levels} levels, {GN_ITERS} GN x {PCG_ITERS} PCG; "
                                        f"one step = one full register_multilevel",
+                           "jacobi_preconditioner": "exact GN diagonal, computed at each level's first "
+                                                    "Gauss-Newton step and kept for the level",
                            "parallelism": f"replicas x{ws}", "l2": "flushed before every step (256 MB write)",
                            "registration_ms": 1e3 * t_max / args.steps, "final_J": r0.J,
                            "gn_done": r0.gn_done, "pcg_total": r0.pcg_total, "ls_trials": r0.ls_trials,

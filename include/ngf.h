@@ -209,6 +209,10 @@ typedef struct {
                              the start of each of its steps, i.e. after every
                              accepted step); 0 = off.  Used to compare starts
                              at equal final objective.  GN only.              */
+    int32_t diag_every;   /* the Jacobi diagonal of the PCG solves is recomputed
+                             at Gauss-Newton steps 0, k, 2k, ... of each level
+                             (k = diag_every) and kept in between; 0 = once per
+                             level, at its first step (the default).  GN only. */
 } ngf_options;
 enum { NGF_METHOD_GN = 0, NGF_METHOD_LBFGS = 1 };
 

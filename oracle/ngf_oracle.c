@@ -616,7 +616,9 @@ void orc_gn_level(const orc_level* L, const double* R, const double* T, double* 
         if (trace) trace[2 * k] = J0;
         double gg = vdot(n, g, g);
         if (gg == 0.0) { rep->status = 8; break; }
-        orc_gn_diagonal(L, R, T, u, diag);
+        /* the preconditioner is refreshed on the level's schedule and
+           otherwise kept from an earlier iterate of the level */
+        if (o->diag_every > 0 ? k % o->diag_every == 0 : k == 0) orc_gn_diagonal(L, R, T, u, diag);
         for (long i = 0; i < n; ++i) rhs[i] = -g[i];
         orc_pcg_info info;
         orc_pcg(L, R, T, u, rhs, diag, o->pcg_iters, o->pcg_rtol, s, &info);

@@ -109,6 +109,9 @@ typedef struct {
     int32_t ls_max;      /* Armijo halvings allowed                       */
     double  armijo_c1;   /* sufficient-decrease constant                  */
     double  pcg_rtol;    /* <= 0: fixed iteration count                   */
+    int32_t diag_every;  /* Jacobi diagonal at steps 0, k, 2k, ... of the
+                            level (k = diag_every), kept in between;
+                            0: at the first step only                     */
 } orc_gn_options;
 
 typedef struct {

@@ -32,7 +32,7 @@ class PcgInfo(C.Structure):
 
 class GnOptions(C.Structure):
     _fields_ = [("gn_iters", C.c_int32), ("pcg_iters", C.c_int32), ("ls_max", C.c_int32),
-                ("armijo_c1", C.c_double), ("pcg_rtol", C.c_double)]
+                ("armijo_c1", C.c_double), ("pcg_rtol", C.c_double), ("diag_every", C.c_int32)]
 
 
 class GnReport(C.Structure):
@@ -178,10 +178,10 @@ def pcg(L, R, T, u, rhs, diag, iters, rtol=0.0):
     return x, info
 
 
-def gn_options(gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rtol=0.0):
+def gn_options(gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rtol=0.0, diag_every=0):
     o = GnOptions()
     o.gn_iters, o.pcg_iters, o.ls_max = gn_iters, pcg_iters, ls_max
-    o.armijo_c1, o.pcg_rtol = armijo_c1, pcg_rtol
+    o.armijo_c1, o.pcg_rtol, o.diag_every = armijo_c1, pcg_rtol, diag_every
     return o
 
 

@@ -824,8 +824,11 @@ static ngf_status register_batch_impl(int np, const ngf_level_desc* finest, cons
             }
             if (std::none_of(active.begin(), active.end(), [](int a) { return a != 0; })) break;
             B_CU(put(tb.act, active), "upload mask");
-            B_TRY(launch_diag(b, tb.diag, act));
-            B_TRY(launch_combine(b, tb.comb_diag.d, act));
+            // Jacobi diagonal at the level's first step, then every diag_every steps
+            if (o->diag_every > 0 ? it % o->diag_every == 0 : it == 0) {
+                B_TRY(launch_diag(b, tb.diag, act));
+                B_TRY(launch_combine(b, tb.comb_diag.d, act));
+            }
             B_CU(launch(k_scale, dim3(grid_for((long long)off[np], 4 * b.sms)), dim3(NT), 0, stream,
                         (long long)off[np], -1.0f, (const float*)g, r),
                  "k_scale");
@@ -934,7 +937,7 @@ extern "C" ngf_status register_batch(int32_t npairs, const ngf_level_desc* fines
         return set_error(nullptr, NGF_EINVAL, "gn_iters_finest and j_target are not supported by the batched registration");
     if (o->method != NGF_METHOD_GN)
         return set_error(nullptr, NGF_EINVAL, "the batched registration runs Gauss-Newton only");
-    if (o->zc < 0) return set_error(nullptr, NGF_EINVAL, "zc must be >= 0");
+    if (o->zc < 0 || o->diag_every < 0) return set_error(nullptr, NGF_EINVAL, "zc and diag_every must be >= 0");
     for (int k = 0; k < npairs; ++k)
         for (const void* ptr : {(const void*)R[k], (const void*)T[k], (const void*)u_out[k]})
             if (!is_device_ptr(ptr))

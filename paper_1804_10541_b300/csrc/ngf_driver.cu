@@ -203,7 +203,7 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
     if (o->levels < 1 || o->levels > 16) return set_error(nullptr, NGF_EINVAL, "levels must be in [1, 16]");
     if (o->gn_iters < 0 || o->pcg_iters < 0 || o->ls_max < 1)
         return set_error(nullptr, NGF_EINVAL, "gn_iters, pcg_iters >= 0 and ls_max >= 1 required");
-    if (o->zc < 0) return set_error(nullptr, NGF_EINVAL, "zc must be >= 0");
+    if (o->zc < 0 || o->diag_every < 0) return set_error(nullptr, NGF_EINVAL, "zc and diag_every must be >= 0");
     if (o->gn_iters_finest < 0 || !(o->j_target >= 0.0))
         return set_error(nullptr, NGF_EINVAL, "gn_iters_finest and j_target must be >= 0");
     if (o->method != NGF_METHOD_GN && o->method != NGF_METHOD_LBFGS)
@@ -380,7 +380,9 @@ extern "C" ngf_status register_multilevel(const ngf_level_desc* finest, const ng
             const double J0 = h[0] + d.alpha * h[1], gg = h[2];
             if (gg == 0.0) break;  // stationary point
             if (l == 0 && o->j_target > 0.0 && J0 <= o->j_target) break;  // target objective reached
-            DRV_TRY(diagonal_impl(p, Rl[l], Tl[l], u, bdiag.as<float>()));
+            // Jacobi diagonal at the level's first step, then every diag_every steps
+            if (o->diag_every > 0 ? k % o->diag_every == 0 : k == 0)
+                DRV_TRY(diagonal_impl(p, Rl[l], Tl[l], u, bdiag.as<float>()));
             DRV_CU(launch(k_scale, dim3(p->node_blocks), dim3(NT), 0, stream, n, -1.0f, (const float*)g, st.r),
                    "k_scale");
             DRV_TRY(pcg_init(pg.p, &st, st.r));

@@ -54,7 +54,7 @@ class Options(C.Structure):
                 ("armijo_c1", C.c_double), ("pcg_rtol", C.c_double), ("start_level", C.c_int32),
                 ("u_init", C.c_void_p), ("use_graph", C.c_int32), ("method", C.c_int32),
                 ("lbfgs_memory", C.c_int32), ("lbfgs_gamma", C.c_double), ("zc", C.c_int32),
-                ("gn_iters_finest", C.c_int32), ("j_target", C.c_double)]
+                ("gn_iters_finest", C.c_int32), ("j_target", C.c_double), ("diag_every", C.c_int32)]
 
 
 class Report(C.Structure):
@@ -325,7 +325,7 @@ def pcg_read(plan, st):
 
 def options(levels, gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rtol=0.0, u_init=None,
             start_level=0, use_graph=True, method=NGF_METHOD_GN, lbfgs_memory=5, lbfgs_gamma=0.0, zc=0,
-            gn_iters_finest=0, j_target=0.0):
+            gn_iters_finest=0, j_target=0.0, diag_every=0):
     o = Options()
     o.levels, o.gn_iters, o.pcg_iters, o.ls_max = levels, gn_iters, pcg_iters, ls_max
     o.armijo_c1, o.pcg_rtol, o.start_level = armijo_c1, pcg_rtol, start_level
@@ -334,6 +334,7 @@ def options(levels, gn_iters=10, pcg_iters=20, ls_max=10, armijo_c1=1e-4, pcg_rt
     o.method, o.lbfgs_memory, o.lbfgs_gamma = int(method), int(lbfgs_memory), float(lbfgs_gamma)
     o.zc = int(zc)
     o.gn_iters_finest, o.j_target = int(gn_iters_finest), float(j_target)
+    o.diag_every = int(diag_every)
     return o
 
 

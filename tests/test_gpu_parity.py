@@ -215,36 +215,39 @@ def test_pcg_matches_oracle_and_graph(ngf):
     assert G.rel(G.f64(x), xo) < G.TOL_PCG
 
 
-def _registration_pair(ngf, gn_iters):
+def _registration_pair(ngf, gn_iters, diag_every=0):
     import oracle as O
     from paper_1804_10541_b300 import synth
     R, T, _, w = synth.make("blobs_32", device="cuda")
     desc = ngf.level_desc(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"])
     N = int(np.prod(w["n"]))
     u = torch.empty(3 * N, device="cuda")
-    opts = ngf.options(levels=w["levels"], gn_iters=gn_iters, pcg_iters=20)
+    opts = ngf.options(levels=w["levels"], gn_iters=gn_iters, pcg_iters=20, diag_every=diag_every)
     rep = ngf.register_multilevel(desc, opts, R, T, u, torch.cuda.Stream())
     L = O.level(w["m"], w["h"], w["n"], w["alpha"], w["tau"], w["rho"])
-    uo, ro = O.register_multilevel(L, w["levels"], O.gn_options(gn_iters=gn_iters, pcg_iters=20), G.f64(R), G.f64(T))
+    oo = O.gn_options(gn_iters=gn_iters, pcg_iters=20, diag_every=diag_every)
+    uo, ro = O.register_multilevel(L, w["levels"], oo, G.f64(R), G.f64(T))
     du = float(np.max(np.abs(G.f64(u) - uo))) / min(w["h"])
     dJ = abs(rep.J - ro.J) / ro.J
     msg = f"max |u - u_oracle| = {du:.3e} voxel, rel J diff = {dJ:.3e}, J = {rep.J} vs {ro.J}"
     return rep, ro, du, dJ, msg
 
 
-def test_register_multilevel_matches_oracle_blobs32(ngf):
-    """Config 0 (2 levels, 20 PCG iterations per step).  With 3 Gauss-Newton
-    steps per level both sides take the same step lengths and the final u
-    agrees within 0.01 voxel.  With the full 10 steps per level an Armijo
-    decision near its threshold can flip between the float32 and float64
-    PCG solutions (step 8 of the finest level takes eta = 1/4 instead of
-    1/8), after which u differs by a fraction of a voxel while the final
-    objective agrees within 0.1%."""
-    rep, ro, du, dJ, msg = _registration_pair(ngf, 3)
+@pytest.mark.parametrize("diag_every", [0, 1])
+def test_register_multilevel_matches_oracle_blobs32(ngf, diag_every):
+    """Config 0 (2 levels, 20 PCG iterations per step), with the Jacobi
+    diagonal once per level (the default) and at every step.  With 3
+    Gauss-Newton steps per level both sides take the same step lengths and
+    the final u agrees within 0.01 voxel.  With the full 10 steps per level
+    an Armijo decision near its threshold can flip between the float32 and
+    float64 PCG solutions (a step of 1/4 instead of 1/8), after which u
+    differs by a fraction of a voxel while the final objective agrees
+    within 0.1%."""
+    rep, ro, du, dJ, msg = _registration_pair(ngf, 3, diag_every)
     assert rep.status == 0 and ro.status == 0, msg
     assert rep.gn_done == ro.gn_done and rep.pcg_total == ro.pcg_total, msg
     assert du < 0.01 and dJ < 1e-5, msg
-    rep, ro, du, dJ, msg = _registration_pair(ngf, 10)
+    rep, ro, du, dJ, msg = _registration_pair(ngf, 10, diag_every)
     assert rep.status == 0 and ro.status == 0, msg
     assert rep.gn_done == ro.gn_done and rep.pcg_total == ro.pcg_total, msg
     assert dJ < 1e-3, msg

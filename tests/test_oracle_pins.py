@@ -501,6 +501,47 @@ def test_gn_level_monotone_and_armijo(orc):
     assert rep.J < 0.9 * trace[0]
 
 
+def test_gn_level_diagonal_schedule(orc):
+    """The Jacobi preconditioner is computed at the level's first iterate and
+    kept (diag_every = 0).  Pinned by recomposing the second step from the
+    building blocks: gradient at u1, PCG with the diagonal taken at u0,
+    Armijo halving from eta = 1.  Refreshing at every step (diag_every = 1)
+    takes the diagonal at u1 instead and gives another second step; a
+    refresh interval longer than the level is the once-per-level schedule."""
+    from paper_1804_10541_b300 import synth
+    m, h, n = (12, 10, 8), (1.0, 1.0, 1.0), (7, 6, 5)
+    R, T, _ = synth.blob_pair(m, seed=3)
+    R, T = R.double().numpy(), T.double().numpy()
+    L = orc.level(m, h, n, alpha=1.0, tau=0.1, rho=0.1)
+    nn = 3 * orc.nnod(L)
+    u0 = np.zeros(nn)
+    u1, rep1, _ = orc.gn_level(L, R, T, u0, orc.gn_options(gn_iters=1, pcg_iters=10))
+    u2, rep2, _ = orc.gn_level(L, R, T, u0, orc.gn_options(gn_iters=2, pcg_iters=10))
+    u2e, _, _ = orc.gn_level(L, R, T, u0, orc.gn_options(gn_iters=2, pcg_iters=10, diag_every=1))
+    u2l, _, _ = orc.gn_level(L, R, T, u0, orc.gn_options(gn_iters=2, pcg_iters=10, diag_every=5))
+    assert rep1.gn_done == 1 and rep2.gn_done == 2
+    g, D, S = orc.gradient(L, R, T, u1)
+    J0 = D + 1.0 * S
+
+    def second_step(diag):
+        s, _ = orc.pcg(L, R, T, u1, -g, diag, 10)
+        gs = float(g @ s)
+        assert gs < 0.0
+        eta = 1.0
+        for _ in range(10):
+            ut = u1 + eta * s
+            Dt, St = orc.objective(L, R, T, ut)
+            if Dt + St <= J0 + 1e-4 * eta * gs:
+                return ut
+            eta *= 0.5
+        raise AssertionError("no Armijo step")
+
+    np.testing.assert_allclose(u2, second_step(orc.gn_diagonal(L, R, T, u0)), rtol=0, atol=1e-12)
+    np.testing.assert_allclose(u2e, second_step(orc.gn_diagonal(L, R, T, u1)), rtol=0, atol=1e-12)
+    assert np.max(np.abs(u2 - u2e)) > 1e-9
+    assert np.array_equal(u2l, u2)
+
+
 # ---- L-BFGS (Sec. 2.3.2) ---------------------------------------------------
 
 def _dense_curvature_hessian(orc, L):
