@@ -289,9 +289,10 @@ static ngf_status create_plan(Plan* p, const ngf_level_desc* d, cudaStream_t str
     // (rounds of 2 CTAs per SM) x (planes marched per chunk, 7 of them fill
     // and drain the image pass's pipeline); small levels get short chunks,
     // since a CTA's march over its planes is sequential
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int dev = 0, sms = 0;
+    NGF_CU(p, cudaGetDevice(&dev), "cudaGetDevice");
+    NGF_CU(p, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev),
+           "cudaDeviceGetAttribute(multiprocessor count)");
     const long long txy = (long long)((p->m[0] + TX - 1) / TX) * ((p->m[1] + TY - 1) / TY);
     const long long slots = 2LL * sms;
     long long best_k = 1, best_cost = LLONG_MAX;

@@ -168,8 +168,9 @@ static ngf_status build_batch(Batch* b, int np, const ngf_level_desc* descs, int
     b->stream = stream;
     b->descs.assign(descs, descs + np);
     int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    B_CU(cudaGetDevice(&dev), "cudaGetDevice");
+    B_CU(cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev),
+         "cudaDeviceGetAttribute(multiprocessor count)");
     if (zc == 0) zc = batch_zc(descs, np, b->sms);
     for (int k = 0; k < np; ++k) {
         ngf_plan* pl = nullptr;
