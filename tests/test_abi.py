@@ -110,6 +110,21 @@ def test_size_limit_and_distance_validation(ngf):
     assert ngf.lib.ngf_batch_create(C.byref(bh), 0, C.byref(ok), 0, None) == -1 and not bh.value
 
 
+def test_preconditioner_schedule_validation(ngf):
+    """A negative refresh interval of the Jacobi diagonal is rejected by the
+    single and the batched registration before any CUDA call."""
+    ok = ngf.level_desc((8, 8, 8), (1, 1, 1), (5, 5, 5))
+    buf = (C.c_float * 600)()
+    rep = ngf.Report()
+    opts = ngf.options(2, diag_every=-1)
+    assert ngf.lib.register_multilevel(C.byref(ok), C.byref(opts), buf, buf, buf, C.byref(rep), None) == -1
+    assert "diag_every" in ngf.ngf_last_error(None)
+    ptrs = (C.c_void_p * 1)(C.addressof(buf))
+    reps = (ngf.Report * 1)()
+    assert ngf.lib.register_batch(1, C.byref(ok), C.byref(opts), ptrs, ptrs, ptrs, reps, 0, None) == -1
+    assert "diag_every" in ngf.ngf_last_error(None)
+
+
 def test_tile_depth_and_convolution_validation(ngf):
     """A negative z-chunk length and convolution shapes outside the documented
     limits are rejected before any CUDA call."""
