@@ -177,9 +177,9 @@ def test_thorax_full_size_properties(ngf):
 
 
 def test_pcg_matches_oracle_and_graph(ngf):
-    """PCG iterates equal the oracle's.  pcg_solve (two launches per
-    iteration: the image pass and the cooperative nodal kernel), directly and
-    as a captured graph, reproduces pcg_step (five launches per iteration)
+    """PCG iterates equal the oracle's.  pcg_solve, with direct launches and
+    as a captured graph, reproduces repeated pcg_step calls (five launches
+    per iteration: Laplacian, image pass, node combine, update, direction)
     bitwise in every state vector and float64 scalar."""
     import oracle as O
     c, _ = G.workload_case("blobs_32")
