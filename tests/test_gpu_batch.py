@@ -105,9 +105,13 @@ def _blob_batch(sizes):
 
 
 @pytest.mark.parametrize("use_graph", [True, False])
-def test_register_batch_equals_per_pair_registration(ngf, use_graph):
+@pytest.mark.parametrize("diag_every", [0, 3])
+def test_register_batch_equals_per_pair_registration(ngf, use_graph, diag_every):
+    """Each pair of a batched registration takes exactly its own
+    registration's decisions, with the Jacobi diagonal once per level and
+    refreshed every third Gauss-Newton step."""
     pairs = _blob_batch([24, 33, 40, 29])
-    opts = ngf.options(2, gn_iters=4, pcg_iters=8, use_graph=use_graph, zc=ZC)
+    opts = ngf.options(2, gn_iters=4, pcg_iters=8, use_graph=use_graph, zc=ZC, diag_every=diag_every)
     ub = [torch.zeros(3 * d.n[0] * d.n[1] * d.n[2], device="cuda") for _, _, d in pairs]
     # graphs need a stream other than the legacy default stream
     stream = torch.cuda.Stream() if use_graph else None
