@@ -37,6 +37,31 @@ def _case(m, h, n, seed):
 
 
 @pytest.mark.parametrize("m,h,n", CASES)
+def test_2d_ssd_operators_match_oracle(ngf, m, h, n):
+    """SSD on a planar level: the halo-free pass with one node plane against
+    the oracle's planar SSD operators (pinned by the dense 2-D assembly)."""
+    import oracle as O
+    c = _case(m, h, n, sum(m) + 3)
+    c.desc = ngf.level_desc(m, h, n, 0.7, 0.1, 0.1, distance=ngf.NGF_DIST_SSD)
+    c.L = O.level(m, h, n, 0.7, distance=O.DIST_SSD)
+    N = c.N
+    with ngf.Plan(c.desc) as pl:
+        D, S = ngf.ngf_objective(pl.handle, c.R, c.T, c.u)
+        g, q, dg = c.empty(), c.empty(), c.empty()
+        ngf.ngf_gradient(pl.handle, c.R, c.T, c.u, g, want_scalars=False)
+        ngf.gn_hessvec(pl.handle, c.R, c.T, c.u, c.p, q)
+        ngf.ngf_gn_diagonal(pl.handle, c.R, c.T, c.u, dg)
+        torch.cuda.synchronize()
+    Do, So = O.objective(c.L, c.Rh, c.Th, c.uh)
+    assert abs(D - Do) / abs(Do) < G.TOL_OBJ and abs(S - So) / So < G.TOL_OBJ
+    assert G.rel(G.f64(g), O.gradient(c.L, c.Rh, c.Th, c.uh)[0]) < G.TOL_GRAD
+    assert G.rel(G.f64(q), O.hessvec(c.L, c.Rh, c.Th, c.uh, c.ph)) < G.TOL_HESS
+    assert G.rel(G.f64(dg), O.gn_diagonal(c.L, c.Rh, c.Th, c.uh)) < G.TOL_DIAG
+    for v in (g, q):  # no z component in 2-D (the diagonal's z block holds the curvature part)
+        assert not torch.any(v[2 * N:])
+
+
+@pytest.mark.parametrize("m,h,n", CASES)
 def test_2d_operators_match_oracle(ngf, m, h, n):
     import oracle as O
     c = _case(m, h, n, sum(m))

@@ -46,6 +46,32 @@ def test_2d_operators_match_dense_assembly(orc, m, h, n):
     assert rel(d[:2 * N], np.diag(H)) < 1e-8
 
 
+@pytest.mark.parametrize("m,h,n", CASES)
+def test_2d_ssd_operators_match_dense_assembly(orc, m, h, n):
+    """SSD on a planar level (Sec. 7: the residual is Tw - R, its Jacobian the
+    identity) against the same dense 2-D factors: D = hbar/2 ||Tw - R||^2,
+    grad = hbar (dT P)^T (Tw - R), H = hbar (dT P)^T (dT P), each with the
+    2-D curvature term; the z block of every field stays zero."""
+    R, T, u2, u3, p2, p3 = _problem(m, n, sum(m) + 7)
+    L = orc.level(m, h, n, 0.7, distance=orc.DIST_SSD)
+    N = n[0] * n[1]
+    a = A.Assembled2D(m, h, n, 0.7, 0.15, 0.25, R, T, u2)
+    res = a.Tw - R
+    Jc = a.dT @ a.P
+    D_ref = 0.5 * a.hbar * np.sum(res ** 2)
+    g_ref = a.hbar * (res @ Jc) + 0.7 * 2.0 * a.hbary * (a.Lap.T @ (a.Lap @ u2))
+    H = a.hbar * Jc.T @ Jc + 0.7 * 2.0 * a.hbary * a.Lap.T @ a.Lap
+    rel = lambda x, y: np.linalg.norm(x - y) / np.linalg.norm(y)
+    D, _ = orc.objective(L, R, T, u3)
+    assert abs(D - D_ref) <= 1e-12 * abs(D_ref)
+    g, Dg, _ = orc.gradient(L, R, T, u3)
+    assert Dg == D and rel(g[:2 * N], g_ref) < 1e-8 and not np.any(g[2 * N:])
+    q = orc.hessvec(L, R, T, u3, p3)
+    assert rel(q[:2 * N], H @ p2) < 1e-8 and not np.any(q[2 * N:])
+    d = orc.gn_diagonal(L, R, T, u3)
+    assert rel(d[:2 * N], np.diag(H)) < 1e-8
+
+
 def test_2d_gradient_finite_differences(orc):
     m, h, n = (9, 7, 1), (1.0, 1.2, 1.0), (5, 4, 1)
     R, T, u2, u3, _, _ = _problem(m, n, 11)
